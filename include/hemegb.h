@@ -1,0 +1,261 @@
+/*
+ * hemegb.h -- C ABI of the GB300 sparse lattice-Boltzmann hot path.
+ *
+ * Method: "Towards Blood Flow in the Virtual Human: Efficient Self-Coupling of
+ * HemeLB" (arXiv 2010.04144).  Section 2 fixes the solver: D3Q19 lattice,
+ * single-relaxation-time (LBGK) collision, rigid walls, pressure and velocity
+ * boundary conditions at inlets and outlets, Newtonian fluid on a sparse
+ * vascular geometry.  Section 2.3 and Section 3 fix the self-coupling: only
+ * averaged macroscopic values cross between coupled boundaries, and the
+ * arterial outlet's average velocity, times a per-pair scale factor (the
+ * velocity-scale equation after Eq. (1)), becomes the velocity boundary
+ * condition of the paired venous inlet.
+ *
+ * Conventions (every function):
+ *   - returns HG_OK (0) or a negative HG_ERR_* code; hg_last_error(ctx) then
+ *     holds a message owned by the context (valid until the next call);
+ *   - sizes and counts are int64_t; handles are opaque;
+ *   - host arrays passed in are owned by the caller and copied during the
+ *     call; host arrays passed out are caller-allocated;
+ *   - the library owns all device memory it allocates (through the context's
+ *     allocator callback, else cudaMalloc);
+ *   - work is ordered on the context's CUDA stream; hg_step* only enqueue,
+ *     hg_read_* / hg_save_state / hg_mass synchronise the stream;
+ *   - a context and its domains are not thread-safe.
+ *
+ * Lattice conventions (identical on every entry point):
+ *   - velocities: i = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),
+ *     (-1,-1,0),(1,-1,0),(-1,1,0),(1,0,1),(-1,0,-1),(1,0,-1),(-1,0,1),(0,1,1),
+ *     (0,-1,-1),(0,1,-1),(0,-1,1); weights 1/3, 1/18, 1/36;
+ *   - canonical site order: ascending 3-D Morton key (x in bit 0);
+ *   - neighbour table nbr[18][N]: nbr[i-1][s] = canonical index of the fluid
+ *     site at x_s - c_i (pull source), else -(2+k) when that lattice point
+ *     lies in the opening of iolet k, else -1 (wall);
+ *   - distributions are stored as deviations from the lattice weights
+ *     (f~ = f - w); FP16/BF16 storage keeps f~_i / w_i.
+ */
+#ifndef HEMEGB_H
+#define HEMEGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---- */
+#define HG_OK 0
+#define HG_ERR_ARG (-1)     /* invalid argument (sizes, ranges, handles) */
+#define HG_ERR_OOM (-2)     /* device or host allocation failed */
+#define HG_ERR_CUDA (-3)    /* a CUDA call failed (message holds the CUDA error) */
+#define HG_ERR_TIMEOUT (-4) /* a bounded device wait gave up (reserved) */
+#define HG_ERR_STATE (-5)   /* call not valid in the object's current state */
+
+/* ---- distribution storage ---- */
+#define HG_STORE_F32 0  /* f~ in FP32 */
+#define HG_STORE_F16 1  /* f~/w in FP16 (round to nearest even), collision in FP32 */
+#define HG_STORE_BF16 2 /* f~/w in BF16 (round to nearest even), collision in FP32 */
+
+/* ---- propagation scheme ---- */
+#define HG_SCHEME_AB 0 /* two buffers, pull streaming every step */
+#define HG_SCHEME_AA 1 /* one buffer, in place: even steps local, odd steps gather+scatter */
+
+/* ---- iolets ---- */
+#define HG_PRESSURE 0  /* anti-bounce-back: f~_i = -f~*_opp + 2 w_i drho_k */
+#define HG_VELOCITY 1  /* moving-wall bounce-back: f~_i = f~*_opp + 6 w_i c_i.u_w */
+#define HG_PLUG 0      /* velocity profile: uniform */
+#define HG_PARABOLIC 1 /* velocity profile: peak on the axis, zero at the radius */
+#define HG_PULSE_CONST 0  /* value(t) = value */
+#define HG_PULSE_COSINE 1 /* value(t) = value * (1 - cos(2 pi t / period)) / 2 */
+#define HG_PULSE_SINE 2   /* value(t) = value * sin(2 pi t / period) */
+
+/* ---- site orderings (device layout; exported data is always canonical) ---- */
+#define HG_ORDER_MORTON 0 /* canonical order */
+
+typedef struct hg_ctx hg_ctx;
+typedef struct hg_domain hg_domain;
+
+/* Device allocator hook: returns a device pointer of at least `bytes` bytes
+ * (256-byte aligned) or NULL; `free` receives the pointer and size. */
+typedef void *(*hg_alloc_fn)(size_t bytes, void *user);
+typedef void (*hg_free_fn)(void *ptr, size_t bytes, void *user);
+
+typedef struct {
+    int32_t device;           /* CUDA device ordinal */
+    int32_t storage;          /* HG_STORE_* */
+    int32_t scheme;           /* HG_SCHEME_* */
+    int32_t block_size;       /* stream-collide threads per block (multiple of 32, <= 512); 0 = 256 */
+    int32_t sites_per_thread; /* 1, 2 or 4; 0 = 1 */
+    int32_t graph_steps;      /* steps captured per CUDA graph; 0 = 16; negative = no graphs */
+    void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
+    hg_alloc_fn alloc;        /* NULL = cudaMalloc */
+    hg_free_fn free;          /* NULL = cudaFree */
+    void *alloc_user;
+} hg_ctx_params;
+
+/* Iolet descriptor.  Section 3.1: vessel tips are cut flat, perpendicular to
+ * the centreline; the cut disc is the opening.  Fixed point: 1 lattice unit =
+ * 1024.  A non-fluid lattice point q is in the opening when it lies beyond the
+ * plane through `centre` normal to `axis` (axis points out of the fluid) by at
+ * most 2 lattice units and within `radius` of the axis line; the test is exact
+ * integer arithmetic, the lowest iolet index wins.  Limits: |centre| <= 2^31,
+ * |axis| components <= 2^20 (not all zero), 0 <= radius <= 2^31. */
+typedef struct {
+    int32_t kind;    /* HG_PRESSURE / HG_VELOCITY */
+    int32_t profile; /* HG_PLUG / HG_PARABOLIC (velocity iolets) */
+    int32_t pulse;   /* HG_PULSE_* */
+    int32_t reserved;
+    double value;    /* density deviation drho (pressure) or peak inward speed (velocity) */
+    double period;   /* pulse period in steps (pulsed iolets) */
+    int64_t centre[3];
+    int64_t axis[3];
+    int64_t radius;
+} hg_iolet;
+
+typedef struct {
+    double tau;       /* relaxation time, 0.5 < tau (Section 3.3 quotes tau in (0.5, 1]) */
+    int32_t ordering; /* HG_ORDER_* device site layout */
+    int32_t reserved;
+} hg_lb_params;
+
+/* One forward coupling pair (Section 3): from now on the velocity iolet
+ * dst_iolet of the destination domain takes, at time t, the value
+ * factor * (mean of u.n over the sites next to src_iolet of the source domain
+ * at time t-1), n the source iolet's unit outward axis. */
+typedef struct {
+    int32_t src_iolet;
+    int32_t dst_iolet;
+    double factor;
+} hg_pair;
+
+/* ---- context ---- */
+
+/* Create a context on p->device.  Storage and scheme apply to every domain of
+ * the context.  Errors: HG_ERR_ARG (bad field), HG_ERR_CUDA. */
+int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out);
+
+/* Destroy a context and every domain still attached to it. */
+int hg_ctx_destroy(hg_ctx *ctx);
+
+/* Message of the last failed call on this context (or its domains); "" if none. */
+const char *hg_last_error(hg_ctx *ctx);
+
+/* Wait for all work enqueued on the context's stream. */
+int hg_sync(hg_ctx *ctx);
+
+/* ---- domains ---- */
+
+/* Build a domain from fluid voxels (Section 2.2: sparse geometry, only fluid
+ * sites stored).  xyz: n_fluid x 3 int32 lattice coordinates, any order, no
+ * duplicates, each in [0, 2^21).  iolets: n_iolets descriptors (<= 256).
+ * Builds the canonical site order and neighbour table, classifies iolet links,
+ * uploads everything and initialises the rest state f~ = 0 at step 0.
+ * Errors: HG_ERR_ARG (range, duplicate, too many iolets, tau <= 0.5),
+ * HG_ERR_OOM, HG_ERR_CUDA. */
+int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets,
+                     int32_t n_iolets, const hg_lb_params *lb, hg_domain **out);
+
+/* Free a domain's device memory and detach it from its context.  Coupling
+ * pairs that involve it are dropped. */
+int hg_domain_destroy(hg_domain *d);
+
+/* Sizes: sites, iolets, sites next to any iolet, completed steps, device
+ * bytes held.  Any out pointer may be NULL. */
+int hg_domain_info(hg_domain *d, int64_t *n_sites, int32_t *n_iolets, int64_t *n_adjacent,
+                   int64_t *step, int64_t *device_bytes);
+
+/* Canonical site coordinates, n_sites x 3 int32 (host). */
+int hg_domain_sites(hg_domain *d, int32_t *xyz_out);
+
+/* Canonical neighbour table as used on the device, nbr[18][n_sites] int32
+ * (host), decoded to the conventions above. */
+int hg_domain_neighbours(hg_domain *d, int32_t *nbr_out);
+
+/* ---- coupling (Section 2.3, Section 3) ---- */
+
+/* Add forward coupling pairs from src to dst (both in ctx, src != dst).  Each
+ * dst_iolet must be a velocity iolet and may appear once; the pairs take
+ * effect from the next step.  Both domains must then be stepped together.
+ * Errors: HG_ERR_ARG. */
+int hg_couple(hg_ctx *ctx, hg_domain *src, hg_domain *dst, const hg_pair *pairs, int32_t n_pairs);
+
+/* Host helper for Section 3's coupling map and scale factors.
+ * Map: arteries in ascending order each take the closest venous inlet not yet
+ * taken; every venous inlet left joins its closest artery (ties: lowest
+ * index; distances compared exactly on the fixed-point centres).  Pressure
+ * drops: dP_v/P_0 = 0.3 + 0.4 * uniforms[v] (uniform in [0.3, 0.7]).
+ * Factors: the velocity-scale equation after Eq. (1),
+ *   v_i/v_0 = (A_0/A_i) r_i / sum_j r_j,  r_i = dP_i L_1 A_i / (dP_1 L_i A_1).
+ * Inputs: art_centres n_art x 3 and ven_centres n_ven x 3 (fixed point 2^-10),
+ * areas in lattice units^2, uniforms n_ven values in [0, 1).  Outputs (n_ven
+ * each): assign (artery index), dist (lattice units), dp, factor.
+ * Errors: HG_ERR_ARG (n_art < 1, zero distance, non-positive area). */
+int hg_coupling_factors(const int64_t *art_centres, const double *art_areas, int32_t n_art,
+                        const int64_t *ven_centres, const double *ven_areas, int32_t n_ven,
+                        const double *uniforms, int32_t *assign, double *dist, double *dp,
+                        double *factor);
+
+/* ---- stepping ---- */
+
+/* Advance every domain of the context by n_steps LB steps.  Step t streams the
+ * post-collision state F_{t-1} (pull from x - c_i; wall, pressure and velocity
+ * rules on non-fluid links, with boundary values of time t), collides (LBGK,
+ * tau) into F_t, then reduces the iolet means of time t in FP64 and sets the
+ * boundary values of time t+1 (pulses; coupled inlets from the means).
+ * Groups of steps run as captured CUDA graphs.  Asynchronous. */
+int hg_step(hg_ctx *ctx, int64_t n_steps);
+
+/* Same for a subset of the context's domains (coupled partners included);
+ * the domains may be at different step counts. */
+int hg_step_domains(hg_ctx *ctx, hg_domain *const *doms, int32_t n_doms, int64_t n_steps);
+
+/* Like hg_step but without graphs and with CUDA events around every kernel:
+ * total milliseconds spent in the stream-collide kernel and in the iolet
+ * update kernel (either pointer may be NULL).  Synchronises. */
+int hg_step_profiled(hg_ctx *ctx, int64_t n_steps, double *ms_stream_collide,
+                     double *ms_iolet);
+
+/* ---- read-back ---- */
+
+/* Macroscopic fields of the current state F_t, canonical order, n_sites x 4
+ * FP32 host array: (drho, ux, uy, uz), drho = rho - 1, u = j / rho. */
+int hg_read_macroscopic(hg_domain *d, float *out, int64_t *step_out);
+
+/* Same into a caller-owned device array (n_sites x 4 FP32, 16-byte aligned);
+ * asynchronous on the context stream. */
+int hg_read_macroscopic_device(hg_domain *d, float *dev_out);
+
+/* Iolet means of the last completed step, n_iolets x 3 FP64 host array:
+ * (mean u.n over the sites next to the iolet, mean drho there, site count);
+ * n is the iolet's unit outward axis.  Sums in FP64 in canonical order. */
+int hg_read_iolet_stats(hg_domain *d, double *out);
+
+/* Boundary values the next step will use, n_iolets FP32 (host). */
+int hg_read_boundary_values(hg_domain *d, float *out);
+
+/* Total mass deviation sum_s sum_i f~_i(s) of the current state, FP64. */
+int hg_mass(hg_domain *d, double *out);
+
+/* ---- checkpoint / resume ---- */
+
+/* Bytes needed by hg_save_state for this domain. */
+int hg_state_bytes(hg_domain *d, int64_t *bytes);
+
+/* Save the current state (step count, boundary values, iolet means, and F_t
+ * in canonical order in the storage type) to a host buffer. */
+int hg_save_state(hg_domain *d, void *host_buf, int64_t bytes);
+
+/* Restore a state written by hg_save_state of a domain with the same
+ * geometry, storage and scheme; stepping then continues bit-identically. */
+int hg_load_state(hg_domain *d, const void *host_buf, int64_t bytes);
+
+/* Raw state of the current time level F_t as 19 x n_sites values of the
+ * storage type (FP32, or f~/w in FP16/BF16), canonical order (host). */
+int hg_read_state(hg_domain *d, void *host_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HEMEGB_H */

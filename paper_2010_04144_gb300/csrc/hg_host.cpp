@@ -1,0 +1,1198 @@
+// hg_host.cpp -- host runtime behind the C ABI in include/hemegb.h.
+//
+// Geometry (Section 2.2: sparse vascular geometry, only non-empty blocks
+// stored): fluid voxels are sorted into canonical Morton order; a sparse set
+// of 8^3 blocks, each with a 512-bit occupancy map, answers "which site sits
+// at lattice point q" in O(1) via popcount rank.  Non-fluid link targets are
+// classified against the iolet openings in exact 128-bit integer arithmetic.
+//
+// Stepping: per set of domains a plan holds the stream-collide tile table,
+// the per-iolet update table and a captured CUDA graph of G steps; kernels
+// read the step parity from device counters, so the graph replays unchanged.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/hemegb.h"
+#include "hg_internal.h"
+
+using namespace hg;
+
+namespace {
+
+// ---------------------------------------------------------------- lattice
+const int kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1, 0},
+                       {0, 0, 1},  {0, 0, -1},  {1, 1, 0},  {-1, -1, 0}, {1, -1, 0},
+                       {-1, 1, 0}, {1, 0, 1},   {-1, 0, -1}, {1, 0, -1}, {-1, 0, 1},
+                       {0, 1, 1},  {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+inline double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
+
+// ---------------------------------------------------------------- threads
+int n_threads() {
+    unsigned h = std::thread::hardware_concurrency();
+    if (h == 0) h = 4;
+    return (int)std::min<unsigned>(h, 64);
+}
+
+template <typename F> void parallel_for(int64_t n, F &&fn, int64_t grain = 1 << 14) {
+    int T = n_threads();
+    int64_t chunks = (n + grain - 1) / grain;
+    if (T <= 1 || chunks <= 1) {
+        fn((int64_t)0, n);
+        return;
+    }
+    std::atomic<int64_t> next{0};
+    std::vector<std::thread> th;
+    for (int t = 0; t < std::min<int64_t>(T, chunks); ++t)
+        th.emplace_back([&] {
+            for (;;) {
+                int64_t c = next.fetch_add(1);
+                if (c >= chunks) break;
+                int64_t lo = c * grain, hi = std::min(n, lo + grain);
+                fn(lo, hi);
+            }
+        });
+    for (auto &x : th) x.join();
+}
+
+// ---------------------------------------------------------------- Morton
+inline uint64_t spread21(uint64_t v) {
+    v &= 0x1fffffULL;
+    v = (v | (v << 32)) & 0x1f00000000ffffULL;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffULL;
+    v = (v | (v << 8)) & 0x100f00f00f00f00fULL;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ULL;
+    v = (v | (v << 2)) & 0x1249249249249249ULL;
+    return v;
+}
+inline uint64_t morton3(uint32_t x, uint32_t y, uint32_t z) {
+    return spread21(x) | (spread21(y) << 1) | (spread21(z) << 2);
+}
+
+// ---------------------------------------------------------------- iolets
+bool iolet_ok(const hg_iolet &io) {
+    const int64_t lim = (int64_t)1 << 31;
+    bool nz = false;
+    for (int d = 0; d < 3; ++d) {
+        if (io.centre[d] < -lim || io.centre[d] > lim) return false;
+        if (io.axis[d] < -(1 << 20) || io.axis[d] > (1 << 20)) return false;
+        nz = nz || io.axis[d] != 0;
+    }
+    if (!nz || io.radius < 0 || io.radius > lim) return false;
+    if (io.kind != HG_PRESSURE && io.kind != HG_VELOCITY) return false;
+    if (io.profile != HG_PLUG && io.profile != HG_PARABOLIC) return false;
+    if (io.pulse < HG_PULSE_CONST || io.pulse > HG_PULSE_SINE) return false;
+    if (io.pulse != HG_PULSE_CONST && !(io.period > 0)) return false;
+    return true;
+}
+
+struct IoletGeom {
+    hg_iolet d;
+    double cx, cy, cz, reach2;  // centre (lattice units) and a bounding radius^2
+};
+
+// Exact opening test: 0 < (q-c).a <= 2|a| and |(q-c) x a|^2 <= r^2 |a|^2 (fixed point).
+bool in_opening(const hg_iolet &io, int64_t qx, int64_t qy, int64_t qz) {
+    typedef __int128 i128;
+    const i128 dx = (i128)qx * 1024 - io.centre[0];
+    const i128 dy = (i128)qy * 1024 - io.centre[1];
+    const i128 dz = (i128)qz * 1024 - io.centre[2];
+    const i128 ax = io.axis[0], ay = io.axis[1], az = io.axis[2];
+    const i128 dot = dx * ax + dy * ay + dz * az;
+    if (dot <= 0) return false;
+    const i128 aa = ax * ax + ay * ay + az * az;
+    if (dot * dot > (i128)(2048 * 2048) * aa) return false;
+    const i128 c0 = dy * az - dz * ay, c1 = dz * ax - dx * az, c2 = dx * ay - dy * ax;
+    const i128 r = io.radius;
+    return c0 * c0 + c1 * c1 + c2 * c2 <= r * r * aa;
+}
+
+int32_t classify(const std::vector<IoletGeom> &io, int64_t qx, int64_t qy, int64_t qz) {
+    for (size_t k = 0; k < io.size(); ++k) {
+        const IoletGeom &g = io[k];
+        const double ddx = qx - g.cx, ddy = qy - g.cy, ddz = qz - g.cz;
+        if (ddx * ddx + ddy * ddy + ddz * ddz > g.reach2) continue;
+        if (in_opening(g.d, qx, qy, qz)) return -(2 + (int32_t)k);
+    }
+    return -1;
+}
+
+// ---------------------------------------------------------------- sparse blocks
+// Blocks of 8^3 lattice points in Morton order: block key = morton >> 9.
+struct BlockIndex {
+    std::vector<uint64_t> bkey;    // sorted block keys
+    std::vector<int64_t> first;    // canonical index of the block's first site
+    std::vector<uint64_t> bits;    // 8 words per block: occupancy by in-block Morton offset
+    std::vector<uint16_t> prefix;  // 8 per block: sites in words before w
+    std::vector<int32_t> table;    // open-addressing hash: block key -> block id
+    uint64_t mask = 0;
+
+    static inline uint64_t hash(uint64_t k) { return (k * 0x9E3779B97F4A7C15ULL) >> 17; }
+
+    void build(const std::vector<uint64_t> &keys) {
+        const int64_t n = (int64_t)keys.size();
+        for (int64_t s = 0; s < n; ++s) {
+            const uint64_t b = keys[s] >> 9;
+            if (bkey.empty() || bkey.back() != b) {
+                bkey.push_back(b);
+                first.push_back(s);
+            }
+        }
+        const int64_t nb = (int64_t)bkey.size();
+        bits.assign(nb * 8, 0);
+        prefix.assign(nb * 8, 0);
+        for (int64_t b = 0; b < nb; ++b) {
+            const int64_t hi = (b + 1 < nb) ? first[b + 1] : n;
+            for (int64_t s = first[b]; s < hi; ++s) {
+                const unsigned o = (unsigned)(keys[s] & 511);
+                bits[b * 8 + (o >> 6)] |= 1ULL << (o & 63);
+            }
+            uint16_t acc = 0;
+            for (int w = 0; w < 8; ++w) {
+                prefix[b * 8 + w] = acc;
+                acc += (uint16_t)__builtin_popcountll(bits[b * 8 + w]);
+            }
+        }
+        uint64_t cap = 16;
+        while (cap < (uint64_t)nb * 2) cap <<= 1;
+        mask = cap - 1;
+        table.assign(cap, -1);
+        for (int64_t b = 0; b < nb; ++b) {
+            uint64_t h = hash(bkey[b]) & mask;
+            while (table[h] >= 0) h = (h + 1) & mask;
+            table[h] = (int32_t)b;
+        }
+    }
+
+    inline int64_t find(uint64_t key) const {
+        const uint64_t b = key >> 9;
+        uint64_t h = hash(b) & mask;
+        for (;;) {
+            const int32_t id = table[h];
+            if (id < 0) return -1;
+            if (bkey[id] == b) {
+                const unsigned o = (unsigned)(key & 511);
+                const uint64_t w = bits[(int64_t)id * 8 + (o >> 6)];
+                const uint64_t bit = 1ULL << (o & 63);
+                if (!(w & bit)) return -1;
+                return first[id] + prefix[(int64_t)id * 8 + (o >> 6)] +
+                       __builtin_popcountll(w & (bit - 1));
+            }
+            h = (h + 1) & mask;
+        }
+    }
+};
+
+// Canonical order: sort (key, index) pairs by key -- bucket by the leading key
+// bits, then sort each bucket, buckets in parallel.
+void sort_keys(std::vector<uint64_t> &key, std::vector<int64_t> &idx) {
+    const int64_t n = (int64_t)key.size();
+    if (n <= 1) return;
+    uint64_t mx = 0;
+    for (int64_t s = 0; s < n; ++s) mx = std::max(mx, key[s]);
+    int bl = 64 - (mx ? __builtin_clzll(mx) : 63);
+    const int nbits = 12;
+    const int shift = std::max(0, bl - nbits);
+    const int64_t nbk = (int64_t)1 << nbits;
+    std::vector<int64_t> cnt(nbk + 1, 0);
+    for (int64_t s = 0; s < n; ++s) cnt[(key[s] >> shift) + 1]++;
+    for (int64_t b = 0; b < nbk; ++b) cnt[b + 1] += cnt[b];
+    std::vector<std::pair<uint64_t, int64_t>> tmp(n);
+    {
+        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+        for (int64_t s = 0; s < n; ++s) tmp[pos[key[s] >> shift]++] = {key[s], idx[s]};
+    }
+    std::atomic<int64_t> next{0};
+    std::vector<std::thread> th;
+    for (int t = 0; t < n_threads(); ++t)
+        th.emplace_back([&] {
+            for (;;) {
+                int64_t b = next.fetch_add(1);
+                if (b >= nbk) break;
+                std::sort(tmp.begin() + cnt[b], tmp.begin() + cnt[b + 1]);
+            }
+        });
+    for (auto &x : th) x.join();
+    for (int64_t s = 0; s < n; ++s) {
+        key[s] = tmp[s].first;
+        idx[s] = tmp[s].second;
+    }
+}
+
+double pulse(int kind, double t, double period) {
+    if (kind == HG_PULSE_COSINE) return 0.5 * (1.0 - std::cos(2.0 * 3.141592653589793 * t / period));
+    if (kind == HG_PULSE_SINE) return std::sin(2.0 * 3.141592653589793 * t / period);
+    return 1.0;
+}
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+// ================================================================ objects
+struct PlanKey {
+    std::vector<int32_t> doms;
+    bool operator<(const PlanKey &o) const { return doms < o.doms; }
+};
+
+struct Plan {
+    std::vector<int32_t> doms;
+    DevBuf tiles, ios, adv;
+    int64_t n_tiles = 0;
+    int n_ios = 0;
+    cudaGraphExec_t graph = nullptr;
+    int graph_steps = 0;
+};
+
+struct CoupleSrc {
+    int32_t src_dom, src_k;
+    double factor;
+};
+
+struct hg_ctx {
+    int device = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int storage = 0, scheme = 0, block = 256, spt = 1, graph_steps = 16;
+    hg_alloc_fn alloc = nullptr;
+    hg_free_fn free_fn = nullptr;
+    void *alloc_user = nullptr;
+    std::string err;
+    std::vector<hg_domain *> doms;  // by index (nullptr = free slot)
+    DevBuf dom_table;               // DomDev[capacity]
+    DevBuf steps;                   // int64[capacity]
+    int capacity = 0;
+    std::map<std::pair<int32_t, int32_t>, CoupleSrc> coupled;  // (dst dom, dst k) -> source
+    std::map<PlanKey, std::unique_ptr<Plan>> plans;
+    DevBuf scratch;                 // mass partials, read-back staging
+    int64_t device_bytes = 0;
+};
+
+struct hg_domain {
+    hg_ctx *ctx = nullptr;
+    int32_t idx = -1;
+    int64_t n = 0, np = 0;
+    int32_t nio = 0;
+    double tau = 0.8;
+    int64_t n_adj = 0;
+    int64_t step = 0;  // host mirror of completed steps
+    std::vector<int32_t> xyz;           // canonical coordinates
+    std::vector<hg_iolet> io;
+    std::vector<int32_t> io_ptr;        // CSR over slots per iolet
+    DevBuf f[2], nbr, iomask, bnd, coef, bcv, io_kind, M, slots;
+    int64_t bytes = 0;
+};
+
+namespace {
+
+int fail(hg_ctx *ctx, int code, const char *fmt, ...) {
+    if (ctx) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof buf, fmt, ap);
+        va_end(ap);
+        ctx->err = buf;
+    }
+    return code;
+}
+
+#define CU(ctx, call)                                                                       \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(ctx, HG_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_));  \
+    } while (0)
+
+int dev_alloc(hg_ctx *ctx, DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    bytes = (bytes + 255) & ~(size_t)255;
+    void *p = nullptr;
+    if (ctx->alloc) {
+        p = ctx->alloc(bytes, ctx->alloc_user);
+        if (!p) return fail(ctx, HG_ERR_OOM, "allocator callback returned NULL for %zu bytes", bytes);
+    } else {
+        cudaError_t e = cudaMalloc(&p, bytes);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            return fail(ctx, HG_ERR_OOM, "cudaMalloc(%zu) failed: %s", bytes, cudaGetErrorString(e));
+        }
+    }
+    b.p = p;
+    b.bytes = bytes;
+    ctx->device_bytes += (int64_t)bytes;
+    return HG_OK;
+}
+
+void dev_free(hg_ctx *ctx, DevBuf &b) {
+    if (!b.p) return;
+    if (ctx->free_fn) ctx->free_fn(b.p, b.bytes, ctx->alloc_user);
+    else cudaFree(b.p);
+    ctx->device_bytes -= (int64_t)b.bytes;
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+void drop_plans(hg_ctx *ctx) {
+    for (auto &kv : ctx->plans) {
+        Plan &p = *kv.second;
+        if (p.graph) cudaGraphExecDestroy(p.graph);
+        dev_free(ctx, p.tiles);
+        dev_free(ctx, p.ios);
+        dev_free(ctx, p.adv);
+    }
+    ctx->plans.clear();
+}
+
+DomDev make_domdev(hg_ctx *ctx, hg_domain *d) {
+    DomDev D;
+    memset(&D, 0, sizeof D);
+    D.f[0] = d->f[0].p;
+    D.f[1] = d->f[1].p;
+    D.nbr = (const int32_t *)d->nbr.p;
+    D.iomask = (const uint32_t *)d->iomask.p;
+    D.bnd = (float4 *)d->bnd.p;
+    D.coef = (const float *)d->coef.p;
+    D.bcv = (const float *)d->bcv.p;
+    D.io_kind = (const int8_t *)d->io_kind.p;
+    D.step = (const int64_t *)ctx->steps.p + d->idx;
+    D.n = d->n;
+    D.np = d->np;
+    D.omega = (float)(1.0 / d->tau);
+    D.n_io = d->nio;
+    return D;
+}
+
+const DomDev *domdev_ptr(hg_domain *d) {
+    return (const DomDev *)d->ctx->dom_table.p + d->idx;
+}
+
+size_t elem_bytes(int storage) { return storage == HG_STORE_F32 ? 4 : 2; }
+
+int ensure_scratch(hg_ctx *ctx, size_t bytes) {
+    if (ctx->scratch.bytes >= bytes) return HG_OK;
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    dev_free(ctx, ctx->scratch);
+    return dev_alloc(ctx, ctx->scratch, bytes);
+}
+
+}  // namespace
+
+// ================================================================ C ABI
+extern "C" {
+
+int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
+    if (!p || !out) return HG_ERR_ARG;
+    *out = nullptr;
+    if (p->storage < HG_STORE_F32 || p->storage > HG_STORE_BF16) return HG_ERR_ARG;
+    if (p->scheme != HG_SCHEME_AB && p->scheme != HG_SCHEME_AA) return HG_ERR_ARG;
+    int block = p->block_size ? p->block_size : 256;
+    int spt = p->sites_per_thread ? p->sites_per_thread : 1;
+    if (block < 32 || block > 512 || block % 32) return HG_ERR_ARG;
+    if (spt != 1 && spt != 2 && spt != 4) return HG_ERR_ARG;
+    if ((p->alloc == nullptr) != (p->free == nullptr)) return HG_ERR_ARG;
+    std::unique_ptr<hg_ctx> c(new hg_ctx);
+    c->device = p->device;
+    c->storage = p->storage;
+    c->scheme = p->scheme;
+    c->block = block;
+    c->spt = spt;
+    c->graph_steps = p->graph_steps == 0 ? 16 : p->graph_steps;
+    c->alloc = p->alloc;
+    c->free_fn = p->free;
+    c->alloc_user = p->alloc_user;
+    if (cudaSetDevice(p->device) != cudaSuccess) {
+        cudaGetLastError();
+        return HG_ERR_CUDA;
+    }
+    if (p->stream) {
+        c->stream = (cudaStream_t)p->stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess)
+            return HG_ERR_CUDA;
+        c->own_stream = true;
+    }
+    c->capacity = 4096;
+    int rc = dev_alloc(c.get(), c->dom_table, sizeof(DomDev) * c->capacity);
+    if (rc == HG_OK) rc = dev_alloc(c.get(), c->steps, sizeof(int64_t) * c->capacity);
+    if (rc != HG_OK) {
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        return rc;
+    }
+    if (cudaMemsetAsync(c->steps.p, 0, c->steps.bytes, c->stream) != cudaSuccess) return HG_ERR_CUDA;
+    c->doms.assign(c->capacity, nullptr);
+    *out = c.release();
+    return HG_OK;
+}
+
+int hg_domain_destroy(hg_domain *d);
+
+int hg_ctx_destroy(hg_ctx *ctx) {
+    if (!ctx) return HG_ERR_ARG;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    for (auto *d : ctx->doms)
+        if (d) hg_domain_destroy(d);
+    drop_plans(ctx);
+    dev_free(ctx, ctx->scratch);
+    dev_free(ctx, ctx->dom_table);
+    dev_free(ctx, ctx->steps);
+    if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return HG_OK;
+}
+
+const char *hg_last_error(hg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+int hg_sync(hg_ctx *ctx) {
+    if (!ctx) return HG_ERR_ARG;
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *iolets,
+                     int32_t nio, const hg_lb_params *lb, hg_domain **out) {
+    if (!ctx) return HG_ERR_ARG;
+    if (!out) return fail(ctx, HG_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    if (n < 0 || (n > 0 && !xyz)) return fail(ctx, HG_ERR_ARG, "bad site array");
+    if (n >= ((int64_t)1 << 31)) return fail(ctx, HG_ERR_ARG, "too many sites (%lld)", (long long)n);
+    if (nio < 0 || nio > kMaxIolets || (nio > 0 && !iolets))
+        return fail(ctx, HG_ERR_ARG, "n_iolets must be in [0, %d]", kMaxIolets);
+    const double tau = lb ? lb->tau : 0.8;
+    if (!(tau > 0.5)) return fail(ctx, HG_ERR_ARG, "tau must exceed 1/2");
+    if (lb && lb->ordering != HG_ORDER_MORTON) return fail(ctx, HG_ERR_ARG, "unknown ordering");
+    for (int k = 0; k < nio; ++k)
+        if (!iolet_ok(iolets[k])) return fail(ctx, HG_ERR_ARG, "iolet %d out of range", k);
+    int slot_idx = -1;
+    for (int i = 0; i < ctx->capacity; ++i)
+        if (!ctx->doms[i]) {
+            slot_idx = i;
+            break;
+        }
+    if (slot_idx < 0) return fail(ctx, HG_ERR_STATE, "context holds too many domains");
+    CU(ctx, cudaSetDevice(ctx->device));
+
+    std::unique_ptr<hg_domain> d(new hg_domain);
+    d->ctx = ctx;
+    d->n = n;
+    d->np = std::max<int64_t>(128, (n + 127) / 128 * 128);
+    d->nio = nio;
+    d->tau = tau;
+    d->io.assign(iolets, iolets + nio);
+
+    // --- canonical order
+    std::vector<uint64_t> key(n);
+    std::vector<int64_t> idx(n);
+    std::atomic<int> bad{0};
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s) {
+            const int32_t x = xyz[3 * s], y = xyz[3 * s + 1], z = xyz[3 * s + 2];
+            if (x < 0 || y < 0 || z < 0 || x >= (1 << 21) || y >= (1 << 21) || z >= (1 << 21)) bad = 1;
+            key[s] = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+            idx[s] = s;
+        }
+    });
+    if (bad) return fail(ctx, HG_ERR_ARG, "site coordinate outside [0, 2^21)");
+    sort_keys(key, idx);
+    for (int64_t s = 1; s < n; ++s)
+        if (key[s] == key[s - 1]) return fail(ctx, HG_ERR_ARG, "duplicate site at canonical index %lld", (long long)s);
+    d->xyz.resize(3 * n);
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s)
+            for (int c = 0; c < 3; ++c) d->xyz[3 * s + c] = xyz[3 * idx[s] + c];
+    });
+    std::vector<int64_t>().swap(idx);
+
+    // --- neighbour table (canonical codes)
+    BlockIndex bi;
+    bi.build(key);
+    std::vector<IoletGeom> geo(nio);
+    for (int k = 0; k < nio; ++k) {
+        geo[k].d = iolets[k];
+        geo[k].cx = iolets[k].centre[0] / 1024.0;
+        geo[k].cy = iolets[k].centre[1] / 1024.0;
+        geo[k].cz = iolets[k].centre[2] / 1024.0;
+        const double r = iolets[k].radius / 1024.0 + 3.0;
+        geo[k].reach2 = r * r + 1.0;
+    }
+    const int64_t np = d->np;
+    std::vector<int32_t> nbr((size_t)18 * np, -1);
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s) {
+            const int64_t x = d->xyz[3 * s], y = d->xyz[3 * s + 1], z = d->xyz[3 * s + 2];
+            for (int i = 1; i < 19; ++i) {
+                const int64_t qx = x - kC[i][0], qy = y - kC[i][1], qz = z - kC[i][2];
+                int64_t v = -1;
+                if (qx >= 0 && qy >= 0 && qz >= 0 && qx < (1 << 21) && qy < (1 << 21) && qz < (1 << 21))
+                    v = bi.find(morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz));
+                nbr[(size_t)(i - 1) * np + s] = v >= 0 ? (int32_t)v : classify(geo, qx, qy, qz);
+            }
+        }
+    });
+    std::vector<uint64_t>().swap(key);
+
+    // --- iolet adjacency: slots in canonical order, per-iolet CSR lists
+    std::vector<int32_t> slot_of(n, -1);
+    int64_t n_adj = 0;
+    std::vector<int64_t> per_io(nio + 1, 0);
+    for (int64_t s = 0; s < n; ++s) {
+        bool adj = false;
+        uint8_t seen[kMaxIolets / 8] = {0};
+        for (int i = 0; i < 18; ++i) {
+            const int32_t v = nbr[(size_t)i * np + s];
+            if (v < -1) {
+                adj = true;
+                const int k = -v - 2;
+                if (!(seen[k >> 3] & (1 << (k & 7)))) {
+                    seen[k >> 3] |= 1 << (k & 7);
+                    per_io[k + 1]++;
+                }
+            }
+        }
+        if (adj) slot_of[s] = (int32_t)n_adj++;
+    }
+    if (n_adj >= (1 << 22)) return fail(ctx, HG_ERR_ARG, "too many sites next to iolets");
+    d->n_adj = n_adj;
+    for (int k = 0; k < nio; ++k) per_io[k + 1] += per_io[k];
+    d->io_ptr.assign(per_io.begin(), per_io.end());
+    std::vector<int32_t> slots(std::max<int64_t>(1, per_io[nio]));
+    std::vector<float> coef((size_t)std::max<int64_t>(1, n_adj) * 18, 0.0f);
+    std::vector<uint32_t> mask((size_t)(np / 32), 0u);
+    {
+        std::vector<int64_t> fill(per_io.begin(), per_io.end() - 1);
+        for (int64_t s = 0; s < n; ++s) {
+            const int32_t sl = slot_of[s];
+            if (sl < 0) continue;
+            mask[s >> 5] |= 1u << (s & 31);
+            uint8_t seen[kMaxIolets / 8] = {0};
+            for (int i = 1; i < 19; ++i) {
+                int32_t &v = nbr[(size_t)(i - 1) * np + s];
+                if (v >= -1) continue;
+                const int k = -v - 2;
+                if (!(seen[k >> 3] & (1 << (k & 7)))) {
+                    seen[k >> 3] |= 1 << (k & 7);
+                    slots[fill[k]++] = sl;
+                }
+                const hg_iolet &io = iolets[k];
+                if (io.kind == HG_VELOCITY) {
+                    const double an = std::sqrt((double)io.axis[0] * io.axis[0] +
+                                                (double)io.axis[1] * io.axis[1] +
+                                                (double)io.axis[2] * io.axis[2]);
+                    const double ah[3] = {io.axis[0] / an, io.axis[1] / an, io.axis[2] / an};
+                    double phi = 1.0;
+                    if (io.profile == HG_PARABOLIC) {
+                        double rel[3], along = 0.0;
+                        for (int c = 0; c < 3; ++c) {
+                            rel[c] = (d->xyz[3 * s + c] - 0.5 * kC[i][c]) - io.centre[c] / 1024.0;
+                            along += rel[c] * ah[c];
+                        }
+                        double p2 = 0.0;
+                        for (int c = 0; c < 3; ++c) {
+                            const double q = rel[c] - along * ah[c];
+                            p2 += q * q;
+                        }
+                        const double r = io.radius / 1024.0;
+                        phi = r > 0 ? std::max(0.0, 1.0 - p2 / (r * r)) : 0.0;
+                    }
+                    const double cdot = -(kC[i][0] * ah[0] + kC[i][1] * ah[1] + kC[i][2] * ah[2]);
+                    coef[(size_t)sl * 18 + (i - 1)] = (float)(6.0 * wgt(i) * cdot * phi);
+                }
+                v = -(2 + k + 256 * sl);  // device code carries the slot
+            }
+        }
+    }
+
+    // --- device buffers
+    hg_ctx *c = ctx;
+    const size_t eb = elem_bytes(ctx->storage);
+    int rc = HG_OK;
+    d->idx = slot_idx;
+    auto A = [&](DevBuf &b, size_t bytes) {
+        if (rc == HG_OK) rc = dev_alloc(c, b, bytes);
+    };
+    A(d->f[0], 19 * (size_t)np * eb);
+    if (ctx->scheme == HG_SCHEME_AB) A(d->f[1], 19 * (size_t)np * eb);
+    A(d->nbr, 18 * (size_t)np * 4);
+    A(d->iomask, (size_t)np / 8);
+    A(d->bnd, (size_t)std::max<int64_t>(1, n_adj) * 16);
+    A(d->coef, coef.size() * 4);
+    A(d->bcv, (size_t)std::max(1, nio) * 4);
+    A(d->io_kind, (size_t)std::max(1, nio));
+    A(d->M, (size_t)std::max(1, nio) * 24);
+    A(d->slots, slots.size() * 4);
+    auto cleanup = [&] {
+        DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->bnd, &d->coef,
+                        &d->bcv, &d->io_kind, &d->M, &d->slots};
+        for (DevBuf *b : bs) dev_free(c, *b);
+    };
+    if (rc != HG_OK) {
+        cleanup();
+        return rc;
+    }
+    for (DevBuf *b : {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->bnd, &d->coef, &d->bcv,
+                      &d->io_kind, &d->M, &d->slots})
+        d->bytes += (int64_t)b->bytes;
+    std::vector<float> bcv(std::max(1, nio), 0.0f);
+    std::vector<int8_t> kinds(std::max(1, nio), 0);
+    for (int k = 0; k < nio; ++k) {
+        bcv[k] = (float)(iolets[k].value * pulse(iolets[k].pulse, 1.0, iolets[k].period));
+        kinds[k] = (int8_t)iolets[k].kind;
+    }
+    cudaError_t e = cudaSuccess;
+    auto H2D = [&](DevBuf &b, const void *src, size_t bytes) {
+        if (e == cudaSuccess) e = cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
+    };
+    H2D(d->nbr, nbr.data(), nbr.size() * 4);
+    H2D(d->iomask, mask.data(), mask.size() * 4);
+    H2D(d->coef, coef.data(), coef.size() * 4);
+    H2D(d->bcv, bcv.data(), bcv.size() * 4);
+    H2D(d->io_kind, kinds.data(), kinds.size());
+    H2D(d->slots, slots.data(), slots.size() * 4);
+    if (e == cudaSuccess) e = cudaMemset(d->f[0].p, 0, d->f[0].bytes);
+    if (e == cudaSuccess && d->f[1].p) e = cudaMemset(d->f[1].p, 0, d->f[1].bytes);
+    if (e == cudaSuccess) e = cudaMemset(d->bnd.p, 0, d->bnd.bytes);
+    if (e == cudaSuccess) e = cudaMemset(d->M.p, 0, d->M.bytes);
+    if (e == cudaSuccess) e = cudaMemset((int64_t *)ctx->steps.p + slot_idx, 0, sizeof(int64_t));
+    DomDev D = make_domdev(ctx, d.get());
+    if (e == cudaSuccess)
+        e = cudaMemcpy((DomDev *)ctx->dom_table.p + slot_idx, &D, sizeof D, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cleanup();
+        return fail(ctx, HG_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
+    }
+    ctx->doms[slot_idx] = d.get();
+    *out = d.release();
+    return HG_OK;
+}
+
+int hg_domain_destroy(hg_domain *d) {
+    if (!d) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    drop_plans(ctx);
+    for (auto it = ctx->coupled.begin(); it != ctx->coupled.end();) {
+        if (it->first.first == d->idx || it->second.src_dom == d->idx) it = ctx->coupled.erase(it);
+        else ++it;
+    }
+    DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->bnd, &d->coef,
+                    &d->bcv, &d->io_kind, &d->M, &d->slots};
+    for (DevBuf *b : bs) dev_free(ctx, *b);
+    ctx->doms[d->idx] = nullptr;
+    delete d;
+    return HG_OK;
+}
+
+int hg_domain_info(hg_domain *d, int64_t *n_sites, int32_t *n_iolets, int64_t *n_adjacent,
+                   int64_t *step, int64_t *device_bytes) {
+    if (!d) return HG_ERR_ARG;
+    if (n_sites) *n_sites = d->n;
+    if (n_iolets) *n_iolets = d->nio;
+    if (n_adjacent) *n_adjacent = d->n_adj;
+    if (step) *step = d->step;
+    if (device_bytes) *device_bytes = d->bytes;
+    return HG_OK;
+}
+
+int hg_domain_sites(hg_domain *d, int32_t *xyz_out) {
+    if (!d || (!xyz_out && d->n)) return HG_ERR_ARG;
+    if (d->n) memcpy(xyz_out, d->xyz.data(), sizeof(int32_t) * 3 * d->n);
+    return HG_OK;
+}
+
+int hg_domain_neighbours(hg_domain *d, int32_t *nbr_out) {
+    if (!d || (!nbr_out && d->n)) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int i = 0; i < 18; ++i)
+        CU(ctx, cudaMemcpy(nbr_out + (size_t)i * d->n, (const int32_t *)d->nbr.p + (size_t)i * d->np,
+                           sizeof(int32_t) * d->n, cudaMemcpyDeviceToHost));
+    for (int64_t j = 0; j < 18 * d->n; ++j) {
+        const int32_t v = nbr_out[j];
+        if (v < -1) nbr_out[j] = -(2 + ((-v - 2) & (kMaxIolets - 1)));
+    }
+    return HG_OK;
+}
+
+int hg_couple(hg_ctx *ctx, hg_domain *src, hg_domain *dst, const hg_pair *pairs, int32_t n) {
+    if (!ctx) return HG_ERR_ARG;
+    if (!src || !dst || src->ctx != ctx || dst->ctx != ctx || src == dst)
+        return fail(ctx, HG_ERR_ARG, "coupling needs two distinct domains of this context");
+    if (n < 0 || (n > 0 && !pairs)) return fail(ctx, HG_ERR_ARG, "bad pair array");
+    for (int j = 0; j < n; ++j) {
+        const hg_pair &p = pairs[j];
+        if (p.src_iolet < 0 || p.src_iolet >= src->nio || p.dst_iolet < 0 || p.dst_iolet >= dst->nio)
+            return fail(ctx, HG_ERR_ARG, "pair %d: iolet index out of range", j);
+        if (dst->io[p.dst_iolet].kind != HG_VELOCITY)
+            return fail(ctx, HG_ERR_ARG, "pair %d: destination iolet is not a velocity iolet", j);
+        if (ctx->coupled.count({dst->idx, p.dst_iolet}))
+            return fail(ctx, HG_ERR_ARG, "pair %d: destination iolet already coupled", j);
+        for (int q = 0; q < j; ++q)
+            if (pairs[q].dst_iolet == p.dst_iolet)
+                return fail(ctx, HG_ERR_ARG, "pair %d: destination iolet repeated", j);
+        if (!std::isfinite(p.factor)) return fail(ctx, HG_ERR_ARG, "pair %d: factor not finite", j);
+    }
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    // the next step's value follows the source's current mean at once
+    std::vector<double> Ms((size_t)std::max(1, src->nio) * 3);
+    CU(ctx, cudaMemcpy(Ms.data(), src->M.p, Ms.size() * 8, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < n; ++j) {
+        const hg_pair &p = pairs[j];
+        ctx->coupled[{dst->idx, p.dst_iolet}] = {src->idx, p.src_iolet, p.factor};
+        const float v = (float)(p.factor * Ms[3 * p.src_iolet]);
+        CU(ctx, cudaMemcpy((float *)dst->bcv.p + p.dst_iolet, &v, 4, cudaMemcpyHostToDevice));
+    }
+    drop_plans(ctx);
+    return HG_OK;
+}
+
+int hg_coupling_factors(const int64_t *art_c, const double *art_a, int32_t na, const int64_t *ven_c,
+                        const double *ven_a, int32_t nv, const double *uni, int32_t *assign,
+                        double *dist, double *dp, double *factor) {
+    if (na < 1 || nv < 0 || !art_c || !art_a || (nv > 0 && (!ven_c || !ven_a || !uni || !assign ||
+                                                          !dist || !dp || !factor)))
+        return HG_ERR_ARG;
+    typedef __int128 i128;
+    auto d2 = [&](int a, int v) {
+        i128 s = 0;
+        for (int c = 0; c < 3; ++c) {
+            const i128 t = (i128)art_c[3 * a + c] - ven_c[3 * v + c];
+            s += t * t;
+        }
+        return s;
+    };
+    std::vector<char> taken(nv, 0);
+    for (int v = 0; v < nv; ++v) assign[v] = -1;
+    for (int a = 0; a < na; ++a) {
+        int best = -1;
+        i128 bd = 0;
+        for (int v = 0; v < nv; ++v) {
+            if (taken[v]) continue;
+            const i128 dd = d2(a, v);
+            if (best < 0 || dd < bd) {
+                best = v;
+                bd = dd;
+            }
+        }
+        if (best < 0) break;
+        taken[best] = 1;
+        assign[best] = a;
+    }
+    for (int v = 0; v < nv; ++v) {
+        if (taken[v]) continue;
+        int best = 0;
+        i128 bd = d2(0, v);
+        for (int a = 1; a < na; ++a) {
+            const i128 dd = d2(a, v);
+            if (dd < bd) {
+                best = a;
+                bd = dd;
+            }
+        }
+        assign[v] = best;
+    }
+    for (int v = 0; v < nv; ++v) {
+        dist[v] = std::sqrt((double)d2(assign[v], v)) / 1024.0;
+        dp[v] = 0.3 + 0.4 * uni[v];
+        if (!(dist[v] > 0) || !(ven_a[v] > 0)) return HG_ERR_ARG;
+    }
+    for (int a = 0; a < na; ++a) {
+        if (!(art_a[a] > 0)) return HG_ERR_ARG;
+        int first = -1;
+        for (int v = 0; v < nv; ++v)
+            if (assign[v] == a) {
+                first = v;
+                break;
+            }
+        if (first < 0) continue;
+        // ratio_i = dP_i L_1 A_i / (dP_1 L_i A_1); factor_i = (A_0 / A_i) ratio_i / sum ratio
+        double total = 0.0;
+        for (int v = 0; v < nv; ++v)
+            if (assign[v] == a)
+                total += dp[v] * dist[first] * ven_a[v] / (dp[first] * dist[v] * ven_a[first]);
+        for (int v = 0; v < nv; ++v)
+            if (assign[v] == a) {
+                const double r = dp[v] * dist[first] * ven_a[v] / (dp[first] * dist[v] * ven_a[first]);
+                factor[v] = (art_a[a] / ven_a[v]) * r / total;
+            }
+    }
+    return HG_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ stepping
+namespace {
+
+int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
+    PlanKey key{doms};
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        out = it->second.get();
+        return HG_OK;
+    }
+    std::unique_ptr<Plan> p(new Plan);
+    p->doms = doms;
+    const int64_t ts = (int64_t)ctx->block * ctx->spt;
+    std::vector<TileDev> tiles;
+    std::vector<IoDev> ios;
+    for (int32_t di : doms) {
+        hg_domain *d = ctx->doms[di];
+        for (int64_t s = 0; s < d->n; s += ts) {
+            TileDev t;
+            t.dom = di;
+            t.count = (int32_t)std::min(ts, d->n - s);
+            t.start = s;
+            tiles.push_back(t);
+        }
+        for (int k = 0; k < d->nio; ++k) {
+            IoDev I;
+            memset(&I, 0, sizeof I);
+            const hg_iolet &io = d->io[k];
+            I.slots = (const int32_t *)d->slots.p + d->io_ptr[k];
+            I.n_slots = (int32_t)(d->io_ptr[k + 1] - d->io_ptr[k]);
+            I.bnd = (const float4 *)d->bnd.p;
+            I.M = (double *)d->M.p + 3 * k;
+            I.bcv = (float *)d->bcv.p + k;
+            I.step = (const int64_t *)ctx->steps.p + di;
+            const double an = std::sqrt((double)io.axis[0] * io.axis[0] + (double)io.axis[1] * io.axis[1] +
+                                        (double)io.axis[2] * io.axis[2]);
+            I.nx = io.axis[0] / an;
+            I.ny = io.axis[1] / an;
+            I.nz = io.axis[2] / an;
+            I.value = io.value;
+            I.period = io.period;
+            I.pulse = io.pulse;
+            auto cp = ctx->coupled.find({di, k});
+            if (cp != ctx->coupled.end()) {
+                hg_domain *sd = ctx->doms[cp->second.src_dom];
+                if (std::find(doms.begin(), doms.end(), cp->second.src_dom) == doms.end())
+                    return fail(ctx, HG_ERR_ARG, "a coupled source domain is not being stepped");
+                const int sk = cp->second.src_k;
+                const hg_iolet &so = sd->io[sk];
+                const double sn = std::sqrt((double)so.axis[0] * so.axis[0] + (double)so.axis[1] * so.axis[1] +
+                                            (double)so.axis[2] * so.axis[2]);
+                I.coupled = 1;
+                I.factor = cp->second.factor;
+                I.src_slots = (const int32_t *)sd->slots.p + sd->io_ptr[sk];
+                I.src_n_slots = (int32_t)(sd->io_ptr[sk + 1] - sd->io_ptr[sk]);
+                I.src_bnd = (const float4 *)sd->bnd.p;
+                I.src_nx = so.axis[0] / sn;
+                I.src_ny = so.axis[1] / sn;
+                I.src_nz = so.axis[2] / sn;
+            }
+            ios.push_back(I);
+        }
+    }
+    p->n_tiles = (int64_t)tiles.size();
+    p->n_ios = (int)ios.size();
+    int rc = dev_alloc(ctx, p->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TileDev));
+    if (rc == HG_OK) rc = dev_alloc(ctx, p->ios, std::max<size_t>(1, ios.size()) * sizeof(IoDev));
+    if (rc == HG_OK) rc = dev_alloc(ctx, p->adv, std::max<size_t>(1, doms.size()) * 4);
+    if (rc != HG_OK) {
+        dev_free(ctx, p->tiles);
+        dev_free(ctx, p->ios);
+        dev_free(ctx, p->adv);
+        return rc;
+    }
+    cudaError_t e = cudaSuccess;
+    if (!tiles.empty()) e = cudaMemcpy(p->tiles.p, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !ios.empty()) e = cudaMemcpy(p->ios.p, ios.data(), ios.size() * sizeof(IoDev), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(p->adv.p, doms.data(), doms.size() * 4, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) return fail(ctx, HG_ERR_CUDA, "plan upload failed: %s", cudaGetErrorString(e));
+    out = p.get();
+    ctx->plans[key] = std::move(p);
+    return HG_OK;
+}
+
+cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k) {
+    CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt};
+    for (int64_t off = 0; off < k; ++off) {
+        cudaError_t e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p,
+                                              (const TileDev *)p->tiles.p, p->n_tiles, (int)off, ctx->stream);
+        if (e != cudaSuccess) return e;
+        e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (int)off, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return launch_advance_list((int64_t *)ctx->steps.p, (const int32_t *)p->adv.p, (int)p->doms.size(), k,
+                               ctx->stream);
+}
+
+int ensure_graph(hg_ctx *ctx, Plan *p) {
+    if (p->graph || ctx->graph_steps <= 0) return HG_OK;
+    cudaGraph_t g = nullptr;
+    CU(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
+    cudaError_t e = enqueue_steps(ctx, p, ctx->graph_steps);
+    cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        return fail(ctx, HG_ERR_CUDA, "graph capture failed: %s",
+                    cudaGetErrorString(e != cudaSuccess ? e : e2));
+    }
+    e = cudaGraphInstantiate(&p->graph, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) {
+        p->graph = nullptr;
+        return fail(ctx, HG_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+    }
+    p->graph_steps = ctx->graph_steps;
+    return HG_OK;
+}
+
+int step_set(hg_ctx *ctx, std::vector<int32_t> doms, int64_t n) {
+    if (n < 0) return fail(ctx, HG_ERR_ARG, "negative step count");
+    std::sort(doms.begin(), doms.end());
+    doms.erase(std::unique(doms.begin(), doms.end()), doms.end());
+    if (doms.empty() || n == 0) return HG_OK;
+    CU(ctx, cudaSetDevice(ctx->device));
+    Plan *p = nullptr;
+    int rc = build_plan(ctx, doms, p);
+    if (rc != HG_OK) return rc;
+    int64_t left = n;
+    if (ctx->graph_steps > 0 && n >= ctx->graph_steps) {
+        rc = ensure_graph(ctx, p);
+        if (rc != HG_OK) return rc;
+        while (left >= p->graph_steps) {
+            CU(ctx, cudaGraphLaunch(p->graph, ctx->stream));
+            left -= p->graph_steps;
+        }
+    }
+    if (left > 0) CU(ctx, enqueue_steps(ctx, p, left));
+    for (int32_t di : doms) ctx->doms[di]->step += n;
+    return HG_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int hg_step(hg_ctx *ctx, int64_t n) {
+    if (!ctx) return HG_ERR_ARG;
+    std::vector<int32_t> doms;
+    for (int i = 0; i < ctx->capacity; ++i)
+        if (ctx->doms[i]) doms.push_back(i);
+    return step_set(ctx, doms, n);
+}
+
+int hg_step_domains(hg_ctx *ctx, hg_domain *const *ds, int32_t nd, int64_t n) {
+    if (!ctx) return HG_ERR_ARG;
+    if (nd < 0 || (nd > 0 && !ds)) return fail(ctx, HG_ERR_ARG, "bad domain list");
+    std::vector<int32_t> doms;
+    for (int j = 0; j < nd; ++j) {
+        if (!ds[j] || ds[j]->ctx != ctx) return fail(ctx, HG_ERR_ARG, "domain %d not in this context", j);
+        doms.push_back(ds[j]->idx);
+    }
+    return step_set(ctx, doms, n);
+}
+
+int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io) {
+    if (!ctx) return HG_ERR_ARG;
+    if (n < 0) return fail(ctx, HG_ERR_ARG, "negative step count");
+    std::vector<int32_t> doms;
+    for (int i = 0; i < ctx->capacity; ++i)
+        if (ctx->doms[i]) doms.push_back(i);
+    if (ms_sc) *ms_sc = 0.0;
+    if (ms_io) *ms_io = 0.0;
+    if (doms.empty() || n == 0) return HG_OK;
+    CU(ctx, cudaSetDevice(ctx->device));
+    Plan *p = nullptr;
+    int rc = build_plan(ctx, doms, p);
+    if (rc != HG_OK) return rc;
+    std::vector<cudaEvent_t> ev((size_t)3 * n);
+    for (auto &x : ev) CU(ctx, cudaEventCreate(&x));
+    CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt};
+    cudaError_t e = cudaSuccess;
+    for (int64_t j = 0; j < n && e == cudaSuccess; ++j) {
+        cudaEventRecord(ev[3 * j], ctx->stream);
+        e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
+                                  p->n_tiles, (int)j, ctx->stream);
+        cudaEventRecord(ev[3 * j + 1], ctx->stream);
+        if (e == cudaSuccess) e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (int)j, ctx->stream);
+        cudaEventRecord(ev[3 * j + 2], ctx->stream);
+    }
+    if (e == cudaSuccess)
+        e = launch_advance_list((int64_t *)ctx->steps.p, (const int32_t *)p->adv.p, (int)doms.size(), n,
+                                ctx->stream);
+    cudaError_t es = cudaStreamSynchronize(ctx->stream);
+    double a = 0.0, b = 0.0;
+    for (int64_t j = 0; j < n && e == cudaSuccess && es == cudaSuccess; ++j) {
+        float x = 0.f, y = 0.f;
+        cudaEventElapsedTime(&x, ev[3 * j], ev[3 * j + 1]);
+        cudaEventElapsedTime(&y, ev[3 * j + 1], ev[3 * j + 2]);
+        a += x;
+        b += y;
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    if (e != cudaSuccess) return fail(ctx, HG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(e));
+    if (es != cudaSuccess) return fail(ctx, HG_ERR_CUDA, "step failed: %s", cudaGetErrorString(es));
+    for (int32_t di : doms) ctx->doms[di]->step += n;
+    if (ms_sc) *ms_sc = a;
+    if (ms_io) *ms_io = b;
+    return HG_OK;
+}
+
+int hg_read_macroscopic_device(hg_domain *d, float *dev_out) {
+    if (!d || (!dev_out && d->n)) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    if (((uintptr_t)dev_out) & 15) return fail(ctx, HG_ERR_ARG, "output must be 16-byte aligned");
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, launch_macroscopic(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, nullptr,
+                               (float4 *)dev_out, ctx->stream));
+    return HG_OK;
+}
+
+int hg_read_macroscopic(hg_domain *d, float *out, int64_t *step_out) {
+    if (!d || (!out && d->n)) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    int rc = ensure_scratch(ctx, (size_t)std::max<int64_t>(1, d->n) * 16);
+    if (rc != HG_OK) return rc;
+    rc = hg_read_macroscopic_device(d, (float *)ctx->scratch.p);
+    if (rc != HG_OK) return rc;
+    if (d->n) CU(ctx, cudaMemcpyAsync(out, ctx->scratch.p, (size_t)d->n * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (step_out) *step_out = d->step;
+    return HG_OK;
+}
+
+int hg_read_iolet_stats(hg_domain *d, double *out) {
+    if (!d || (!out && d->nio)) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (d->nio) CU(ctx, cudaMemcpyAsync(out, d->M.p, (size_t)d->nio * 24, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+int hg_read_boundary_values(hg_domain *d, float *out) {
+    if (!d || (!out && d->nio)) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (d->nio) CU(ctx, cudaMemcpyAsync(out, d->bcv.p, (size_t)d->nio * 4, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+int hg_mass(hg_domain *d, double *out) {
+    if (!d || !out) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    const int64_t P = mass_partials_needed(d->n);
+    int rc = ensure_scratch(ctx, (size_t)(P + 1) * 8);
+    if (rc != HG_OK) return rc;
+    double *part = (double *)ctx->scratch.p;
+    CU(ctx, launch_mass(ctx->storage, domdev_ptr(d), d->n, d->np, part, part + P, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(out, part + P, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+// checkpoint layout: header | bcv[nio] f32 | M[nio*3] f64 | F[19][n] storage
+struct StateHeader {
+    char magic[8];
+    int64_t n, step;
+    int32_t nio, storage, scheme, version;
+};
+
+int hg_state_bytes(hg_domain *d, int64_t *bytes) {
+    if (!d || !bytes) return HG_ERR_ARG;
+    *bytes = (int64_t)sizeof(StateHeader) + (int64_t)d->nio * 4 + (int64_t)d->nio * 24 +
+             19 * d->n * (int64_t)elem_bytes(d->ctx->storage);
+    return HG_OK;
+}
+
+int hg_read_state(hg_domain *d, void *host_out) {
+    if (!d || (!host_out && d->n)) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    const size_t fb = 19 * (size_t)d->n * elem_bytes(ctx->storage);
+    int rc = ensure_scratch(ctx, std::max<size_t>(fb, 16));
+    if (rc != HG_OK) return rc;
+    CU(ctx, launch_export_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, nullptr, ctx->scratch.p,
+                                ctx->stream));
+    if (fb) CU(ctx, cudaMemcpyAsync(host_out, ctx->scratch.p, fb, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+int hg_save_state(hg_domain *d, void *buf, int64_t bytes) {
+    if (!d || !buf) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    int64_t need = 0;
+    hg_state_bytes(d, &need);
+    if (bytes < need) return fail(ctx, HG_ERR_ARG, "buffer too small (%lld < %lld)", (long long)bytes, (long long)need);
+    StateHeader h;
+    memset(&h, 0, sizeof h);
+    memcpy(h.magic, "HEMEGB1", 8);
+    h.n = d->n;
+    h.step = d->step;
+    h.nio = d->nio;
+    h.storage = ctx->storage;
+    h.scheme = ctx->scheme;
+    h.version = 1;
+    char *p = (char *)buf;
+    memcpy(p, &h, sizeof h);
+    p += sizeof h;
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (d->nio) {
+        CU(ctx, cudaMemcpy(p, d->bcv.p, (size_t)d->nio * 4, cudaMemcpyDeviceToHost));
+        p += (size_t)d->nio * 4;
+        CU(ctx, cudaMemcpy(p, d->M.p, (size_t)d->nio * 24, cudaMemcpyDeviceToHost));
+        p += (size_t)d->nio * 24;
+    }
+    return hg_read_state(d, p);
+}
+
+int hg_load_state(hg_domain *d, const void *buf, int64_t bytes) {
+    if (!d || !buf) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    int64_t need = 0;
+    hg_state_bytes(d, &need);
+    if (bytes < need) return fail(ctx, HG_ERR_ARG, "buffer too small");
+    StateHeader h;
+    memcpy(&h, buf, sizeof h);
+    if (memcmp(h.magic, "HEMEGB1", 8) != 0 || h.version != 1)
+        return fail(ctx, HG_ERR_ARG, "not a hemegb state");
+    if (h.n != d->n || h.nio != d->nio || h.storage != ctx->storage || h.scheme != ctx->scheme)
+        return fail(ctx, HG_ERR_ARG, "state does not match this domain (sites, iolets, storage or scheme)");
+    if (h.step < 0) return fail(ctx, HG_ERR_ARG, "negative step");
+    const char *p = (const char *)buf + sizeof h;
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (d->nio) {
+        CU(ctx, cudaMemcpy(d->bcv.p, p, (size_t)d->nio * 4, cudaMemcpyHostToDevice));
+        p += (size_t)d->nio * 4;
+        CU(ctx, cudaMemcpy(d->M.p, p, (size_t)d->nio * 24, cudaMemcpyHostToDevice));
+        p += (size_t)d->nio * 24;
+    }
+    CU(ctx, cudaMemcpy((int64_t *)ctx->steps.p + d->idx, &h.step, 8, cudaMemcpyHostToDevice));
+    d->step = h.step;
+    const size_t fb = 19 * (size_t)d->n * elem_bytes(ctx->storage);
+    int rc = ensure_scratch(ctx, std::max<size_t>(fb, 16));
+    if (rc != HG_OK) return rc;
+    if (fb) CU(ctx, cudaMemcpy(ctx->scratch.p, p, fb, cudaMemcpyHostToDevice));
+    CU(ctx, launch_import_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, nullptr, ctx->scratch.p,
+                                ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+}  // extern "C"

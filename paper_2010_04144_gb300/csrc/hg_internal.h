@@ -1,0 +1,89 @@
+// hg_internal.h -- device-side tables shared by the host runtime (hg_host.cpp)
+// and the kernels (hg_kernels.cu).  Not part of the public ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hg {
+
+// Device encoding of a non-fluid link in the neighbour table:
+//   -1                      wall
+//   -(2 + k + 256 * slot)   opening of iolet k (k < 256); `slot` is the
+//                           site's index in the domain's list of sites next
+//                           to any iolet (canonical order).
+// Fluid links hold the device index of the pull source.
+constexpr int kMaxIolets = 256;
+
+enum Storage : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
+enum Scheme : int { kAB = 0, kAA = 1 };
+
+// Per-domain descriptor read by the stream-collide and read-back kernels.
+struct DomDev {
+    void *f[2];               // distributions, SoA [19][np]; AA uses f[0] only
+    const int32_t *nbr;       // [18][np] device codes
+    const uint32_t *iomask;   // bit s: site s has an iolet link
+    float4 *bnd;              // per adjacent slot: (drho, ux, uy, uz) of the step's G_t
+    const float *coef;        // per adjacent slot x 18: velocity-link coefficient 6 w_i c_i.(-a) phi
+    const float *bcv;         // per iolet: boundary value of the step being run
+    const int8_t *io_kind;    // per iolet: 0 pressure, 1 velocity
+    const int64_t *step;      // completed steps before the current launch group
+    int64_t n;                // sites
+    int64_t np;               // row stride (n padded)
+    float omega;              // 1 / tau
+    int32_t n_io;
+};
+
+// One block of the stream-collide grid: `count` sites of domain `dom` from `start`.
+struct TileDev {
+    int32_t dom;
+    int32_t count;
+    int64_t start;
+};
+
+// Per-iolet work of the iolet-update kernel (reduction + next boundary value).
+struct IoDev {
+    const int32_t *slots;     // adjacent-site slots of this iolet, canonical order
+    const float4 *bnd;        // owner's per-slot moments
+    const int32_t *src_slots; // coupled source: its slots (or null)
+    const float4 *src_bnd;
+    double *M;                // out: (mean u.n, mean drho, count)
+    float *bcv;               // out: boundary value for the next step
+    const int64_t *step;      // owner's completed-step counter
+    double nx, ny, nz;        // unit outward axis
+    double src_nx, src_ny, src_nz;
+    double value, period, factor;
+    int32_t n_slots, src_n_slots;
+    int32_t pulse;
+    int32_t coupled;
+};
+
+// Launch configuration of the stream-collide kernel.
+struct CollideCfg {
+    int storage;
+    int scheme;
+    int block;
+    int spt;
+};
+
+cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
+                                  int64_t n_tiles, int off, cudaStream_t st);
+cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, int off, cudaStream_t st);
+cudaError_t launch_advance_list(int64_t *steps_base, const int32_t *idx, int n, int64_t by,
+                                cudaStream_t st);
+// Reconstruct F_t of one domain (device order) and write macroscopic fields
+// (drho, ux, uy, uz) to out[perm ? perm[s] : s].
+cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, int64_t n,
+                               const int64_t *canon_of, float4 *out, cudaStream_t st);
+// Raw state export/import of F_t in canonical order (storage type, [19][n]).
+cudaError_t launch_export_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
+                                const int64_t *canon_of, void *out, cudaStream_t st);
+cudaError_t launch_import_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
+                                const int64_t *canon_of, const void *in, cudaStream_t st);
+// Mass: FP64 partial sums over fixed chunks of the stored values, then a
+// fixed-order final sum.  partials needs mass_partials_needed(n) doubles.
+int64_t mass_partials_needed(int64_t n);
+cudaError_t launch_mass(int storage, const DomDev *dom_dev, int64_t n, int64_t np,
+                        double *partials, double *out, cudaStream_t st);
+
+}  // namespace hg

@@ -19,3 +19,22 @@ def oracle_mod():
 
     oracle.lib()  # builds libhemeoracle.so on first use
     return oracle
+
+
+@pytest.fixture(scope="session")
+def hemegb_lib():
+    """The built extension (compiled here if missing or stale; nvcc cross-compiles without a GPU)."""
+    from paper_2010_04144_gb300 import build as B
+    from paper_2010_04144_gb300 import hemegb
+
+    B.build()
+    return hemegb
+
+
+@pytest.fixture(scope="session")
+def gpu(hemegb_lib):
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return hemegb_lib
