@@ -237,6 +237,26 @@ int hg_read_boundary_values(hg_domain *d, float *out);
 /* Total mass deviation sum_s sum_i f~_i(s) of the current state, FP64. */
 int hg_mass(hg_domain *d, double *out);
 
+/* Total mass deviation of a caller-owned distribution array, without any
+ * device allocation.  The paper has no counterpart: this exists for callers
+ * that may not allocate device memory -- an application whose own pool
+ * already owns the whole device heap, or a monitoring thread that must not
+ * call cudaMalloc/cudaFree because they can synchronise the device and stall
+ * the solver.  f_dev: 19 rows of row_stride values of the given storage type
+ * (HG_STORE_*; FP16/BF16 rows hold f~/w), sites 0..n-1 of each row are summed
+ * (FP64, fixed chunks of 8192 sites, same order as hg_mass); out_dev: one
+ * double in device memory; stream: cudaStream_t (NULL = legacy default).
+ * Scratch: a fixed 16384-double array inside the library, held on every GPU
+ * that loads it until the process exits, so n is limited to 134,217,728 sites
+ * (HG_ERR_ARG beyond).  The first call on a device looks up that array's
+ * device address (cudaGetSymbolAddress) with the device current; make that
+ * first call before any stream capture.  All calls share the array: calls
+ * whose kernels overlap on the GPU race and may return wrong sums; calls
+ * ordered on one stream are safe.  Asynchronous.  Errors: HG_ERR_ARG,
+ * HG_ERR_CUDA. */
+int hg_mass_noalloc(const void *f_dev, int32_t storage, int64_t n, int64_t row_stride,
+                    double *out_dev, void *stream);
+
 /* ---- checkpoint / resume ---- */
 
 /* Bytes needed by hg_save_state for this domain. */

@@ -84,6 +84,8 @@ _SIGS = {
     "hg_save_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
     "hg_load_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
     "hg_read_state": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_mass_noalloc": ([C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p],
+                        C.c_int),
 }
 
 
