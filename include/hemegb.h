@@ -88,6 +88,8 @@ typedef struct {
     int32_t block_size;       /* stream-collide threads per block (multiple of 32, <= 512); 0 = 256 */
     int32_t sites_per_thread; /* 1, 2 or 4; 0 = 1 */
     int32_t graph_steps;      /* steps captured per CUDA graph; 0 = 16; negative = no graphs */
+    int32_t kernel_variant;   /* 0 = gathers into registers; 1 = gathers staged in shared memory
+                                 by cp.async (sites_per_thread 1 or 2) */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */
@@ -212,9 +214,18 @@ int hg_step_domains(hg_ctx *ctx, hg_domain *const *doms, int32_t n_doms, int64_t
 
 /* Like hg_step but without graphs and with CUDA events around every kernel:
  * total milliseconds spent in the stream-collide kernel and in the iolet
- * update kernel (either pointer may be NULL).  Synchronises. */
+ * update kernel; per_step (2 x n_steps floats, may be NULL) receives each
+ * step's (stream-collide ms, iolet-update ms).  Any pointer may be NULL.
+ * Synchronises. */
 int hg_step_profiled(hg_ctx *ctx, int64_t n_steps, double *ms_stream_collide,
-                     double *ms_iolet);
+                     double *ms_iolet, float *per_step);
+
+/* Change the stream-collide launch shape of an existing context (threads per
+ * block: multiple of 32, <= 512; sites per thread: 1, 2 or 4; kernel variant
+ * as in hg_ctx_params).  Results do not depend on it (each site's arithmetic
+ * is the same); used by the autotuner.  Errors: HG_ERR_ARG. */
+int hg_ctx_set_launch(hg_ctx *ctx, int32_t block_size, int32_t sites_per_thread,
+                      int32_t kernel_variant);
 
 /* ---- read-back ---- */
 

@@ -253,7 +253,7 @@ struct Plan {
     DevBuf tiles, ios, adv;
     int64_t n_tiles = 0;
     int n_ios = 0;
-    cudaGraphExec_t graph = nullptr;
+    cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // by parity mode
     int graph_steps = 0;
 };
 
@@ -266,7 +266,7 @@ struct hg_ctx {
     int device = 0;
     cudaStream_t stream = nullptr;
     bool own_stream = false;
-    int storage = 0, scheme = 0, block = 256, spt = 1, graph_steps = 16;
+    int storage = 0, scheme = 0, block = 256, spt = 1, variant = 0, graph_steps = 16;
     hg_alloc_fn alloc = nullptr;
     hg_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
@@ -349,7 +349,8 @@ void dev_free(hg_ctx *ctx, DevBuf &b) {
 void drop_plans(hg_ctx *ctx) {
     for (auto &kv : ctx->plans) {
         Plan &p = *kv.second;
-        if (p.graph) cudaGraphExecDestroy(p.graph);
+        for (auto &g : p.graph)
+            if (g) cudaGraphExecDestroy(g);
         dev_free(ctx, p.tiles);
         dev_free(ctx, p.ios);
         dev_free(ctx, p.adv);
@@ -403,6 +404,8 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     int spt = p->sites_per_thread ? p->sites_per_thread : 1;
     if (block < 32 || block > 512 || block % 32) return HG_ERR_ARG;
     if (spt != 1 && spt != 2 && spt != 4) return HG_ERR_ARG;
+    if (p->kernel_variant < 0 || p->kernel_variant > 1 || (p->kernel_variant == 1 && spt == 4))
+        return HG_ERR_ARG;
     if ((p->alloc == nullptr) != (p->free == nullptr)) return HG_ERR_ARG;
     std::unique_ptr<hg_ctx> c(new hg_ctx);
     c->device = p->device;
@@ -410,6 +413,7 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     c->scheme = p->scheme;
     c->block = block;
     c->spt = spt;
+    c->variant = p->kernel_variant;
     c->graph_steps = p->graph_steps == 0 ? 16 : p->graph_steps;
     c->alloc = p->alloc;
     c->free_fn = p->free;
@@ -469,7 +473,8 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     if (!out) return fail(ctx, HG_ERR_ARG, "out is NULL");
     *out = nullptr;
     if (n < 0 || (n > 0 && !xyz)) return fail(ctx, HG_ERR_ARG, "bad site array");
-    if (n >= ((int64_t)1 << 31)) return fail(ctx, HG_ERR_ARG, "too many sites (%lld)", (long long)n);
+    if (n > ((int64_t)200 << 20))  // 32-bit row offsets in the AA kernels need 19 * np < 2^32
+        return fail(ctx, HG_ERR_ARG, "too many sites in one domain (%lld > 209715200)", (long long)n);
     if (nio < 0 || nio > kMaxIolets || (nio > 0 && !iolets))
         return fail(ctx, HG_ERR_ARG, "n_iolets must be in [0, %d]", kMaxIolets);
     const double tau = lb ? lb->tau : 0.8;
@@ -921,11 +926,30 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     return HG_OK;
 }
 
-cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k) {
-    CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt};
+// Parity mode of a domain set: 0 / 1 = every domain has completed an even / odd
+// number of steps (AA kernels specialised per step kind), 2 = mixed.
+int parity_mode(hg_ctx *ctx, const std::vector<int32_t> &doms) {
+    int m = -1;
+    for (int32_t di : doms) {
+        const int q = (int)(ctx->doms[di]->step & 1);
+        if (m < 0) m = q;
+        else if (m != q) return 2;
+    }
+    return m < 0 ? 0 : m;
+}
+
+// Kernel parity argument for the step at offset `off` of a group starting in `mode`.
+inline int step_parity(hg_ctx *ctx, int mode, int64_t off) {
+    if (ctx->scheme == HG_SCHEME_AB || mode == 2) return 2;
+    return (int)((mode + off + 1) & 1);  // 1 when the executed step is odd
+}
+
+cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
+    CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
     for (int64_t off = 0; off < k; ++off) {
         cudaError_t e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p,
-                                              (const TileDev *)p->tiles.p, p->n_tiles, (int)off, ctx->stream);
+                                              (const TileDev *)p->tiles.p, p->n_tiles, (int)off,
+                                              step_parity(ctx, mode, off), ctx->stream);
         if (e != cudaSuccess) return e;
         e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (int)off, ctx->stream);
         if (e != cudaSuccess) return e;
@@ -934,11 +958,11 @@ cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k) {
                                ctx->stream);
 }
 
-int ensure_graph(hg_ctx *ctx, Plan *p) {
-    if (p->graph || ctx->graph_steps <= 0) return HG_OK;
+int ensure_graph(hg_ctx *ctx, Plan *p, int mode) {
+    if (p->graph[mode] || ctx->graph_steps <= 0) return HG_OK;
     cudaGraph_t g = nullptr;
     CU(ctx, cudaStreamBeginCapture(ctx->stream, cudaStreamCaptureModeThreadLocal));
-    cudaError_t e = enqueue_steps(ctx, p, ctx->graph_steps);
+    cudaError_t e = enqueue_steps(ctx, p, ctx->graph_steps, mode);
     cudaError_t e2 = cudaStreamEndCapture(ctx->stream, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -946,10 +970,10 @@ int ensure_graph(hg_ctx *ctx, Plan *p) {
         return fail(ctx, HG_ERR_CUDA, "graph capture failed: %s",
                     cudaGetErrorString(e != cudaSuccess ? e : e2));
     }
-    e = cudaGraphInstantiate(&p->graph, g, 0);
+    e = cudaGraphInstantiate(&p->graph[mode], g, 0);
     cudaGraphDestroy(g);
     if (e != cudaSuccess) {
-        p->graph = nullptr;
+        p->graph[mode] = nullptr;
         return fail(ctx, HG_ERR_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
     }
     p->graph_steps = ctx->graph_steps;
@@ -966,15 +990,17 @@ int step_set(hg_ctx *ctx, std::vector<int32_t> doms, int64_t n) {
     int rc = build_plan(ctx, doms, p);
     if (rc != HG_OK) return rc;
     int64_t left = n;
+    int mode = parity_mode(ctx, doms);
     if (ctx->graph_steps > 0 && n >= ctx->graph_steps) {
-        rc = ensure_graph(ctx, p);
-        if (rc != HG_OK) return rc;
-        while (left >= p->graph_steps) {
-            CU(ctx, cudaGraphLaunch(p->graph, ctx->stream));
-            left -= p->graph_steps;
+        while (left >= ctx->graph_steps) {
+            rc = ensure_graph(ctx, p, mode);
+            if (rc != HG_OK) return rc;
+            CU(ctx, cudaGraphLaunch(p->graph[mode], ctx->stream));
+            left -= ctx->graph_steps;
+            if (mode != 2) mode = (int)((mode + ctx->graph_steps) & 1);
         }
     }
-    if (left > 0) CU(ctx, enqueue_steps(ctx, p, left));
+    if (left > 0) CU(ctx, enqueue_steps(ctx, p, left, mode));
     for (int32_t di : doms) ctx->doms[di]->step += n;
     return HG_OK;
 }
@@ -1002,7 +1028,7 @@ int hg_step_domains(hg_ctx *ctx, hg_domain *const *ds, int32_t nd, int64_t n) {
     return step_set(ctx, doms, n);
 }
 
-int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io) {
+int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float *per_step) {
     if (!ctx) return HG_ERR_ARG;
     if (n < 0) return fail(ctx, HG_ERR_ARG, "negative step count");
     std::vector<int32_t> doms;
@@ -1017,12 +1043,13 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io) {
     if (rc != HG_OK) return rc;
     std::vector<cudaEvent_t> ev((size_t)3 * n);
     for (auto &x : ev) CU(ctx, cudaEventCreate(&x));
-    CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt};
+    CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
+    const int mode = parity_mode(ctx, doms);
     cudaError_t e = cudaSuccess;
     for (int64_t j = 0; j < n && e == cudaSuccess; ++j) {
         cudaEventRecord(ev[3 * j], ctx->stream);
         e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
-                                  p->n_tiles, (int)j, ctx->stream);
+                                  p->n_tiles, (int)j, step_parity(ctx, mode, j), ctx->stream);
         cudaEventRecord(ev[3 * j + 1], ctx->stream);
         if (e == cudaSuccess) e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (int)j, ctx->stream);
         cudaEventRecord(ev[3 * j + 2], ctx->stream);
@@ -1038,6 +1065,10 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io) {
         cudaEventElapsedTime(&y, ev[3 * j + 1], ev[3 * j + 2]);
         a += x;
         b += y;
+        if (per_step) {
+            per_step[2 * j] = x;
+            per_step[2 * j + 1] = y;
+        }
     }
     for (auto &x : ev) cudaEventDestroy(x);
     if (e != cudaSuccess) return fail(ctx, HG_ERR_CUDA, "launch failed: %s", cudaGetErrorString(e));
@@ -1045,6 +1076,22 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io) {
     for (int32_t di : doms) ctx->doms[di]->step += n;
     if (ms_sc) *ms_sc = a;
     if (ms_io) *ms_io = b;
+    return HG_OK;
+}
+
+int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) {
+    if (!ctx) return HG_ERR_ARG;
+    if (block < 32 || block > 512 || block % 32) return fail(ctx, HG_ERR_ARG, "block size must be a multiple of 32 in [32, 512]");
+    if (spt != 1 && spt != 2 && spt != 4) return fail(ctx, HG_ERR_ARG, "sites per thread must be 1, 2 or 4");
+    if (variant < 0 || variant > 1 || (variant == 1 && spt == 4))
+        return fail(ctx, HG_ERR_ARG, "kernel variant must be 0, or 1 with 1 or 2 sites per thread");
+    if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    ctx->block = block;
+    ctx->spt = spt;
+    ctx->variant = variant;
+    drop_plans(ctx);
     return HG_OK;
 }
 

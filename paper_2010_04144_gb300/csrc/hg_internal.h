@@ -64,10 +64,13 @@ struct CollideCfg {
     int scheme;
     int block;
     int spt;
+    int variant;  // 0 = gathers into registers, 1 = gathers staged by cp.async (spt 1 or 2)
 };
 
+// parity (AA only): 0 = every domain runs an even step, 1 = odd, 2 = per-domain
+// parity read from the step counters.
 cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                                  int64_t n_tiles, int off, cudaStream_t st);
+                                  int64_t n_tiles, int off, int parity, cudaStream_t st);
 cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, int off, cudaStream_t st);
 cudaError_t launch_advance_list(int64_t *steps_base, const int32_t *idx, int n, int64_t by,
                                 cudaStream_t st);

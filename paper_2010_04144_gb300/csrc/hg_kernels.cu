@@ -127,16 +127,14 @@ __device__ __forceinline__ float4 collide(float g[19], float omega) {
     return make_float4(drho, ux, uy, uz);
 }
 
+// Read-only (non-coherent) loads; 16-bit types go through __ldg on their bit
+// pattern so the compiler can still schedule them freely.
 template <typename T> __device__ __forceinline__ T ldg_nc(const T *p) { return __ldg(p); }
 template <> __device__ __forceinline__ __half ldg_nc(const __half *p) {
-    unsigned short r;
-    asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(r) : "l"(p));
-    return __ushort_as_half(r);
+    return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p)));
 }
 template <> __device__ __forceinline__ __nv_bfloat16 ldg_nc(const __nv_bfloat16 *p) {
-    unsigned short r;
-    asm volatile("ld.global.nc.u16 %0, [%1];" : "=h"(r) : "l"(p));
-    return __ushort_as_bfloat16(r);
+    return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p)));
 }
 
 // ---- A/B pull: F_{t-1} in src, F_t to dst ----
@@ -170,6 +168,15 @@ __device__ __forceinline__ void site_ab(const DomDev &D, const typename St<S>::T
 }
 
 // ---- AA even step: state G_t natural at the own site -> F_t swapped at the own site ----
+// The store base is passed through an opaque move so the compiler recomputes
+// the 19 store addresses after the collision instead of keeping the load
+// addresses alive across it (75 -> ~45 registers).
+template <typename T> __device__ __forceinline__ T *opaque(T *p) {
+    T *q;
+    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
+    return q;
+}
+
 template <int S>
 __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T *buf, int64_t s,
                                              bool flagged) {
@@ -189,9 +196,10 @@ __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T 
         });
     }
     const float4 m = collide(g, D.omega);
+    typename St<S>::T *wb = opaque(buf + s);
     unroll<0, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        buf[(int64_t)OPP(I) * np + s] = Tr::template st<I>(g[I]);
+        wb[(int64_t)OPP(I) * np] = Tr::template st<I>(g[I]);
     });
     if (slot >= 0) D.bnd[slot] = m;
 }
@@ -200,41 +208,293 @@ __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T 
 template <int S>
 __device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s) {
     using Tr = St<S>;
-    const int64_t np = D.np;
+    const uint32_t np = (uint32_t)D.np;
+    const uint32_t su = (uint32_t)s;
     int32_t nb[18];
 #pragma unroll
-    for (int i = 0; i < 18; ++i) nb[i] = __ldg(D.nbr + (int64_t)i * np + s);
+    for (int i = 0; i < 18; ++i) nb[i] = __ldg(D.nbr + (i * np + su));
     float g[19];
-    g[0] = Tr::template ld<0>(buf[s]);
+    g[0] = Tr::template ld<0>(buf[su]);
     int slot = -1;
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
         const int32_t v = nb[I - 1];
         if (v >= 0) {
-            g[I] = Tr::template ld<I>(buf[(int64_t)OPP(I) * np + v]);
+            g[I] = Tr::template ld<I>(buf[OPP(I) * np + (uint32_t)v]);
         } else {
-            const float raw = Tr::template ld<OPP(I)>(buf[(int64_t)I * np + s]);
+            const float raw = Tr::template ld<OPP(I)>(buf[I * np + su]);
             g[I] = link_rule<I>(D, v, raw, slot);
         }
     });
     const float4 m = collide(g, D.omega);
-    buf[s] = Tr::template st<0>(g[0]);
+    buf[su] = Tr::template st<0>(g[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int32_t t = nb[OPP(I) - 1];  // site at x + c_I
-        if (t >= 0) buf[(int64_t)I * np + t] = Tr::template st<I>(g[I]);
-        else buf[(int64_t)OPP(I) * np + s] = Tr::template st<I>(g[I]);  // raw, rule applied on read
+        int32_t t;  // site at x + c_I (reloaded: keeps 18 entries from staying live)
+        asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(t) : "l"(D.nbr + ((OPP(I) - 1) * np + su)));
+        const uint32_t off = t >= 0 ? I * np + (uint32_t)t : OPP(I) * np + su;  // raw if not fluid
+        buf[off] = Tr::template st<I>(g[I]);
     });
     if (slot >= 0) D.bnd[slot] = m;
 }
 
-template <int S, int SCHEME, int SPT>
+// ==== async-staged variant (V = 1) ==========================================
+// The 19 gathers of every site a thread owns are issued as cp.async copies into
+// a shared-memory stage [SPT][19][blockDim] (4-byte words) before one wait, so
+// the loads in flight do not hold registers.  16-bit elements are fetched as
+// the aligned 32-bit word that contains them; `sel` remembers which half.
+__device__ __forceinline__ uint32_t smem_addr(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void cp_async4(uint32_t dst, const void *src) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() {
+    asm volatile("cp.async.commit_group;\ncp.async.wait_group 0;\n" ::: "memory");
+}
+
+template <int S> struct Word;
+template <> struct Word<kF32> {
+    static __device__ __forceinline__ const void *src(const float *p, uint32_t &sel, int) {
+        return p;
+    }
+    template <int I> static __device__ __forceinline__ float get(uint32_t w, uint32_t) {
+        return __uint_as_float(w);
+    }
+};
+template <int S16> struct Word16 {
+    using T = typename St<S16>::T;
+    static __device__ __forceinline__ const void *src(const T *p, uint32_t &sel, int I) {
+        const uintptr_t a = (uintptr_t)p;
+        sel |= (uint32_t)((a >> 1) & 1u) << I;
+        return (const void *)(a & ~(uintptr_t)3);
+    }
+    template <int I> static __device__ __forceinline__ float get(uint32_t w, uint32_t sel) {
+        const unsigned short h = (unsigned short)(((sel >> I) & 1u) ? (w >> 16) : (w & 0xffffu));
+        if constexpr (S16 == kF16) return St<kF16>::template ld<I>(__ushort_as_half(h));
+        else return St<kBF16>::template ld<I>(__ushort_as_bfloat16(h));
+    }
+};
+template <> struct Word<kF16> : Word16<kF16> {};
+template <> struct Word<kBF16> : Word16<kBF16> {};
+
+// Issue the gathers of site s: incoming direction I from `src_row(I)` at the
+// pull source, or the own opposite value on non-fluid links.  AA odd reads the
+// swapped slot OPP(I) at the source and the natural slot I at the own site.
+template <int S, bool AA>
+__device__ __forceinline__ void issue_gathers(const DomDev &D, const typename St<S>::T *src,
+                                              int64_t s, uint32_t stage, uint32_t rstride,
+                                              uint32_t &sel, uint32_t &wall, uint32_t &iol) {
+    const int64_t np = D.np;
+    int32_t nb[18];
+#pragma unroll
+    for (int i = 0; i < 18; ++i) nb[i] = __ldg(D.nbr + (int64_t)i * np + s);
+    cp_async4(stage, Word<S>::src(src + s, sel, 0));
+    unroll<1, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        const int32_t v = nb[I - 1];
+        const typename St<S>::T *p;
+        if (v >= 0) {
+            p = src + (int64_t)(AA ? OPP(I) : I) * np + v;
+        } else {
+            p = src + (int64_t)(AA ? I : OPP(I)) * np + s;
+            if (v == -1) wall |= 1u << I;
+            else iol |= 1u << I;
+        }
+        cp_async4(stage + I * rstride, Word<S>::src(p, sel, I));
+    });
+}
+
+// Read the staged values back, apply the boundary rules, collide.
+template <int S>
+__device__ __forceinline__ float4 staged_collide(const DomDev &D, const uint32_t *st,
+                                                 uint32_t rwords, int64_t s, uint32_t sel,
+                                                 uint32_t iol, float g[19], int &slot) {
+    unroll<0, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        g[I] = Word<S>::template get<I>(st[I * rwords], sel);
+    });
+    if (iol) {  // rare: links into an iolet opening
+        unroll<1, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            if ((iol >> I) & 1u) {
+                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * D.np + s);
+                g[I] = link_rule<I>(D, v, g[I], slot);
+            }
+        });
+    }
+    return collide(g, D.omega);
+}
+
+template <int S, int SPT>
+__device__ __forceinline__ void tile_ab_async(const DomDev &D, const TileDev &tl, int64_t t,
+                                              uint32_t *stage_base) {
+    using T = typename St<S>::T;
+    const T *src = (const T *)D.f[(t - 1) & 1];
+    T *dst = (T *)D.f[t & 1];
+    const uint32_t B = blockDim.x;
+    uint32_t sel[SPT], iol[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        sel[j] = 0;
+        iol[j] = 0;
+        uint32_t wall = 0;
+        const int r = j * B + threadIdx.x;
+        if (r < tl.count)
+            issue_gathers<S, false>(D, src, tl.start + r, smem_addr(stage_base + (j * 19) * B + threadIdx.x),
+                                    4 * B, sel[j], wall, iol[j]);
+    }
+    cp_async_wait_all();
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        const int r = j * B + threadIdx.x;
+        if (r >= tl.count) continue;
+        const int64_t s = tl.start + r;
+        float g[19];
+        int slot = -1;
+        const float4 m = staged_collide<S>(D, stage_base + (j * 19) * B + threadIdx.x, B, s, sel[j],
+                                           iol[j], g, slot);
+        T *wb = opaque(dst + s);
+        unroll<0, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            wb[(int64_t)I * D.np] = St<S>::template st<I>(g[I]);
+        });
+        if (slot >= 0) D.bnd[slot] = m;
+    }
+}
+
+template <int S, int SPT>
+__device__ __forceinline__ void tile_aa_odd_async(const DomDev &D, const TileDev &tl,
+                                                  uint32_t *stage_base) {
+    using T = typename St<S>::T;
+    T *buf = (T *)D.f[0];
+    const uint32_t B = blockDim.x;
+    uint32_t sel[SPT], iol[SPT];
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        sel[j] = 0;
+        iol[j] = 0;
+        uint32_t wall = 0;
+        const int r = j * B + threadIdx.x;
+        if (r < tl.count)
+            issue_gathers<S, true>(D, buf, tl.start + r, smem_addr(stage_base + (j * 19) * B + threadIdx.x),
+                                   4 * B, sel[j], wall, iol[j]);
+    }
+    cp_async_wait_all();
+#pragma unroll
+    for (int j = 0; j < SPT; ++j) {
+        const int r = j * B + threadIdx.x;
+        if (r >= tl.count) continue;
+        const int64_t s = tl.start + r;
+        float g[19];
+        int slot = -1;
+        const float4 m = staged_collide<S>(D, stage_base + (j * 19) * B + threadIdx.x, B, s, sel[j],
+                                           iol[j], g, slot);
+        const int32_t *nb2 = opaque(D.nbr);  // fresh (L1-resident) reads for the scatter
+        T *wb = opaque(buf);
+        const int64_t np = D.np;
+        wb[s] = St<S>::template st<0>(g[0]);
+        unroll<1, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            const int32_t tg = __ldg(nb2 + (int64_t)(OPP(I) - 1) * np + s);  // site at x + c_I
+            const int64_t off = tg >= 0 ? (int64_t)I * np + tg : (int64_t)OPP(I) * np + s;
+            wb[off] = St<S>::template st<I>(g[I]);
+        });
+        if (slot >= 0) D.bnd[slot] = m;
+    }
+}
+
+// AA even step on pairs of adjacent sites (2 per thread): vector loads/stores.
+template <int S> struct Pair;
+template <> struct Pair<kF32> {
+    using V = float2;
+    template <int I> static __device__ __forceinline__ void ld(const float *p, float &a, float &b) {
+        const float2 v = *(const float2 *)p;
+        a = v.x;
+        b = v.y;
+    }
+    template <int I> static __device__ __forceinline__ void st(float *p, float a, float b) {
+        *(float2 *)p = make_float2(a, b);
+    }
+};
+template <int S16> struct Pair16 {
+    using T = typename St<S16>::T;
+    template <int I> static __device__ __forceinline__ void ld(const T *p, float &a, float &b) {
+        const uint32_t w = *(const uint32_t *)p;
+        if constexpr (S16 == kF16) {
+            a = St<kF16>::template ld<I>(__ushort_as_half((unsigned short)(w & 0xffffu)));
+            b = St<kF16>::template ld<I>(__ushort_as_half((unsigned short)(w >> 16)));
+        } else {
+            a = St<kBF16>::template ld<I>(__ushort_as_bfloat16((unsigned short)(w & 0xffffu)));
+            b = St<kBF16>::template ld<I>(__ushort_as_bfloat16((unsigned short)(w >> 16)));
+        }
+    }
+    template <int I> static __device__ __forceinline__ void st(T *p, float a, float b) {
+        const T ha = St<S16>::template st<I>(a), hb = St<S16>::template st<I>(b);
+        uint32_t w;
+        if constexpr (S16 == kF16) w = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
+        else w = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
+        *(uint32_t *)p = w;
+    }
+};
+template <> struct Pair<kF16> : Pair16<kF16> {};
+template <> struct Pair<kBF16> : Pair16<kBF16> {};
+
+template <int S>
+__device__ __forceinline__ void tile_aa_even_pairs(const DomDev &D, const TileDev &tl) {
+    using T = typename St<S>::T;
+    T *buf = (T *)D.f[0];
+    const int64_t np = D.np;
+    for (int r = 2 * threadIdx.x; r < tl.count; r += 2 * blockDim.x) {
+        const int64_t s = tl.start + r;  // even: tiles start at multiples of 64
+        if (r + 1 >= tl.count) {         // ragged tail: one site
+            const uint32_t word = __ldg(D.iomask + (s >> 5));
+            site_aa_even<S>(D, buf, s, (word >> (s & 31)) & 1u);
+            continue;
+        }
+        float ga[19], gb[19];
+        unroll<0, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            Pair<S>::template ld<I>(buf + (int64_t)I * np + s, ga[I], gb[I]);
+        });
+        const uint32_t word = __ldg(D.iomask + (s >> 5));
+        int slot_a = -1, slot_b = -1;
+        if ((word >> (s & 31)) & 1u) {
+            unroll<1, 19>([&](auto ic) {
+                constexpr int I = decltype(ic)::v;
+                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * np + s);
+                if (v < -1) ga[I] = link_rule<I>(D, v, ga[I], slot_a);
+            });
+        }
+        if ((word >> ((s + 1) & 31)) & 1u) {
+            unroll<1, 19>([&](auto ic) {
+                constexpr int I = decltype(ic)::v;
+                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * np + s + 1);
+                if (v < -1) gb[I] = link_rule<I>(D, v, gb[I], slot_b);
+            });
+        }
+        const float4 ma = collide(ga, D.omega);
+        const float4 mb = collide(gb, D.omega);
+        T *wb = opaque(buf + s);
+        unroll<0, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            Pair<S>::template st<I>(wb + (int64_t)OPP(I) * np, ga[I], gb[I]);
+        });
+        if (slot_a >= 0) D.bnd[slot_a] = ma;
+        if (slot_b >= 0) D.bnd[slot_b] = mb;
+    }
+}
+
+// PAR selects the AA step kind: 0 = even, 1 = odd, 2 = read from the domain's
+// counter per block (batches whose domains are at different parities).
+template <int S, int SCHEME, int SPT, int PAR, int V>
 __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict__ doms,
-                                                         const TileDev *__restrict__ tiles,
-                                                         int off) {
+                                                        const TileDev *__restrict__ tiles,
+                                                        int off) {
     using T = typename St<S>::T;
     __shared__ DomDev D;
     __shared__ int64_t t_now;
+    extern __shared__ uint32_t stage[];
     const TileDev tl = tiles[blockIdx.x];
     if (threadIdx.x == 0) {
         D = doms[tl.dom];
@@ -242,6 +502,15 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
     }
     __syncthreads();
     const int64_t t = t_now;
+    if constexpr (V == 1) {
+        if constexpr (SCHEME == kAB) {
+            tile_ab_async<S, SPT>(D, tl, t, stage);
+        } else {
+            const bool odd = PAR == 2 ? (t & 1) != 0 : PAR == 1;
+            if (odd) tile_aa_odd_async<S, SPT>(D, tl, stage);
+            else tile_aa_even_pairs<S>(D, tl);
+        }
+    } else {
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
         const int r = j * blockDim.x + threadIdx.x;
@@ -255,13 +524,15 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
             }
         } else {
             T *buf = (T *)D.f[0];
-            if (t & 1) {
+            const bool odd = PAR == 2 ? (t & 1) != 0 : PAR == 1;
+            if (odd) {
                 if (live) site_aa_odd<S>(D, buf, s);
             } else {
                 const uint32_t word = live ? __ldg(D.iomask + (s >> 5)) : 0u;
                 if (live) site_aa_even<S>(D, buf, s, (word >> (s & 31)) & 1u);
             }
         }
+    }
     }
 }
 
@@ -292,20 +563,38 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
     }
 }
 
+constexpr int kIoThreads = 1024;  // fixed: the summation order depends on it
+constexpr int kIoBatch = 4;       // independent loads in flight per thread
+
+// Thread t sums slots t, t + B, t + 2B, ... in that order (B = kIoThreads), then a
+// fixed shuffle tree combines the threads: the result depends only on the list.
 __device__ __forceinline__ void reduce_iolet(const int32_t *slots, const float4 *bnd, int n,
                                              double nx, double ny, double nz, double &su,
                                              double &sr) {
     su = 0.0;
     sr = 0.0;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        const float4 m = bnd[slots[j]];
-        su += (double)m.y * nx + (double)m.z * ny + (double)m.w * nz;
-        sr += (double)m.x;
+    for (int base = 0; base < n; base += kIoThreads * kIoBatch) {
+        int sl[kIoBatch];
+#pragma unroll
+        for (int b = 0; b < kIoBatch; ++b) {
+            const int j = base + b * kIoThreads + threadIdx.x;
+            sl[b] = j < n ? __ldg(slots + j) : -1;
+        }
+        float4 m[kIoBatch];
+#pragma unroll
+        for (int b = 0; b < kIoBatch; ++b) m[b] = sl[b] >= 0 ? bnd[sl[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int b = 0; b < kIoBatch; ++b) {
+            if (sl[b] >= 0) {
+                su += (double)m[b].y * nx + (double)m[b].z * ny + (double)m[b].w * nz;
+                sr += (double)m[b].x;
+            }
+        }
     }
     block_sum2(su, sr);
 }
 
-__global__ void __launch_bounds__(256) k_iolet_update(const IoDev *__restrict__ ios, int off) {
+__global__ void __launch_bounds__(kIoThreads) k_iolet_update(const IoDev *__restrict__ ios, int off) {
     const IoDev &I = ios[blockIdx.x];
     double su, sr;
     reduce_iolet(I.slots, I.bnd, I.n_slots, I.nx, I.ny, I.nz, su, sr);
@@ -315,19 +604,18 @@ __global__ void __launch_bounds__(256) k_iolet_update(const IoDev *__restrict__ 
         I.M[1] = I.n_slots ? sr / cnt : 0.0;
         I.M[2] = cnt;
     }
-    double val;
     if (I.coupled) {
         double cu, cr;
         reduce_iolet(I.src_slots, I.src_bnd, I.src_n_slots, I.src_nx, I.src_ny, I.src_nz, cu, cr);
-        val = I.factor * (I.src_n_slots ? cu / (double)I.src_n_slots : 0.0);
-    } else {
+        if (threadIdx.x == 0)
+            *I.bcv = (float)(I.factor * (I.src_n_slots ? cu / (double)I.src_n_slots : 0.0));
+    } else if (threadIdx.x == 0) {  // FP64 transcendentals are slow on this part: one thread
         const double tn = (double)(*I.step + off + 2);  // the next step
         double p = 1.0;
         if (I.pulse == 1) p = 0.5 * (1.0 - cos(2.0 * 3.141592653589793 * tn / I.period));
         else if (I.pulse == 2) p = sin(2.0 * 3.141592653589793 * tn / I.period);
-        val = I.value * p;
+        *I.bcv = (float)(I.value * p);
     }
-    if (threadIdx.x == 0) *I.bcv = (float)val;
 }
 
 __global__ void k_advance_list(int64_t *base, const int32_t *idx, int n, int64_t by) {
@@ -449,16 +737,44 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double *parti
     if (threadIdx.x == 0) *out = a;
 }
 
-template <int S, int SCHEME>
+template <int S, int SCHEME, int PAR, int V, int SPT>
+cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
+                          int64_t n_tiles, int off, cudaStream_t st) {
+    const size_t smem = V == 1 ? (size_t)SPT * 19 * cfg.block * 4 : 0;
+    auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    k<<<(unsigned)n_tiles, cfg.block, smem, st>>>(doms, tiles, off);
+    return cudaGetLastError();
+}
+
+template <int S, int SCHEME, int PAR>
 cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                           int64_t n_tiles, int off, cudaStream_t st) {
+    if (cfg.variant == 1) {
+        switch (cfg.spt) {
+            case 1: return launch_sc_one<S, SCHEME, PAR, 1, 1>(cfg, doms, tiles, n_tiles, off, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 1, 2>(cfg, doms, tiles, n_tiles, off, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     switch (cfg.spt) {
-        case 1: k_stream_collide<S, SCHEME, 1><<<(unsigned)n_tiles, cfg.block, 0, st>>>(doms, tiles, off); break;
-        case 2: k_stream_collide<S, SCHEME, 2><<<(unsigned)n_tiles, cfg.block, 0, st>>>(doms, tiles, off); break;
-        case 4: k_stream_collide<S, SCHEME, 4><<<(unsigned)n_tiles, cfg.block, 0, st>>>(doms, tiles, off); break;
+        case 1: return launch_sc_one<S, SCHEME, PAR, 0, 1>(cfg, doms, tiles, n_tiles, off, st);
+        case 2: return launch_sc_one<S, SCHEME, PAR, 0, 2>(cfg, doms, tiles, n_tiles, off, st);
+        case 4: return launch_sc_one<S, SCHEME, PAR, 0, 4>(cfg, doms, tiles, n_tiles, off, st);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
+}
+
+template <int S>
+cudaError_t launch_sc_storage(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
+                              int64_t n_tiles, int off, int parity, cudaStream_t st) {
+    if (cfg.scheme == kAB) return launch_sc_spt<S, kAB, 2>(cfg, doms, tiles, n_tiles, off, st);
+    if (parity == 0) return launch_sc_spt<S, kAA, 0>(cfg, doms, tiles, n_tiles, off, st);
+    if (parity == 1) return launch_sc_spt<S, kAA, 1>(cfg, doms, tiles, n_tiles, off, st);
+    return launch_sc_spt<S, kAA, 2>(cfg, doms, tiles, n_tiles, off, st);
 }
 
 inline unsigned rb_grid(int64_t n) {
@@ -470,23 +786,17 @@ inline unsigned rb_grid(int64_t n) {
 }  // namespace
 
 cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                                  int64_t n_tiles, int off, cudaStream_t st) {
+                                  int64_t n_tiles, int off, int parity, cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    if (cfg.scheme == kAB) {
-        if (cfg.storage == kF32) return launch_sc_spt<kF32, kAB>(cfg, doms, tiles, n_tiles, off, st);
-        if (cfg.storage == kF16) return launch_sc_spt<kF16, kAB>(cfg, doms, tiles, n_tiles, off, st);
-        if (cfg.storage == kBF16) return launch_sc_spt<kBF16, kAB>(cfg, doms, tiles, n_tiles, off, st);
-    } else {
-        if (cfg.storage == kF32) return launch_sc_spt<kF32, kAA>(cfg, doms, tiles, n_tiles, off, st);
-        if (cfg.storage == kF16) return launch_sc_spt<kF16, kAA>(cfg, doms, tiles, n_tiles, off, st);
-        if (cfg.storage == kBF16) return launch_sc_spt<kBF16, kAA>(cfg, doms, tiles, n_tiles, off, st);
-    }
+    if (cfg.storage == kF32) return launch_sc_storage<kF32>(cfg, doms, tiles, n_tiles, off, parity, st);
+    if (cfg.storage == kF16) return launch_sc_storage<kF16>(cfg, doms, tiles, n_tiles, off, parity, st);
+    if (cfg.storage == kBF16) return launch_sc_storage<kBF16>(cfg, doms, tiles, n_tiles, off, parity, st);
     return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, int off, cudaStream_t st) {
     if (n_ios <= 0) return cudaSuccess;
-    k_iolet_update<<<n_ios, 256, 0, st>>>(ios, off);
+    k_iolet_update<<<n_ios, kIoThreads, 0, st>>>(ios, off);
     return cudaGetLastError();
 }
 

@@ -43,7 +43,8 @@ FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_size_t, C.c_void_p)
 class hg_ctx_params(C.Structure):
     _fields_ = [("device", C.c_int32), ("storage", C.c_int32), ("scheme", C.c_int32),
                 ("block_size", C.c_int32), ("sites_per_thread", C.c_int32),
-                ("graph_steps", C.c_int32), ("stream", C.c_void_p), ("alloc", ALLOC_FN),
+                ("graph_steps", C.c_int32), ("kernel_variant", C.c_int32),
+                ("stream", C.c_void_p), ("alloc", ALLOC_FN),
                 ("free", FREE_FN), ("alloc_user", C.c_void_p)]
 
 
@@ -74,7 +75,7 @@ _SIGS = {
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hg_step": ([C.c_void_p, C.c_int64], C.c_int),
     "hg_step_domains": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_int64], C.c_int),
-    "hg_step_profiled": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p], C.c_int),
+    "hg_step_profiled": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hg_read_macroscopic": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hg_read_macroscopic_device": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_read_iolet_stats": ([C.c_void_p, C.c_void_p], C.c_int),
@@ -84,6 +85,7 @@ _SIGS = {
     "hg_save_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
     "hg_load_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
     "hg_read_state": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_ctx_set_launch": ([C.c_void_p, C.c_int32, C.c_int32, C.c_int32], C.c_int),
     "hg_mass_noalloc": ([C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p],
                         C.c_int),
 }
@@ -177,7 +179,7 @@ class Context:
     """One device, one stream, one storage type and propagation scheme."""
 
     def __init__(self, device=0, storage="f32", scheme="ab", block_size=0, sites_per_thread=0,
-                 graph_steps=0, stream=None, torch_memory=True):
+                 graph_steps=0, stream=None, torch_memory=True, kernel_variant=0):
         import torch
 
         self.torch = torch
@@ -189,6 +191,7 @@ class Context:
         p = hg_ctx_params()
         p.device, p.storage, p.scheme = device, self.storage, self.scheme
         p.block_size, p.sites_per_thread, p.graph_steps = block_size, sites_per_thread, graph_steps
+        p.kernel_variant = kernel_variant
         p.stream = self.stream.cuda_stream
         self._alloc = _TorchAllocator(device) if torch_memory else None
         if self._alloc is not None:
@@ -210,6 +213,11 @@ class Context:
             arr[j].src_iolet, arr[j].dst_iolet, arr[j].factor = int(sk), int(dk), float(f)
         self._ck(lib().hg_couple(self.h, src.h, dst.h, arr, len(pairs)))
 
+    def set_launch(self, block_size, sites_per_thread, kernel_variant=0):
+        self._ck(lib().hg_ctx_set_launch(self.h, int(block_size), int(sites_per_thread),
+                                         int(kernel_variant)))
+        self.launch = (int(block_size), int(sites_per_thread), int(kernel_variant))
+
     def step(self, n):
         self._ck(lib().hg_step(self.h, int(n)))
 
@@ -217,9 +225,14 @@ class Context:
         arr = (C.c_void_p * max(1, len(doms)))(*[d.h for d in doms])
         self._ck(lib().hg_step_domains(self.h, arr, len(doms), int(n)))
 
-    def step_profiled(self, n):
+    def step_profiled(self, n, per_step=False):
+        """Run n steps with CUDA events around every kernel: (stream-collide ms, iolet ms)
+        totals, plus the (n, 2) per-step array when per_step is true."""
         a, b = C.c_double(), C.c_double()
-        self._ck(lib().hg_step_profiled(self.h, int(n), C.byref(a), C.byref(b)))
+        arr = np.zeros((max(1, int(n)), 2), np.float32)
+        self._ck(lib().hg_step_profiled(self.h, int(n), C.byref(a), C.byref(b), _p(arr)))
+        if per_step:
+            return a.value, b.value, arr[: int(n)]
         return a.value, b.value
 
     def sync(self):

@@ -252,3 +252,38 @@ def test_errors_are_reported(gpu):
         assert a.step == 5 and b.step == 3
     finally:
         ctx.close()
+
+
+LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128, 2, 1),
+            ("aa", 256, 1, 0), ("aa", 128, 4, 0), ("aa", 256, 1, 1), ("aa", 256, 2, 1),
+            ("aa", 64, 2, 1)]
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_kernel_variants_bit_identical(gpu, storage):
+    """Every scheme, launch shape and kernel variant computes the same bits per site."""
+    geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
+    ref = {}
+    for (scheme, block, spt, var) in LAUNCHES:
+        ctx = gpu.Context(storage=storage, scheme=scheme, block_size=block, sites_per_thread=spt,
+                          kernel_variant=var)
+        try:
+            d = ctx.domain(geo.xyz, geo.iolets, tau=TAU)
+            for steps in (1, 2, 35, 120):
+                ctx.step(steps - d.step)
+                got = (d.state(), d.iolet_stats(), d.boundary_values())
+                if steps not in ref:
+                    ref[steps] = got
+                for x, y in zip(ref[steps], got):
+                    assert np.array_equal(x, y), (scheme, block, spt, var, steps)
+        finally:
+            ctx.close()
+
+
+def test_variant1_against_oracle(gpu, oracle_mod):
+    geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
+    for scheme in ("ab", "aa"):
+        errs, _, _, _, _ = _run_pair(gpu, oracle_mod, geo, 151, scheme=scheme,
+                                     checkpoints=(50, 101), sites_per_thread=2, kernel_variant=1)
+        for eu, ep in errs:
+            assert eu < TOL["f32"] and ep < TOL["f32"], (scheme, errs)
