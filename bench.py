@@ -64,7 +64,7 @@ def workload(scale=1.71, depth=6, root_radius=24.0, seed=2010041442):
 
 
 class ClockSampler:
-    """nvidia-smi clock/throttle sampling during the timed region."""
+    """nvidia-smi clock/throttle sampling; only samples taken inside marked timed regions count."""
 
     Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
          "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -74,23 +74,29 @@ class ClockSampler:
         self.device = device
         self.proc = None
         self.lines = []
+        self.active = False
 
-    def __enter__(self):
+    def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.Q}",
                                           "--format=csv,noheader,nounits", "-lms", "100"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.t = threading.Thread(target=self._read, daemon=True)
             self.t.start()
+            time.sleep(0.3)
         except Exception:
             self.proc = None
         return self
 
+    def mark(self, on):
+        self.active = on
+
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            if self.active:
+                self.lines.append(line.strip())
 
-    def __exit__(self, *a):
+    def stop(self):
         if self.proc:
             self.proc.terminate()
             try:
@@ -119,6 +125,30 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def profiled_traffic(variant_key, launch):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel build."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            t = json.load(f)
+        e = t.get(variant_key)
+        if e and e.get("launch") == launch and e.get("kernel_source_sha") == kernel_source_sha():
+            return e["bytes_per_launch"], e.get("scaled_from")
+    except Exception:
+        pass
+    return None, None
+
+
+def kernel_source_sha():
+    import hashlib
+
+    h = hashlib.sha256()
+    for f in ("hg_kernels.cu", "hg_internal.h"):
+        with open(os.path.join(ROOT, "paper_2010_04144_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
 def dist_setup():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
@@ -135,50 +165,69 @@ def dist_setup():
 
 
 def max_over_ranks(x, dist, device):
+    """Largest value over all ranks (the slowest replica's time)."""
     if dist is None:
         return x
     import torch
 
-    t = torch.tensor([x], dtype=torch.float64, device=f"cuda:{device}")
+    dev = f"cuda:{device}" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
 
 
-def barrier(dist, stream=None):
+def barrier(dist):
     import torch
 
-    torch.cuda.synchronize()
+    if torch.cuda.is_available():
+        torch.cuda.synchronize()
     if dist is not None:
         dist.barrier()
-        torch.cuda.synchronize()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
 
 
-def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler=None):
-    """Device-timed steps (graphs), per-kernel launch durations, and the e2e job."""
+def whole_job_mflups(sites_per_rank, world_size, steps, max_ms):
+    """Weak scaling: every rank advances its own replica; units of all ranks / slowest time."""
+    return sites_per_rank * world_size * steps / (max_ms / 1e3) / 1e6
+
+
+def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler):
+    """Autotuned launch shape, device-timed steps (graphs), per-kernel times, e2e job."""
     import torch
+
+    from paper_2010_04144_gb300.autotune import autotune
 
     ctx = H.Context(device=device, storage=storage, scheme=scheme)
     try:
         d = ctx.domain(geo.xyz, geo.iolets, tau=0.8)
         n = d.n
         st = ctx.stream
+        nvtx = torch.cuda.nvtx
+        tag = f"{storage}:{scheme}"
+        nvtx.range_push(f"{tag}-autotune")
+        best, timing = autotune(ctx)
+        nvtx.range_pop()
         # warm-up, then the timed region: exactly `steps` steps, barrier + sync on both sides
         ctx.step(warmup)
         barrier(dist)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        if sampler:
-            sampler.__enter__()
+        sampler.mark(True)
+        nvtx.range_push(f"{tag}-timed")
         e0.record(st)
         ctx.step(steps)
         e1.record(st)
         barrier(dist)
-        if sampler:
-            sampler.__exit__()
-        ms = e0.elapsed_time(e1)
-        ms = max_over_ranks(ms, dist, device)
-        # per-kernel durations (CUDA events on the context stream, no graph)
+        nvtx.range_pop()
+        sampler.mark(False)
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, device)
+        # per-kernel durations (CUDA events on the context stream around every launch)
+        nvtx.range_push(f"{tag}-profiled")
         ms_sc, ms_io = ctx.step_profiled(steps)
+        nvtx.range_pop()
         # end to end through the C ABI: host state in (pinned), `steps` steps, macroscopic out
+        import ctypes as C
+
         state = d.save_state()
         pinned = torch.empty(state.size, dtype=torch.uint8, pin_memory=True)
         pinned.numpy()[:] = state
@@ -187,18 +236,17 @@ def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler=N
         t0 = time.perf_counter()
         d.load_state(pinned.numpy())
         ctx.step(steps)
-        from paper_2010_04144_gb300 import hemegb as _H
-        import ctypes as C
-
-        rc = _H.lib().hg_read_macroscopic(d.h, C.c_void_p(out.data_ptr()), None)
+        rc = H.lib().hg_read_macroscopic(d.h, C.c_void_p(out.data_ptr()), None)
         if rc != 0:
             raise RuntimeError("read-back failed")
         barrier(dist)
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device)
-        launches_timed = steps * (1 + (1 if geo.iolets else 0)) + (steps + 15) // 16
-        return dict(n=n, ms=ms, ms_sc=ms_sc, ms_io=ms_io, e2e_s=e2e_s,
-                    h2d=int(state.size), d2h=int(n * 16), launches=launches_timed,
-                    device_bytes=d.info()["device_bytes"])
+        gs = 16
+        launches = steps * (1 + (1 if geo.iolets else 0)) + (steps + gs - 1) // gs
+        return dict(n=n, ms=ms, ms_sc=ms_sc, ms_io=ms_io, e2e_s=e2e_s, h2d=int(state.size),
+                    d2h=int(n * 16), launches=launches, device_bytes=d.info()["device_bytes"],
+                    launch={"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]},
+                    tuning_ms={f"{b}x{t}v{v}": round(x, 4) for (b, t, v), x in timing.items()})
     finally:
         ctx.close()
 
@@ -251,20 +299,214 @@ def run_reference(args):
     print(json.dumps(line))
 
 
+def _geo_pool_gen(args):
+    """Worker (spawned process): voxelise one request's geometries."""
+    from paper_2010_04144_gb300 import synth as S
+
+    spec, coupled = args
+    art = S.tree(spec, inlet_speed=0.05, period=1000.0)
+    if not coupled:
+        return (art,)
+    ven = S.tree(spec, venous=True, venous_offset=0.0)
+    return (art, ven)
+
+
+def run_serve(args, H, device):
+    """Serving workload: seeded request stream, continuous batching, p50/p99 time-to-result."""
+    import multiprocessing as mp
+
+    from paper_2010_04144_gb300 import serve as SV
+    from paper_2010_04144_gb300 import synth as S
+
+    reqs = S.request_stream(n_requests=args.requests, rate_per_s=args.rate,
+                            sites_range=(args.min_sites, args.max_sites), steps=args.serve_steps)
+    pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    t0 = time.perf_counter()
+    geos = pool.map(_geo_pool_gen, [(r.spec, r.coupled) for r in reqs], chunksize=1)
+    pool.close()
+    gen_s = time.perf_counter() - t0
+    srv = SV.Server(device=device, storage=args.serve_storage, scheme="aa",
+                    budget_bytes=args.budget_gb * 1e9, chunk_steps=100)
+    try:
+        for r, g in zip(reqs, geos):
+            if r.coupled:
+                job = SV.coupled_job_from_trees(r.rid, r.arrival_s, r.steps, g[0], g[1],
+                                                S.uniform_draws(r.rid + 7919, len(g[1].iolets)))
+            else:
+                job = SV.Job(rid=r.rid, arrival_s=r.arrival_s, steps=r.steps, geoms=[g[0]])
+            srv.submit(job)
+        srv.run()
+        st = srv.stats()
+    finally:
+        srv.close()
+    sites = [sum(x.n for x in g) for g in geos]
+    offered = sum(sites) * args.serve_steps / (reqs[-1].arrival_s or 1.0) / 1e6
+    line = {"metric": "served time-to-result p50/p99 (s) and aggregate MFLUPS", "value": st["p50_s"],
+            "unit": "s (p50 time-to-result)", "p99_s": st["p99_s"], "higher_is_better": False,
+            "aggregate_mflups": st["aggregate_mflups"], "n_gpus": 1, "dtype": args.serve_storage + "-stored/f32-compute",
+            "data": "synthetic (seeded request stream)",
+            "config": {"workload": f"{args.requests} seeded tree requests, Poisson {args.rate}/s, "
+                                   f"sites log-uniform [{args.min_sites:.0e}, {args.max_sites:.0e}], "
+                                   f"half coupled pairs, {args.serve_steps} steps each",
+                       "budget_gb": args.budget_gb, "tick_steps": 100, "scheme": "aa",
+                       "total_sites": int(sum(sites)), "offered_mflups": offered,
+                       "geometry_generation_s": gen_s},
+            "serving": st}
+    print(json.dumps(line))
+
+
+def run_coupled(args, H, device):
+    """Coupled pair: arterial tree and its venous twin stepped in the same launches."""
+    import torch
+
+    from paper_2010_04144_gb300 import synth as S
+    from paper_2010_04144_gb300.autotune import autotune
+
+    spec = S.TreeSpec(depth=6, root_radius=24.0, seed=2010041442, scale=args.coupled_scale)
+    art = S.tree(spec, inlet_speed=0.05, period=1000.0)
+    ven = S.tree(spec, venous=True)
+    ctx = H.Context(device=device, storage="f32", scheme=args.coupled_scheme)
+    try:
+        da = ctx.domain(art.xyz, art.iolets)
+        dv = ctx.domain(ven.xyz, ven.iolets)
+        pairs = []
+        for k in range(1, len(art.iolets)):  # mirrored leaf k feeds venous inlet k (1:1 map)
+            _, _, _, f = H.hg_coupling_factors([art.iolets[k].centre], [art.iolets[k].area()],
+                                               [ven.iolets[k].centre], [ven.iolets[k].area()], [0.5])
+            pairs.append((k, k, float(f[0])))
+        ctx.couple(da, dv, pairs)
+        best, _ = autotune(ctx)
+        ctx.step(args.warmup)
+        barrier(None)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        ctx.step(args.steps)
+        e1.record(ctx.stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        ms_sc, ms_io = ctx.step_profiled(min(args.steps, 200))
+        n = da.n + dv.n
+        B = BYTES_PER_UPDATE[("f32", args.coupled_scheme)]
+        per = ms_sc / min(args.steps, 200)
+        peak, kind = hbm_peak()
+        Mv = dv.iolet_stats()
+        Ma = da.iolet_stats()
+        ratio = [float(-Mv[k, 0] / Ma[k, 0]) if Ma[k, 0] else None for k in range(1, len(art.iolets))]
+        line = {"metric": "MFLUPS, coupled arterial+venous pair in one launch sequence",
+                "value": n * args.steps / (ms / 1e3) / 1e6, "unit": "MFLUPS", "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+                "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded tree pair)",
+                "config": {"workload": f"arterial tree d=6 R=24x{args.coupled_scale} + venous twin (radii x1.2)",
+                           "arterial_sites": da.n, "venous_sites": dv.n, "pairs": len(pairs),
+                           "factor": pairs[0][2], "scheme": args.coupled_scheme,
+                           "launch": {"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]}},
+                "roofline": {"bound": "hbm", "achieved": B * n / (per / 1e3) / 1e9, "peak": peak,
+                             "unit": "GB/s", "frac": B * n / (per / 1e3) / 1e9 / peak,
+                             "bytes_per_update": B},
+                "iolet_update_ms": ms_io / min(args.steps, 200),
+                "venous_over_arterial_mean_u": ratio[:8]}
+        print(json.dumps(line))
+    finally:
+        ctx.close()
+
+
+def run_precision(args, H, device):
+    """FP32 vs FP16 vs BF16 storage: throughput on the large tree, error vs the FP64 oracle."""
+    import torch
+
+    from paper_2010_04144_gb300 import synth as S
+    from paper_2010_04144_gb300.autotune import autotune
+
+    spec = S.TreeSpec(depth=8, root_radius=40.0, seed=2010041442, scale=args.precision_scale)
+    geo = S.tree(spec, inlet_speed=0.05, period=1000.0)
+    peak, kind = hbm_peak()
+    out = {}
+    for storage, scheme in (("f32", "ab"), ("f32", "aa"), ("f16", "aa"), ("bf16", "aa")):
+        ctx = H.Context(device=device, storage=storage, scheme=scheme)
+        try:
+            d = ctx.domain(geo.xyz, geo.iolets)
+            best, _ = autotune(ctx)
+            ctx.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            ctx.step(args.steps)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1)
+            ms_sc, _ = ctx.step_profiled(min(args.steps, 100))
+            B = BYTES_PER_UPDATE[(storage, scheme)]
+            per = ms_sc / min(args.steps, 100)
+            out[f"{storage}:{scheme}"] = {"mflups": d.n * args.steps / (ms / 1e3) / 1e6,
+                                          "roofline_frac": B * d.n / (per / 1e3) / 1e9 / peak,
+                                          "launch": list(best), "device_gb": d.info()["device_bytes"] / 1e9}
+        finally:
+            ctx.close()
+    err = {}
+    if not args.no_cpu_baseline:
+        import oracle
+
+        small = S.tree(S.TreeSpec(depth=8, root_radius=40.0, seed=2010041442, scale=args.error_scale),
+                       inlet_speed=0.05, period=1000.0)
+        od = oracle.Domain(small.xyz, small.iolets, tau=0.8)
+        oracle.System([od]).step(args.error_steps)
+        ref = od.moments()
+        for storage in ("f32", "f16", "bf16"):
+            ctx = H.Context(device=device, storage=storage, scheme="aa")
+            try:
+                d = ctx.domain(small.xyz, small.iolets)
+                ctx.step(args.error_steps)
+                m = d.macroscopic().astype(np.float64)
+                eu = float(np.linalg.norm(m[:, 1:] - ref[:, 1:]) / np.linalg.norm(ref[:, 1:]))
+                ep = float(np.linalg.norm(m[:, 0] - ref[:, 0]) / np.linalg.norm(ref[:, 0]))
+                err[storage] = {"velocity_rel_l2": eu, "pressure_rel_l2": ep}
+            finally:
+                ctx.close()
+        err["instance"] = f"d=8 R=40x{args.error_scale} ({small.n} sites), {args.error_steps} steps"
+    line = {"metric": "MFLUPS and HBM-roofline fraction, FP32 vs FP16/BF16-stored",
+            "value": out["f16:aa"]["mflups"], "unit": "MFLUPS (f16:aa)", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
+            "dtype": "f16-stored/f32-compute", "data": "synthetic (seeded tree)",
+            "config": {"workload": f"tree d=8 R=40x{args.precision_scale}", "fluid_sites": geo.n},
+            "variants": out, "error_vs_fp64_oracle": err}
+    print(json.dumps(line))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="hemegb", choices=["hemegb", "reference"])
     ap.add_argument("--scale", type=float, default=1.71)
     ap.add_argument("--variants", default="f32:aa,f32:ab,f16:aa,bf16:aa")
-    ap.add_argument("--headline", default="f32:aa")
+    ap.add_argument("--headline", default="f32:best")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve"])
+    ap.add_argument("--coupled-scale", type=float, default=2.12)
+    ap.add_argument("--coupled-scheme", default="ab")
+    ap.add_argument("--precision-scale", type=float, default=1.84)
+    ap.add_argument("--error-scale", type=float, default=0.54)
+    ap.add_argument("--error-steps", type=int, default=500)
+    ap.add_argument("--requests", type=int, default=256)
+    ap.add_argument("--rate", type=float, default=4.0)
+    ap.add_argument("--min-sites", type=float, default=5e4)
+    ap.add_argument("--max-sites", type=float, default=4e7)
+    ap.add_argument("--serve-steps", type=int, default=2000)
+    ap.add_argument("--serve-storage", default="f16")
+    ap.add_argument("--budget-gb", type=float, default=180.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
         return run_reference(args)
+    if args.config != "tree":
+        import torch
+
+        from paper_2010_04144_gb300 import hemegb as H
+
+        H.lib()
+        torch.cuda.set_device(0)
+        return {"coupled": run_coupled, "precision": run_precision, "serve": run_serve}[args.config](args, H, 0)
 
     import torch
 
@@ -278,37 +520,43 @@ def main():
     cfg["steps_per_job"] = args.steps
     peak, peak_kind = hbm_peak()
     variants = [tuple(v.split(":")) for v in args.variants.split(",")]
-    head = tuple(args.headline.split(":"))
-    if head not in variants:
-        variants.insert(0, head)
     results = {}
-    sampler = ClockSampler(device)
-    for (storage, scheme) in variants:
-        r = time_variant(H, geo, storage, scheme, args.steps, args.warmup, dist, device,
-                         sampler if (storage, scheme) == head else None)
-        B = BYTES_PER_UPDATE[(storage, scheme)]
-        r["mflups"] = r["n"] * args.steps / (r["ms"] / 1e3) / 1e6
-        per_launch_ms = r["ms_sc"] / args.steps
-        r["achieved_gbs"] = B * r["n"] / (per_launch_ms / 1e3) / 1e9
-        r["bytes_per_update"] = B
-        results[(storage, scheme)] = r
+    sampler = ClockSampler(device).start()
+    try:
+        for (storage, scheme) in variants:
+            r = time_variant(H, geo, storage, scheme, args.steps, args.warmup, dist, device, sampler)
+            B = BYTES_PER_UPDATE[(storage, scheme)]
+            r["mflups"] = r["n"] * ws * args.steps / (r["ms"] / 1e3) / 1e6
+            r["achieved_gbs"] = B * r["n"] / (r["ms_sc"] / args.steps / 1e3) / 1e9
+            r["bytes_per_update"] = B
+            results[(storage, scheme)] = r
+    finally:
+        sampler.stop()
+    if args.headline == "f32:best":
+        f32 = [k for k in results if k[0] == "f32"]
+        head = max(f32, key=lambda k: results[k]["mflups"]) if f32 else next(iter(results))
+    else:
+        head = tuple(args.headline.split(":"))
     h = results[head]
     total_sites = h["n"] * ws
-    value = total_sites * args.steps / (h["ms"] / 1e3) / 1e6
+    value = whole_job_mflups(h["n"], ws, args.steps, h["ms"])
     e2e_value = total_sites * args.steps / h["e2e_s"] / 1e6
+    traffic, scaled_from = profiled_traffic(f"{head[0]}:{head[1]}", h["launch"])
     line = {
         "metric": "MFLUPS (D3Q19 LBGK site updates per second / 1e6), whole hot path per step",
         "value": value, "unit": "MFLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[head[0]],
         "data": "synthetic (seeded tree geometry, rest initial state)",
-        "config": {**cfg, "storage": head[0], "scheme": head[1],
+        "config": {**cfg, "storage": head[0], "scheme": head[1], "launch": h["launch"],
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": h["achieved_gbs"], "peak": peak, "unit": "GB/s",
-                     "frac": h["achieved_gbs"] / peak, "traffic": None,
+                     "frac": h["achieved_gbs"] / peak, "traffic": traffic,
+                     "traffic_note": scaled_from,
                      "kernel": "k_stream_collide",
                      "bytes_per_update": h["bytes_per_update"],
-                     "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)"},
+                     "launch_ms": h["ms_sc"] / args.steps,
+                     "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
         "e2e": {"value": e2e_value, "unit": "MFLUPS",
                 "h2d_bytes_per_step": h["h2d"] / args.steps,
                 "d2h_bytes_per_step": h["d2h"] / args.steps,
@@ -320,6 +568,7 @@ def main():
                                    "bytes_per_update": r["bytes_per_update"],
                                    "stream_collide_ms": r["ms_sc"] / args.steps,
                                    "iolet_update_ms": r["ms_io"] / args.steps,
+                                   "launch": r["launch"], "tuning_ms": r["tuning_ms"],
                                    "device_bytes": r["device_bytes"]}
                      for (s, c), r in results.items()},
     }

@@ -230,8 +230,9 @@ void sort_keys(std::vector<uint64_t> &key, std::vector<int64_t> &idx) {
 }
 
 double pulse(int kind, double t, double period) {
-    if (kind == HG_PULSE_COSINE) return 0.5 * (1.0 - std::cos(2.0 * 3.141592653589793 * t / period));
-    if (kind == HG_PULSE_SINE) return std::sin(2.0 * 3.141592653589793 * t / period);
+    const double ph = kind == HG_PULSE_CONST ? 0.0 : std::fmod(t, period) / period;
+    if (kind == HG_PULSE_COSINE) return 0.5 * (1.0 - std::cos(2.0 * 3.141592653589793 * ph));
+    if (kind == HG_PULSE_SINE) return std::sin(2.0 * 3.141592653589793 * ph);
     return 1.0;
 }
 
@@ -250,9 +251,10 @@ struct PlanKey {
 
 struct Plan {
     std::vector<int32_t> doms;
-    DevBuf tiles, ios, adv;
+    DevBuf tiles, ios, adv, chunks, partials, counters;
     int64_t n_tiles = 0;
     int n_ios = 0;
+    int n_chunks = 0;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // by parity mode
     int graph_steps = 0;
 };
@@ -351,9 +353,8 @@ void drop_plans(hg_ctx *ctx) {
         Plan &p = *kv.second;
         for (auto &g : p.graph)
             if (g) cudaGraphExecDestroy(g);
-        dev_free(ctx, p.tiles);
-        dev_free(ctx, p.ios);
-        dev_free(ctx, p.adv);
+        for (DevBuf *b : {&p.tiles, &p.ios, &p.adv, &p.chunks, &p.partials, &p.counters})
+            dev_free(ctx, *b);
     }
     ctx->plans.clear();
 }
@@ -857,6 +858,8 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     const int64_t ts = (int64_t)ctx->block * ctx->spt;
     std::vector<TileDev> tiles;
     std::vector<IoDev> ios;
+    std::vector<int2> chunks;
+    std::vector<std::pair<int32_t, int32_t>> io_key;  // (domain, iolet) of each IoDev
     for (int32_t di : doms) {
         hg_domain *d = ctx->doms[di];
         for (int64_t s = 0; s < d->n; s += ts) {
@@ -884,42 +887,41 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
             I.value = io.value;
             I.period = io.period;
             I.pulse = io.pulse;
+            I.n_chunks = std::max(1, (I.n_slots + kIoChunk - 1) / kIoChunk);
+            I.part0 = (int32_t)chunks.size();
+            for (int c = 0; c < I.n_chunks; ++c) chunks.push_back(make_int2((int)ios.size(), c));
             auto cp = ctx->coupled.find({di, k});
             if (cp != ctx->coupled.end()) {
                 hg_domain *sd = ctx->doms[cp->second.src_dom];
                 if (std::find(doms.begin(), doms.end(), cp->second.src_dom) == doms.end())
                     return fail(ctx, HG_ERR_ARG, "a coupled source domain is not being stepped");
-                const int sk = cp->second.src_k;
-                const hg_iolet &so = sd->io[sk];
-                const double sn = std::sqrt((double)so.axis[0] * so.axis[0] + (double)so.axis[1] * so.axis[1] +
-                                            (double)so.axis[2] * so.axis[2]);
                 I.coupled = 1;
                 I.factor = cp->second.factor;
-                I.src_slots = (const int32_t *)sd->slots.p + sd->io_ptr[sk];
-                I.src_n_slots = (int32_t)(sd->io_ptr[sk + 1] - sd->io_ptr[sk]);
-                I.src_bnd = (const float4 *)sd->bnd.p;
-                I.src_nx = so.axis[0] / sn;
-                I.src_ny = so.axis[1] / sn;
-                I.src_nz = so.axis[2] / sn;
+                I.src_M = (const double *)sd->M.p + 3 * cp->second.src_k;
             }
             ios.push_back(I);
         }
     }
     p->n_tiles = (int64_t)tiles.size();
     p->n_ios = (int)ios.size();
+    p->n_chunks = (int)chunks.size();
     int rc = dev_alloc(ctx, p->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TileDev));
     if (rc == HG_OK) rc = dev_alloc(ctx, p->ios, std::max<size_t>(1, ios.size()) * sizeof(IoDev));
     if (rc == HG_OK) rc = dev_alloc(ctx, p->adv, std::max<size_t>(1, doms.size()) * 4);
+    if (rc == HG_OK) rc = dev_alloc(ctx, p->chunks, std::max<size_t>(1, chunks.size()) * sizeof(int2));
+    if (rc == HG_OK) rc = dev_alloc(ctx, p->partials, std::max<size_t>(1, chunks.size()) * sizeof(double2));
+    if (rc == HG_OK) rc = dev_alloc(ctx, p->counters, (ios.size() + 1) * sizeof(unsigned));
     if (rc != HG_OK) {
-        dev_free(ctx, p->tiles);
-        dev_free(ctx, p->ios);
-        dev_free(ctx, p->adv);
+        for (DevBuf *b : {&p->tiles, &p->ios, &p->adv, &p->chunks, &p->partials, &p->counters})
+            dev_free(ctx, *b);
         return rc;
     }
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = cudaMemset(p->counters.p, 0, p->counters.bytes);
     if (!tiles.empty()) e = cudaMemcpy(p->tiles.p, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess && !ios.empty()) e = cudaMemcpy(p->ios.p, ios.data(), ios.size() * sizeof(IoDev), cudaMemcpyHostToDevice);
     if (e == cudaSuccess) e = cudaMemcpy(p->adv.p, doms.data(), doms.size() * 4, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess && !chunks.empty())
+        e = cudaMemcpy(p->chunks.p, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) return fail(ctx, HG_ERR_CUDA, "plan upload failed: %s", cudaGetErrorString(e));
     out = p.get();
     ctx->plans[key] = std::move(p);
@@ -951,7 +953,8 @@ cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
                                               (const TileDev *)p->tiles.p, p->n_tiles, (int)off,
                                               step_parity(ctx, mode, off), ctx->stream);
         if (e != cudaSuccess) return e;
-        e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (int)off, ctx->stream);
+        e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (const int2 *)p->chunks.p, p->n_chunks,
+                                (double2 *)p->partials.p, (unsigned *)p->counters.p, (int)off, ctx->stream);
         if (e != cudaSuccess) return e;
     }
     return launch_advance_list((int64_t *)ctx->steps.p, (const int32_t *)p->adv.p, (int)p->doms.size(), k,
@@ -1051,7 +1054,9 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float
         e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
                                   p->n_tiles, (int)j, step_parity(ctx, mode, j), ctx->stream);
         cudaEventRecord(ev[3 * j + 1], ctx->stream);
-        if (e == cudaSuccess) e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (int)j, ctx->stream);
+        if (e == cudaSuccess)
+            e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (const int2 *)p->chunks.p, p->n_chunks,
+                                    (double2 *)p->partials.p, (unsigned *)p->counters.p, (int)j, ctx->stream);
         cudaEventRecord(ev[3 * j + 2], ctx->stream);
     }
     if (e == cudaSuccess)

@@ -45,18 +45,22 @@ struct TileDev {
 struct IoDev {
     const int32_t *slots;     // adjacent-site slots of this iolet, canonical order
     const float4 *bnd;        // owner's per-slot moments
-    const int32_t *src_slots; // coupled source: its slots (or null)
-    const float4 *src_bnd;
+    const double *src_M;      // coupled source iolet's means (or null)
     double *M;                // out: (mean u.n, mean drho, count)
     float *bcv;               // out: boundary value for the next step
     const int64_t *step;      // owner's completed-step counter
     double nx, ny, nz;        // unit outward axis
-    double src_nx, src_ny, src_nz;
     double value, period, factor;
-    int32_t n_slots, src_n_slots;
+    int32_t n_slots;
+    int32_t n_chunks;         // ceil(n_slots / kIoChunk), at least 1
+    int32_t part0;            // first partial of this iolet in the plan's partials array
     int32_t pulse;
     int32_t coupled;
+    int32_t pad;
 };
+
+// Slots reduced by one CTA of the iolet-update kernel.
+constexpr int kIoChunk = 256;
 
 // Launch configuration of the stream-collide kernel.
 struct CollideCfg {
@@ -71,7 +75,10 @@ struct CollideCfg {
 // parity read from the step counters.
 cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                                   int64_t n_tiles, int off, int parity, cudaStream_t st);
-cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, int off, cudaStream_t st);
+// One CTA per (iolet, chunk) in `chunks`; partials: 2 doubles per chunk;
+// counters: n_ios + 1 zeroed unsigned ints (left zeroed on return).
+cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, const int2 *chunks, int n_chunks,
+                                double2 *partials, unsigned *counters, int off, cudaStream_t st);
 cudaError_t launch_advance_list(int64_t *steps_base, const int32_t *idx, int n, int64_t by,
                                 cudaStream_t st);
 // Reconstruct F_t of one domain (device order) and write macroscopic fields

@@ -563,59 +563,80 @@ __device__ __forceinline__ void block_sum2(double &a, double &b) {
     }
 }
 
-constexpr int kIoThreads = 1024;  // fixed: the summation order depends on it
-constexpr int kIoBatch = 4;       // independent loads in flight per thread
-
-// Thread t sums slots t, t + B, t + 2B, ... in that order (B = kIoThreads), then a
-// fixed shuffle tree combines the threads: the result depends only on the list.
-__device__ __forceinline__ void reduce_iolet(const int32_t *slots, const float4 *bnd, int n,
-                                             double nx, double ny, double nz, double &su,
-                                             double &sr) {
-    su = 0.0;
-    sr = 0.0;
-    for (int base = 0; base < n; base += kIoThreads * kIoBatch) {
-        int sl[kIoBatch];
-#pragma unroll
-        for (int b = 0; b < kIoBatch; ++b) {
-            const int j = base + b * kIoThreads + threadIdx.x;
-            sl[b] = j < n ? __ldg(slots + j) : -1;
-        }
-        float4 m[kIoBatch];
-#pragma unroll
-        for (int b = 0; b < kIoBatch; ++b) m[b] = sl[b] >= 0 ? bnd[sl[b]] : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int b = 0; b < kIoBatch; ++b) {
-            if (sl[b] >= 0) {
-                su += (double)m[b].y * nx + (double)m[b].z * ny + (double)m[b].w * nz;
-                sr += (double)m[b].x;
-            }
-        }
+// One CTA per (iolet, chunk of kIoChunk slots): thread t takes slot t of the
+// chunk, a fixed shuffle tree sums the block, the partial goes to
+// partials[part0 + chunk].  The CTA that completes an iolet (atomic ticket, no
+// waiting) sums its partials in chunk order -> M; the CTA that completes the
+// last iolet sets every iolet's boundary value for the next step.  The result
+// depends only on the slot lists, never on scheduling.
+__global__ void __launch_bounds__(kIoChunk) k_iolet_update(const IoDev *__restrict__ ios, int n_ios,
+                                                           const int2 *__restrict__ chunks,
+                                                           double2 *partials, unsigned *counters,
+                                                           int off) {
+    __shared__ int s_last;
+    const int2 ck = chunks[blockIdx.x];
+    const IoDev &I = ios[ck.x];
+    double su = 0.0, sr = 0.0;
+    const int j = ck.y * kIoChunk + threadIdx.x;
+    if (j < I.n_slots) {
+        const float4 m = I.bnd[__ldg(I.slots + j)];
+        su = (double)m.y * I.nx + (double)m.z * I.ny + (double)m.w * I.nz;
+        sr = (double)m.x;
     }
     block_sum2(su, sr);
-}
-
-__global__ void __launch_bounds__(kIoThreads) k_iolet_update(const IoDev *__restrict__ ios, int off) {
-    const IoDev &I = ios[blockIdx.x];
-    double su, sr;
-    reduce_iolet(I.slots, I.bnd, I.n_slots, I.nx, I.ny, I.nz, su, sr);
+    if (threadIdx.x == 0) {
+        partials[I.part0 + ck.y] = make_double2(su, sr);
+        __threadfence();
+        s_last = atomicAdd(&counters[ck.x], 1u) == (unsigned)(I.n_chunks - 1);
+    }
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    __shared__ double2 s_part[kIoChunk];
+    double a = 0.0, b = 0.0;
+    for (int c0 = 0; c0 < I.n_chunks; c0 += kIoChunk) {  // all loads in flight, then an ordered sum
+        const int c = c0 + threadIdx.x;
+        if (c < I.n_chunks) s_part[threadIdx.x] = __ldcg(partials + I.part0 + c);
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            const int m = min(kIoChunk, I.n_chunks - c0);
+            for (int q = 0; q < m; ++q) {
+                a += s_part[q].x;
+                b += s_part[q].y;
+            }
+        }
+        __syncthreads();
+    }
     if (threadIdx.x == 0) {
         const double cnt = (double)I.n_slots;
-        I.M[0] = I.n_slots ? su / cnt : 0.0;
-        I.M[1] = I.n_slots ? sr / cnt : 0.0;
+        I.M[0] = I.n_slots ? a / cnt : 0.0;
+        I.M[1] = I.n_slots ? b / cnt : 0.0;
         I.M[2] = cnt;
+        counters[ck.x] = 0u;
+        __threadfence();
+        s_last = atomicAdd(&counters[n_ios], 1u) == (unsigned)(n_ios - 1);
     }
-    if (I.coupled) {
-        double cu, cr;
-        reduce_iolet(I.src_slots, I.src_bnd, I.src_n_slots, I.src_nx, I.src_ny, I.src_nz, cu, cr);
-        if (threadIdx.x == 0)
-            *I.bcv = (float)(I.factor * (I.src_n_slots ? cu / (double)I.src_n_slots : 0.0));
-    } else if (threadIdx.x == 0) {  // FP64 transcendentals are slow on this part: one thread
-        const double tn = (double)(*I.step + off + 2);  // the next step
-        double p = 1.0;
-        if (I.pulse == 1) p = 0.5 * (1.0 - cos(2.0 * 3.141592653589793 * tn / I.period));
-        else if (I.pulse == 2) p = sin(2.0 * 3.141592653589793 * tn / I.period);
-        *I.bcv = (float)(I.value * p);
+    __syncthreads();
+    if (!s_last) return;
+    __threadfence();
+    for (int k = threadIdx.x; k < n_ios; k += blockDim.x) {
+        const IoDev &J = ios[k];
+        double val;
+        if (J.coupled) {
+            val = J.factor * __ldcg(J.src_M);
+        } else {
+            // phase of the next step in [0, 1): exact remainder first, so the FP64
+            // cosine only ever sees an argument in [0, 2 pi)
+            const double tn = (double)(*J.step + off + 2);
+            const double ph = J.pulse ? fmod(tn, J.period) / J.period : 0.0;
+            double p = 1.0;
+            if (J.pulse == 1) p = 0.5 * (1.0 - cos(2.0 * 3.141592653589793 * ph));
+            else if (J.pulse == 2) p = sin(2.0 * 3.141592653589793 * ph);
+            val = J.value * p;
+        }
+        *J.bcv = (float)val;
     }
+    if (threadIdx.x == 0) counters[n_ios] = 0u;
 }
 
 __global__ void k_advance_list(int64_t *base, const int32_t *idx, int n, int64_t by) {
@@ -794,9 +815,10 @@ cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, con
     return cudaErrorInvalidValue;
 }
 
-cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, int off, cudaStream_t st) {
-    if (n_ios <= 0) return cudaSuccess;
-    k_iolet_update<<<n_ios, kIoThreads, 0, st>>>(ios, off);
+cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, const int2 *chunks, int n_chunks,
+                                double2 *partials, unsigned *counters, int off, cudaStream_t st) {
+    if (n_ios <= 0 || n_chunks <= 0) return cudaSuccess;
+    k_iolet_update<<<n_chunks, kIoChunk, 0, st>>>(ios, n_ios, chunks, partials, counters, off);
     return cudaGetLastError();
 }
 

@@ -287,3 +287,28 @@ def test_variant1_against_oracle(gpu, oracle_mod):
                                      checkpoints=(50, 101), sites_per_thread=2, kernel_variant=1)
         for eu, ep in errs:
             assert eu < TOL["f32"] and ep < TOL["f32"], (scheme, errs)
+
+
+def test_autotune_leaves_state_unchanged(gpu):
+    from paper_2010_04144_gb300.autotune import autotune
+
+    geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
+    for scheme in ("ab", "aa"):
+        ctx = gpu.Context(storage="f32", scheme=scheme)
+        ref = gpu.Context(storage="f32", scheme=scheme)
+        try:
+            d = ctx.domain(geo.xyz, geo.iolets, tau=TAU)
+            r = ref.domain(geo.xyz, geo.iolets, tau=TAU)
+            ctx.step(33)
+            ref.step(33)
+            best, timing = autotune(ctx, use_cache=False)
+            assert best in timing and len(timing) >= 4
+            assert d.step == 33
+            assert np.array_equal(d.state(), r.state())
+            ctx.step(20)
+            ref.step(20)
+            assert np.array_equal(d.state(), r.state())
+            assert np.array_equal(d.iolet_stats(), r.iolet_stats())
+        finally:
+            ctx.close()
+            ref.close()

@@ -1,0 +1,67 @@
+"""Serving on the GPU: a request's result is the same alone and in a mix.
+
+Each domain's arithmetic is independent of the other domains packed into the
+same launches (and the iolet reductions are per iolet in a fixed order), so
+the bar is bit-identity, stricter than the stated tolerance.
+"""
+import numpy as np
+import pytest
+
+from paper_2010_04144_gb300 import serve as SV
+from paper_2010_04144_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+
+class _Clock:
+    def __init__(self, dt=0.01):
+        self.t, self.dt = 0.0, dt
+
+    def __call__(self):
+        self.t += self.dt
+        return self.t
+
+    def sleep(self, s):
+        self.t += s
+
+
+def _tree(seed, depth=3, r=5.0, **kw):
+    return S.tree(S.TreeSpec(depth=depth, root_radius=r, seed=seed), **kw)
+
+
+@pytest.mark.parametrize("storage,scheme", [("f16", "aa"), ("f32", "ab")])
+def test_alone_vs_mixed_bit_identical(gpu, storage, scheme):
+    a = _tree(11, inlet_speed=0.04, period=300.0)
+    steps = 400
+    alone = SV.Server(storage=storage, scheme=scheme, budget_bytes=4e9, chunk_steps=50)
+    try:
+        alone.submit(SV.Job(rid=0, arrival_s=0.0, steps=steps, geoms=[a], want_state=True))
+        clk = _Clock()
+        ref = alone.run(clock=clk, sleep=clk.sleep)[0].result
+    finally:
+        alone.close()
+
+    mix = SV.Server(storage=storage, scheme=scheme, budget_bytes=4e9, chunk_steps=50)
+    try:
+        b = _tree(12, depth=4, r=4.0)
+        art = _tree(13, inlet_speed=0.03)
+        ven = _tree(13, venous=True)
+        u = S.uniform_draws(99, len(ven.iolets))
+        mix.submit(SV.Job(rid=1, arrival_s=0.0, steps=300, geoms=[b]))
+        mix.submit(SV.coupled_job_from_trees(2, 0.0, 250 * 2, art, ven, u))
+        mix.submit(SV.Job(rid=0, arrival_s=0.05, steps=steps, geoms=[a], want_state=True))
+        mix.submit(SV.Job(rid=3, arrival_s=0.1, steps=100, geoms=[_tree(14)]))
+        clk = _Clock()
+        done = {j.rid: j for j in mix.run(clock=clk, sleep=clk.sleep)}
+        assert set(done) == {0, 1, 2, 3}
+        got = done[0].result
+        assert np.array_equal(got["state"][0], ref["state"][0])
+        assert np.array_equal(got["iolet_stats"][0], ref["iolet_stats"][0])
+        assert got["mass"][0] == ref["mass"][0]
+        # the coupled request ran coupled: venous inlets carry nonzero imposed flow
+        assert np.any(done[2].result["iolet_stats"][1][1:, 0] != 0.0)
+        st = mix.stats()
+        assert st["requests"] == 4 and st["aggregate_mflups"] > 0
+        assert mix.in_use == 0
+    finally:
+        mix.close()
