@@ -21,6 +21,7 @@ import os
 DEFAULT_CANDIDATES = (
     (256, 1, 0), (128, 1, 0), (512, 1, 0), (256, 2, 0),
     (128, 1, 1), (128, 2, 1), (256, 2, 1), (64, 2, 1),
+    (128, 2, 2), (256, 2, 2), (256, 1, 2),  # variant 2: AA scheme only
 )
 
 
@@ -73,6 +74,8 @@ def autotune(ctx, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2, use_cache=T
             best = tuple(hit["best"])
             ctx.set_launch(*best)
             return best, {tuple(int(x) for x in k.split("x")): v for k, v in hit["ms"].items()}
+    if ctx.scheme != 1:
+        candidates = [c for c in candidates if c[2] != 2]
     steps += steps & 1  # balance odd and even steps of the AA scheme
     saved = [(d, d.save_state()) for d in ctx.domains]
     timing = {}

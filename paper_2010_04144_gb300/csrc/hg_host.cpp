@@ -275,6 +275,7 @@ struct hg_ctx {
     std::string err;
     std::vector<hg_domain *> doms;  // by index (nullptr = free slot)
     DevBuf dom_table;               // DomDev[capacity]
+    DevBuf errw;                    // device error word (bounded waits that gave up)
     DevBuf steps;                   // int64[capacity]
     int capacity = 0;
     std::map<std::pair<int32_t, int32_t>, CoupleSrc> coupled;  // (dst dom, dst k) -> source
@@ -371,6 +372,7 @@ DomDev make_domdev(hg_ctx *ctx, hg_domain *d) {
     D.bcv = (const float *)d->bcv.p;
     D.io_kind = (const int8_t *)d->io_kind.p;
     D.step = (const int64_t *)ctx->steps.p + d->idx;
+    D.err = (int32_t *)ctx->errw.p;
     D.n = d->n;
     D.np = d->np;
     D.omega = (float)(1.0 / d->tau);
@@ -405,7 +407,8 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     int spt = p->sites_per_thread ? p->sites_per_thread : 1;
     if (block < 32 || block > 512 || block % 32) return HG_ERR_ARG;
     if (spt != 1 && spt != 2 && spt != 4) return HG_ERR_ARG;
-    if (p->kernel_variant < 0 || p->kernel_variant > 1 || (p->kernel_variant == 1 && spt == 4))
+    if (p->kernel_variant < 0 || p->kernel_variant > 2 || (p->kernel_variant >= 1 && spt == 4) ||
+        (p->kernel_variant == 2 && p->scheme != HG_SCHEME_AA))
         return HG_ERR_ARG;
     if ((p->alloc == nullptr) != (p->free == nullptr)) return HG_ERR_ARG;
     std::unique_ptr<hg_ctx> c(new hg_ctx);
@@ -433,11 +436,13 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     c->capacity = 4096;
     int rc = dev_alloc(c.get(), c->dom_table, sizeof(DomDev) * c->capacity);
     if (rc == HG_OK) rc = dev_alloc(c.get(), c->steps, sizeof(int64_t) * c->capacity);
+    if (rc == HG_OK) rc = dev_alloc(c.get(), c->errw, 256);
     if (rc != HG_OK) {
         if (c->own_stream) cudaStreamDestroy(c->stream);
         return rc;
     }
     if (cudaMemsetAsync(c->steps.p, 0, c->steps.bytes, c->stream) != cudaSuccess) return HG_ERR_CUDA;
+    if (cudaMemsetAsync(c->errw.p, 0, c->errw.bytes, c->stream) != cudaSuccess) return HG_ERR_CUDA;
     c->doms.assign(c->capacity, nullptr);
     *out = c.release();
     return HG_OK;
@@ -454,6 +459,7 @@ int hg_ctx_destroy(hg_ctx *ctx) {
     drop_plans(ctx);
     dev_free(ctx, ctx->scratch);
     dev_free(ctx, ctx->dom_table);
+    dev_free(ctx, ctx->errw);
     dev_free(ctx, ctx->steps);
     if (ctx->own_stream) cudaStreamDestroy(ctx->stream);
     delete ctx;
@@ -465,6 +471,12 @@ const char *hg_last_error(hg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null c
 int hg_sync(hg_ctx *ctx) {
     if (!ctx) return HG_ERR_ARG;
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    int32_t e = 0;
+    CU(ctx, cudaMemcpy(&e, ctx->errw.p, sizeof e, cudaMemcpyDeviceToHost));
+    if (e) {
+        CU(ctx, cudaMemset(ctx->errw.p, 0, sizeof e));
+        return fail(ctx, HG_ERR_TIMEOUT, "a bounded device wait gave up (code %d); the state is not trusted", e);
+    }
     return HG_OK;
 }
 
@@ -1088,8 +1100,8 @@ int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) 
     if (!ctx) return HG_ERR_ARG;
     if (block < 32 || block > 512 || block % 32) return fail(ctx, HG_ERR_ARG, "block size must be a multiple of 32 in [32, 512]");
     if (spt != 1 && spt != 2 && spt != 4) return fail(ctx, HG_ERR_ARG, "sites per thread must be 1, 2 or 4");
-    if (variant < 0 || variant > 1 || (variant == 1 && spt == 4))
-        return fail(ctx, HG_ERR_ARG, "kernel variant must be 0, or 1 with 1 or 2 sites per thread");
+    if (variant < 0 || variant > 2 || (variant >= 1 && spt == 4) || (variant == 2 && ctx->scheme != HG_SCHEME_AA))
+        return fail(ctx, HG_ERR_ARG, "kernel variant must be 0, or 1/2 with 1 or 2 sites per thread (2: AA only)");
     if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));

@@ -28,6 +28,7 @@ struct DomDev {
     const float *bcv;         // per iolet: boundary value of the step being run
     const int8_t *io_kind;    // per iolet: 0 pressure, 1 velocity
     const int64_t *step;      // completed steps before the current launch group
+    int32_t *err;             // context error word: set when a bounded device wait gives up
     int64_t n;                // sites
     int64_t np;               // row stride (n padded)
     float omega;              // 1 / tau
@@ -68,7 +69,8 @@ struct CollideCfg {
     int scheme;
     int block;
     int spt;
-    int variant;  // 0 = gathers into registers, 1 = gathers staged by cp.async (spt 1 or 2)
+    int variant;  // 0 = gathers into registers, 1 = gathers staged by cp.async (spt 1 or 2),
+                  // 2 = as 1, and the AA even step moves whole rows with TMA bulk copies
 };
 
 // parity (AA only): 0 = every domain runs an even step, 1 = odd, 2 = per-domain

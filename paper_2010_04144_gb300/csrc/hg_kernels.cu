@@ -485,6 +485,106 @@ __device__ __forceinline__ void tile_aa_even_pairs(const DomDev &D, const TileDe
     }
 }
 
+// ==== TMA bulk-copy AA even step (V = 2) ======================================
+// One thread moves the tile's 19 rows (contiguous segments of the SoA arrays)
+// into shared memory with cp.async.bulk, completion tracked by an mbarrier;
+// every thread collides its sites from shared memory, writes the swapped
+// result back into the same column, and one thread stores the 19 rows with
+// bulk copies.  The wait is bounded: on timeout the context error word is set.
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity) {
+    for (uint32_t it = 0; it < kWaitLimit; ++it)
+        if (mbar_try_wait(bar, parity)) return true;
+    return false;
+}
+__device__ __forceinline__ void bulk_g2s(void *sdst, const void *gsrc, uint32_t bytes, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(sdst)),
+        "l"(gsrc), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+__device__ __forceinline__ void bulk_s2g(void *gdst, const void *ssrc, uint32_t bytes) {
+    asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(gdst), "r"(smem_addr(ssrc)),
+                 "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void bulk_commit_wait_read() {
+    asm volatile("cp.async.bulk.commit_group;\ncp.async.bulk.wait_group.read 0;\n" ::: "memory");
+}
+
+template <int S>
+__device__ __forceinline__ void tile_aa_even_tma(const DomDev &D, const TileDev &tl, uint32_t cap,
+                                                 unsigned char *smem) {
+    using T = typename St<S>::T;
+    constexpr uint32_t E = sizeof(T);
+    T *buf = (T *)D.f[0];
+    const int64_t np = D.np;
+    uint64_t *bar = (uint64_t *)smem;
+    T *rows = (T *)(smem + 16);
+    const uint32_t bytes = ((uint32_t)tl.count * E + 15u) & ~15u;  // padding keeps it inside the row
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_expect_tx(bar, 19u * bytes);
+        for (int I = 0; I < 19; ++I) bulk_g2s(rows + (size_t)I * cap, buf + (int64_t)I * np + tl.start, bytes, bar);
+    }
+    const bool ok = __syncthreads_and(mbar_wait_bounded(bar, 0));
+    if (!ok) {  // never expected: report, let the copies land, leave the tile untouched
+        if (threadIdx.x == 0) atomicExch(D.err, 1);
+        mbar_wait_bounded(bar, 0);
+        return;
+    }
+    for (int r = threadIdx.x; r < tl.count; r += blockDim.x) {
+        const int64_t s = tl.start + r;
+        float g[19];
+        unroll<0, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            g[I] = St<S>::template ld<I>(rows[(size_t)I * cap + r]);
+        });
+        int slot = -1;
+        if ((__ldg(D.iomask + (s >> 5)) >> (s & 31)) & 1u) {
+            unroll<1, 19>([&](auto ic) {
+                constexpr int I = decltype(ic)::v;
+                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * np + s);
+                if (v < -1) g[I] = link_rule<I>(D, v, g[I], slot);
+            });
+        }
+        const float4 m = collide(g, D.omega);
+        unroll<0, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            rows[(size_t)OPP(I) * cap + r] = St<S>::template st<I>(g[I]);
+        });
+        if (slot >= 0) D.bnd[slot] = m;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int I = 0; I < 19; ++I) bulk_s2g(buf + (int64_t)I * np + tl.start, rows + (size_t)I * cap, bytes);
+        bulk_commit_wait_read();
+    }
+}
+
 // PAR selects the AA step kind: 0 = even, 1 = odd, 2 = read from the domain's
 // counter per block (batches whose domains are at different parities).
 template <int S, int SCHEME, int SPT, int PAR, int V>
@@ -494,7 +594,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
     using T = typename St<S>::T;
     __shared__ DomDev D;
     __shared__ int64_t t_now;
-    extern __shared__ uint32_t stage[];
+    extern __shared__ __align__(128) uint32_t stage[];
     const TileDev tl = tiles[blockIdx.x];
     if (threadIdx.x == 0) {
         D = doms[tl.dom];
@@ -502,12 +602,13 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
     }
     __syncthreads();
     const int64_t t = t_now;
-    if constexpr (V == 1) {
+    if constexpr (V >= 1) {
         if constexpr (SCHEME == kAB) {
             tile_ab_async<S, SPT>(D, tl, t, stage);
         } else {
             const bool odd = PAR == 2 ? (t & 1) != 0 : PAR == 1;
             if (odd) tile_aa_odd_async<S, SPT>(D, tl, stage);
+            else if constexpr (V == 2) tile_aa_even_tma<S>(D, tl, (uint32_t)(SPT * blockDim.x), (unsigned char *)stage);
             else tile_aa_even_pairs<S>(D, tl);
         }
     } else {
@@ -761,7 +862,9 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double *parti
 template <int S, int SCHEME, int PAR, int V, int SPT>
 cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                           int64_t n_tiles, int off, cudaStream_t st) {
-    const size_t smem = V == 1 ? (size_t)SPT * 19 * cfg.block * 4 : 0;
+    // V1: cp.async stage of 4-byte words; V2 also holds the even step's 19 rows + mbarrier
+    size_t smem = V >= 1 ? (size_t)SPT * 19 * cfg.block * 4 : 0;
+    if (V == 2) smem += 16;
     auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -778,6 +881,14 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
         switch (cfg.spt) {
             case 1: return launch_sc_one<S, SCHEME, PAR, 1, 1>(cfg, doms, tiles, n_tiles, off, st);
             case 2: return launch_sc_one<S, SCHEME, PAR, 1, 2>(cfg, doms, tiles, n_tiles, off, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (cfg.variant == 2) {
+        if (SCHEME == kAB) return cudaErrorInvalidValue;
+        switch (cfg.spt) {
+            case 1: return launch_sc_one<S, SCHEME, PAR, 2, 1>(cfg, doms, tiles, n_tiles, off, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 2, 2>(cfg, doms, tiles, n_tiles, off, st);
             default: return cudaErrorInvalidValue;
         }
     }

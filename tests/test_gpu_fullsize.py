@@ -1,0 +1,107 @@
+"""Full-size parity on the benchmark workload (~10M-site tree), sampled.
+
+Both sides start from the same seeded state (the input generator's uniform
+perturbation, quantised by this test to the storage type), placed at an odd
+step count so the AA scheme holds it in its scattered layout.  The GPU runs
+one step in the benchmark's launch configuration (autotuned; the tuning cache
+makes it the same choice).  The oracle computes, site by site and from its own
+ordering and neighbour rows, the update of a sample of sites: every site next
+to an iolet, the ragged tail of the site list and seeded random sites.
+Neighbour rows must match bit-exactly, updated distributions to FP32 rounding
+(FP16: storage rounding), iolet means of the step to the same bars.
+"""
+import os
+import sys
+
+import numpy as np
+import pytest
+
+from paper_2010_04144_gb300 import synth as S
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+W = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+
+
+@pytest.fixture(scope="module")
+def bench_case(oracle_mod):
+    sys.path.insert(0, ROOT)
+    import bench
+
+    geo, _ = bench.workload()
+    od = oracle_mod.Domain(geo.xyz, geo.iolets, tau=0.8, with_nbr=False)
+    rng = np.random.default_rng(2024)
+    n = od.n
+    # candidates for iolet adjacency: sites within reach of an opening (oracle's own rows decide)
+    cand = []
+    for io in geo.iolets:
+        c = np.array(io.centre) / 1024.0
+        reach = io.radius / 1024.0 + 3.0
+        cand.append(np.nonzero(((od.xyz - c) ** 2).sum(1) <= reach * reach)[0])
+    cand = np.unique(np.concatenate(cand))
+    crow = od.nbr_rows(od.xyz[cand])
+    adjacent = cand[(crow < -1).any(axis=1)]
+    sample = np.unique(np.concatenate([adjacent, np.arange(max(0, n - 700), n),
+                                       rng.integers(0, n, 20000)]))
+    rows = od.nbr_rows(od.xyz[sample])
+    table = np.full((18, n), -1, np.int32)     # the oracle's own rows at the sampled sites
+    table[:, sample] = rows.T
+    od.nbr = table
+    F0 = S.random_state(n, seed=77, amplitude=2e-3)
+    return geo, od, sample, rows, adjacent, F0
+
+
+def _quantise(F0, storage):
+    if storage == "f32":
+        raw = F0.astype(np.float32)
+        return raw, raw.astype(np.float64)
+    h = (F0 / W[:, None]).astype(np.float16)
+    return h, h.astype(np.float64) * W[:, None]
+
+
+@pytest.mark.parametrize("storage,scheme", [("f32", "ab"), ("f32", "aa"), ("f16", "aa")])
+def test_fullsize_sampled(gpu, oracle_mod, bench_case, storage, scheme):
+    from paper_2010_04144_gb300.autotune import autotune
+
+    geo, od, sample, rows, adjacent, F0 = bench_case
+    raw, F_in = _quantise(F0, storage)
+    t = 37
+    bc = np.array([io.value * oracle_mod.pulse(io.pulse, t + 1, io.period) for io in geo.iolets])
+    ctx = gpu.Context(storage=storage, scheme=scheme)
+    try:
+        d = ctx.domain(geo.xyz, geo.iolets, tau=0.8)
+        autotune(ctx)
+        buf = d.save_state()
+        nio = len(geo.iolets)
+        buf[16:24] = np.frombuffer(np.int64(t).tobytes(), np.uint8)
+        buf[40:40 + 4 * nio] = np.frombuffer(bc.astype(np.float32).tobytes(), np.uint8)
+        buf[40 + 28 * nio:] = np.frombuffer(raw.tobytes(), np.uint8)
+        d.load_state(buf)
+        assert d.step == t
+        assert np.array_equal(d.state_f64(), F_in)          # import into the scheme's layout
+        ctx.step(1)
+        F1 = d.state_f64()[:, sample].T
+        M1 = d.iolet_stats()
+        nbr_gpu = d.neighbours()
+        assert np.array_equal(d.sites(), od.xyz)
+    finally:
+        ctx.close()
+    assert np.array_equal(nbr_gpu[:, sample], rows.T)        # neighbour rows bit-exact
+    out, mom = od.step_sites(F_in, bc, sample)
+    scale = np.abs(F_in).max()
+    tol = {"f32": 2e-6, "f16": 2e-3}[storage]
+    err = np.abs(F1 - out)
+    assert err.max() <= tol * scale, (err.max(), scale)
+    idx = {s: i for i, s in enumerate(sample)}
+    for k, io in enumerate(geo.iolets):
+        sites = [s for s in adjacent if (rows[idx[s]] == -(2 + k)).any()]
+        nh = np.array(io.axis, float) / np.linalg.norm(io.axis)
+        m = mom[[idx[s] for s in sites]]
+        assert M1[k, 2] == len(sites)
+        if sites:
+            ref_un = float(np.mean(m[:, 1:] @ nh))
+            ref_dr = float(np.mean(m[:, 0]))
+            bar = {"f32": 1e-5, "f16": 3e-3}[storage]
+            assert abs(M1[k, 0] - ref_un) <= bar * np.abs(m[:, 1:]).max()
+            assert abs(M1[k, 1] - ref_dr) <= bar * np.abs(m[:, 0]).max()

@@ -256,7 +256,7 @@ def test_errors_are_reported(gpu):
 
 LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128, 2, 1),
             ("aa", 256, 1, 0), ("aa", 128, 4, 0), ("aa", 256, 1, 1), ("aa", 256, 2, 1),
-            ("aa", 64, 2, 1)]
+            ("aa", 64, 2, 1), ("aa", 128, 2, 2), ("aa", 256, 1, 2), ("aa", 64, 2, 2)]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16"])
