@@ -479,7 +479,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="hemegb", choices=["hemegb", "reference"])
     ap.add_argument("--scale", type=float, default=1.71)
-    ap.add_argument("--variants", default="f32:aa,f32:ab,f16:aa,bf16:aa")
+    ap.add_argument("--variants", default="f32:ab,f32:aa,f16:ab,f16:aa,bf16:aa")
     ap.add_argument("--headline", default="f32:best")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve"])

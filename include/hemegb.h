@@ -150,7 +150,7 @@ int hg_sync(hg_ctx *ctx);
 
 /* Build a domain from fluid voxels (Section 2.2: sparse geometry, only fluid
  * sites stored).  xyz: n_fluid x 3 int32 lattice coordinates, any order, no
- * duplicates, each in [0, 2^21).  iolets: n_iolets descriptors (<= 256).
+ * duplicates, each in [0, 2^21).  iolets: n_iolets descriptors (<= 4096).
  * Builds the canonical site order and neighbour table, classifies iolet links,
  * uploads everything and initialises the rest state f~ = 0 at step 0.
  * Errors: HG_ERR_ARG (range, duplicate, too many iolets, tau <= 0.5),

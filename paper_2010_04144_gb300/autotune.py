@@ -22,6 +22,7 @@ DEFAULT_CANDIDATES = (
     (256, 1, 0), (128, 1, 0), (512, 1, 0), (256, 2, 0),
     (128, 1, 1), (128, 2, 1), (256, 2, 1), (64, 2, 1),
     (128, 2, 2), (256, 2, 2), (256, 1, 2),  # variant 2: AA scheme only
+    (256, 1, 3), (128, 1, 3), (256, 2, 3),
 )
 
 

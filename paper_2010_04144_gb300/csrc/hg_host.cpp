@@ -295,7 +295,9 @@ struct hg_domain {
     std::vector<int32_t> xyz;           // canonical coordinates
     std::vector<hg_iolet> io;
     std::vector<int32_t> io_ptr;        // CSR over slots per iolet
-    DevBuf f[2], nbr, iomask, bnd, coef, bcv, io_kind, M, slots;
+    DevBuf f[2], nbr, iomask, ioprefix, io_codes, bnd, coef, bcv, io_kind, M, slots;
+    std::vector<int32_t> io_codes_host;  // per slot x 18, canonical codes
+    std::vector<int32_t> slot_of_site;   // canonical site -> slot or -1
     int64_t bytes = 0;
 };
 
@@ -367,6 +369,8 @@ DomDev make_domdev(hg_ctx *ctx, hg_domain *d) {
     D.f[1] = d->f[1].p;
     D.nbr = (const int32_t *)d->nbr.p;
     D.iomask = (const uint32_t *)d->iomask.p;
+    D.ioprefix = (const int32_t *)d->ioprefix.p;
+    D.io_codes = (const int32_t *)d->io_codes.p;
     D.bnd = (float4 *)d->bnd.p;
     D.coef = (const float *)d->coef.p;
     D.bcv = (const float *)d->bcv.p;
@@ -407,7 +411,8 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     int spt = p->sites_per_thread ? p->sites_per_thread : 1;
     if (block < 32 || block > 512 || block % 32) return HG_ERR_ARG;
     if (spt != 1 && spt != 2 && spt != 4) return HG_ERR_ARG;
-    if (p->kernel_variant < 0 || p->kernel_variant > 2 || (p->kernel_variant >= 1 && spt == 4) ||
+    if (p->kernel_variant < 0 || p->kernel_variant > 3 ||
+        ((p->kernel_variant == 1 || p->kernel_variant == 2) && spt == 4) ||
         (p->kernel_variant == 2 && p->scheme != HG_SCHEME_AA))
         return HG_ERR_ARG;
     if ((p->alloc == nullptr) != (p->free == nullptr)) return HG_ERR_ARG;
@@ -569,40 +574,45 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     std::vector<int64_t> per_io(nio + 1, 0);
     for (int64_t s = 0; s < n; ++s) {
         bool adj = false;
-        uint8_t seen[kMaxIolets / 8] = {0};
+        int seen[18], n_seen = 0;  // distinct iolets touched by this site
         for (int i = 0; i < 18; ++i) {
             const int32_t v = nbr[(size_t)i * np + s];
             if (v < -1) {
                 adj = true;
                 const int k = -v - 2;
-                if (!(seen[k >> 3] & (1 << (k & 7)))) {
-                    seen[k >> 3] |= 1 << (k & 7);
+                bool dup = false;
+                for (int q = 0; q < n_seen; ++q) dup = dup || seen[q] == k;
+                if (!dup) {
+                    seen[n_seen++] = k;
                     per_io[k + 1]++;
                 }
             }
         }
         if (adj) slot_of[s] = (int32_t)n_adj++;
     }
-    if (n_adj >= (1 << 22)) return fail(ctx, HG_ERR_ARG, "too many sites next to iolets");
     d->n_adj = n_adj;
     for (int k = 0; k < nio; ++k) per_io[k + 1] += per_io[k];
     d->io_ptr.assign(per_io.begin(), per_io.end());
     std::vector<int32_t> slots(std::max<int64_t>(1, per_io[nio]));
     std::vector<float> coef((size_t)std::max<int64_t>(1, n_adj) * 18, 0.0f);
     std::vector<uint32_t> mask((size_t)(np / 32), 0u);
+    std::vector<int32_t> codes((size_t)std::max<int64_t>(1, n_adj) * 18, -1);
     {
         std::vector<int64_t> fill(per_io.begin(), per_io.end() - 1);
         for (int64_t s = 0; s < n; ++s) {
             const int32_t sl = slot_of[s];
             if (sl < 0) continue;
             mask[s >> 5] |= 1u << (s & 31);
-            uint8_t seen[kMaxIolets / 8] = {0};
+            int seen[18], n_seen = 0;
+            for (int i = 1; i < 19; ++i) codes[(size_t)sl * 18 + (i - 1)] = nbr[(size_t)(i - 1) * np + s];
             for (int i = 1; i < 19; ++i) {
-                int32_t &v = nbr[(size_t)(i - 1) * np + s];
+                const int32_t v = nbr[(size_t)(i - 1) * np + s];
                 if (v >= -1) continue;
                 const int k = -v - 2;
-                if (!(seen[k >> 3] & (1 << (k & 7)))) {
-                    seen[k >> 3] |= 1 << (k & 7);
+                bool dup = false;
+                for (int q = 0; q < n_seen; ++q) dup = dup || seen[q] == k;
+                if (!dup) {
+                    seen[n_seen++] = k;
                     slots[fill[k]++] = sl;
                 }
                 const hg_iolet &io = iolets[k];
@@ -627,12 +637,36 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
                         phi = r > 0 ? std::max(0.0, 1.0 - p2 / (r * r)) : 0.0;
                     }
                     const double cdot = -(kC[i][0] * ah[0] + kC[i][1] * ah[1] + kC[i][2] * ah[2]);
-                    coef[(size_t)sl * 18 + (i - 1)] = (float)(6.0 * wgt(i) * cdot * phi);
+                    // 16-bit storage holds f~/w and collides on it: the coefficient drops w_i
+                    const double wi = ctx->storage == HG_STORE_F32 ? wgt(i) : 1.0;
+                    coef[(size_t)sl * 18 + (i - 1)] = (float)(6.0 * wi * cdot * phi);
                 }
-                v = -(2 + k + 256 * sl);  // device code carries the slot
             }
         }
     }
+    // per-32-site prefix counts of flagged sites: slot = rank of the site's flag
+    std::vector<int32_t> prefix(mask.size(), 0);
+    {
+        int32_t acc = 0;
+        for (size_t w = 0; w < mask.size(); ++w) {
+            prefix[w] = acc;
+            acc += __builtin_popcount(mask[w]);
+        }
+    }
+    // virtual indices for every non-fluid link (walls and iolet links alike)
+    const bool aa = ctx->scheme == HG_SCHEME_AA;
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s)
+            for (int i = 1; i < 19; ++i) {
+                int32_t &v = nbr[(size_t)(i - 1) * np + s];
+                if (v >= 0) continue;
+                const int opp = (i & 1) ? i + 1 : i - 1;
+                const int64_t d = aa ? (int64_t)(i - opp) : (int64_t)(opp - i);
+                v = (int32_t)(s + d * np);
+            }
+    });
+    d->io_codes_host = codes;
+    d->slot_of_site = slot_of;
 
     // --- device buffers
     hg_ctx *c = ctx;
@@ -646,6 +680,8 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     if (ctx->scheme == HG_SCHEME_AB) A(d->f[1], 19 * (size_t)np * eb);
     A(d->nbr, 18 * (size_t)np * 4);
     A(d->iomask, (size_t)np / 8);
+    A(d->ioprefix, (size_t)np / 8);
+    A(d->io_codes, codes.size() * 4);
     A(d->bnd, (size_t)std::max<int64_t>(1, n_adj) * 16);
     A(d->coef, coef.size() * 4);
     A(d->bcv, (size_t)std::max(1, nio) * 4);
@@ -653,16 +689,16 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     A(d->M, (size_t)std::max(1, nio) * 24);
     A(d->slots, slots.size() * 4);
     auto cleanup = [&] {
-        DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->bnd, &d->coef,
-                        &d->bcv, &d->io_kind, &d->M, &d->slots};
+        DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
+                        &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots};
         for (DevBuf *b : bs) dev_free(c, *b);
     };
     if (rc != HG_OK) {
         cleanup();
         return rc;
     }
-    for (DevBuf *b : {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->bnd, &d->coef, &d->bcv,
-                      &d->io_kind, &d->M, &d->slots})
+    for (DevBuf *b : {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
+                      &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots})
         d->bytes += (int64_t)b->bytes;
     std::vector<float> bcv(std::max(1, nio), 0.0f);
     std::vector<int8_t> kinds(std::max(1, nio), 0);
@@ -676,6 +712,8 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     };
     H2D(d->nbr, nbr.data(), nbr.size() * 4);
     H2D(d->iomask, mask.data(), mask.size() * 4);
+    H2D(d->ioprefix, prefix.data(), prefix.size() * 4);
+    H2D(d->io_codes, codes.data(), codes.size() * 4);
     H2D(d->coef, coef.data(), coef.size() * 4);
     H2D(d->bcv, bcv.data(), bcv.size() * 4);
     H2D(d->io_kind, kinds.data(), kinds.size());
@@ -707,8 +745,8 @@ int hg_domain_destroy(hg_domain *d) {
         if (it->first.first == d->idx || it->second.src_dom == d->idx) it = ctx->coupled.erase(it);
         else ++it;
     }
-    DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->bnd, &d->coef,
-                    &d->bcv, &d->io_kind, &d->M, &d->slots};
+    DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
+                    &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots};
     for (DevBuf *b : bs) dev_free(ctx, *b);
     ctx->doms[d->idx] = nullptr;
     delete d;
@@ -740,10 +778,14 @@ int hg_domain_neighbours(hg_domain *d, int32_t *nbr_out) {
     for (int i = 0; i < 18; ++i)
         CU(ctx, cudaMemcpy(nbr_out + (size_t)i * d->n, (const int32_t *)d->nbr.p + (size_t)i * d->np,
                            sizeof(int32_t) * d->n, cudaMemcpyDeviceToHost));
-    for (int64_t j = 0; j < 18 * d->n; ++j) {
-        const int32_t v = nbr_out[j];
-        if (v < -1) nbr_out[j] = -(2 + ((-v - 2) & (kMaxIolets - 1)));
-    }
+    // virtual indices (outside [0, n)) mark non-fluid links: wall, or the iolet code of the slot
+    for (int i = 0; i < 18; ++i)
+        for (int64_t s = 0; s < d->n; ++s) {
+            int32_t &v = nbr_out[(size_t)i * d->n + s];
+            if (v >= 0 && v < d->n) continue;
+            const int32_t sl = d->slot_of_site[s];
+            v = sl >= 0 ? d->io_codes_host[(size_t)sl * 18 + i] : -1;
+        }
     return HG_OK;
 }
 
@@ -1100,8 +1142,9 @@ int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) 
     if (!ctx) return HG_ERR_ARG;
     if (block < 32 || block > 512 || block % 32) return fail(ctx, HG_ERR_ARG, "block size must be a multiple of 32 in [32, 512]");
     if (spt != 1 && spt != 2 && spt != 4) return fail(ctx, HG_ERR_ARG, "sites per thread must be 1, 2 or 4");
-    if (variant < 0 || variant > 2 || (variant >= 1 && spt == 4) || (variant == 2 && ctx->scheme != HG_SCHEME_AA))
-        return fail(ctx, HG_ERR_ARG, "kernel variant must be 0, or 1/2 with 1 or 2 sites per thread (2: AA only)");
+    if (variant < 0 || variant > 3 || ((variant == 1 || variant == 2) && spt == 4) ||
+        (variant == 2 && ctx->scheme != HG_SCHEME_AA))
+        return fail(ctx, HG_ERR_ARG, "kernel variant must be 0 or 3, or 1/2 with 1 or 2 sites per thread (2: AA only)");
     if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));

@@ -7,13 +7,14 @@
 
 namespace hg {
 
-// Device encoding of a non-fluid link in the neighbour table:
-//   -1                      wall
-//   -(2 + k + 256 * slot)   opening of iolet k (k < 256); `slot` is the
-//                           site's index in the domain's list of sites next
-//                           to any iolet (canonical order).
-// Fluid links hold the device index of the pull source.
-constexpr int kMaxIolets = 256;
+// Device neighbour table: entry i-1 of site s holds the device index of the
+// pull source when it is fluid, else a virtual index chosen so the scheme's
+// gather address lands on the site's own opposite slot (bounce-back):
+//   A/B:  s + (opp(i) - i) * np      (src row i  + v  ==  row opp(i) + s)
+//   AA:   s + (i - opp(i)) * np      (buf row opp(i) + v  ==  row i + s)
+// Virtual indices lie outside [0, n).  Links into iolet openings are told apart
+// through iomask / ioprefix / io_codes (canonical codes per boundary slot).
+constexpr int kMaxIolets = 4096;
 
 enum Storage : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
 enum Scheme : int { kAB = 0, kAA = 1 };
@@ -23,6 +24,8 @@ struct DomDev {
     void *f[2];               // distributions, SoA [19][np]; AA uses f[0] only
     const int32_t *nbr;       // [18][np] device codes
     const uint32_t *iomask;   // bit s: site s has an iolet link
+    const int32_t *ioprefix;  // per 32-site word: flagged sites before it (slot = rank of the flag)
+    const int32_t *io_codes;  // per slot x 18: canonical codes (-1 wall, -(2+k) iolet, >= 0 fluid)
     float4 *bnd;              // per adjacent slot: (drho, ux, uy, uz) of the step's G_t
     const float *coef;        // per adjacent slot x 18: velocity-link coefficient 6 w_i c_i.(-a) phi
     const float *bcv;         // per iolet: boundary value of the step being run

@@ -17,6 +17,12 @@
 //
 // The step parity is read from a device counter, so one captured CUDA graph
 // replays any number of times without re-recording kernel arguments.
+//
+// Neighbour table on the device: entry i-1 of site s is the index of the pull
+// source x_s - c_i when it is fluid, else a virtual index s + d*np (d = +-1)
+// chosen so that the scheme's usual address formula reaches the site's own
+// opposite slot -- the bounce-back value -- with no branch.  Links into iolet
+// openings are fixed up on a rare path (iomask, ioprefix, io_codes).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -44,29 +50,38 @@ __host__ __device__ constexpr int OPP(int i) { return i == 0 ? 0 : ((i & 1) ? i 
 __host__ __device__ constexpr float W(int i) {
     return i == 0 ? (1.0f / 3.0f) : (i <= 6 ? (1.0f / 18.0f) : (1.0f / 36.0f));
 }
-__host__ __device__ constexpr float INVW(int i) { return i == 0 ? 3.0f : (i <= 6 ? 18.0f : 36.0f); }
 __host__ __device__ constexpr double WD(int i) {
     return i == 0 ? (1.0 / 3.0) : (i <= 6 ? (1.0 / 18.0) : (1.0 / 36.0));
 }
 
 // ---- storage traits ----
+// ld/st convert between storage and the collision variable: FP32 stores f~ and
+// collides on f~; FP16/BF16 store h = f~/w (avoids subnormals) and collide on h
+// directly (collide_scaled), so no per-value scaling is executed.  phys gives
+// the physical deviation f~ for read-back.
 template <int S> struct St;
 template <> struct St<kF32> {
     using T = float;
+    static constexpr bool kScaled = false;
     template <int I> static __device__ __forceinline__ float ld(T v) { return v; }
     template <int I> static __device__ __forceinline__ T st(float v) { return v; }
+    template <int I> static __device__ __forceinline__ float phys(T v) { return v; }
     static __device__ __forceinline__ double ldd(T v, int) { return (double)v; }
 };
 template <> struct St<kF16> {
     using T = __half;
-    template <int I> static __device__ __forceinline__ float ld(T v) { return __half2float(v) * W(I); }
-    template <int I> static __device__ __forceinline__ T st(float v) { return __float2half_rn(v * INVW(I)); }
+    static constexpr bool kScaled = true;
+    template <int I> static __device__ __forceinline__ float ld(T v) { return __half2float(v); }
+    template <int I> static __device__ __forceinline__ T st(float v) { return __float2half_rn(v); }
+    template <int I> static __device__ __forceinline__ float phys(T v) { return __half2float(v) * W(I); }
     static __device__ __forceinline__ double ldd(T v, int i) { return (double)__half2float(v) * WD(i); }
 };
 template <> struct St<kBF16> {
     using T = __nv_bfloat16;
-    template <int I> static __device__ __forceinline__ float ld(T v) { return __bfloat162float(v) * W(I); }
-    template <int I> static __device__ __forceinline__ T st(float v) { return __float2bfloat16_rn(v * INVW(I)); }
+    static constexpr bool kScaled = true;
+    template <int I> static __device__ __forceinline__ float ld(T v) { return __bfloat162float(v); }
+    template <int I> static __device__ __forceinline__ T st(float v) { return __float2bfloat16_rn(v); }
+    template <int I> static __device__ __forceinline__ float phys(T v) { return __bfloat162float(v) * W(I); }
     static __device__ __forceinline__ double ldd(T v, int i) { return (double)__bfloat162float(v) * WD(i); }
 };
 
@@ -78,57 +93,110 @@ template <int B, int E, typename F> __device__ __forceinline__ void unroll(F &&f
     }
 }
 
-// Boundary rule for a non-fluid link in direction I whose device code is v < 0;
-// raw = the site's own post-collision value leaving towards x - c_I (direction opp(I)).
-template <int I>
-__device__ __forceinline__ float link_rule(const DomDev &D, int32_t v, float raw, int &slot) {
-    if (v == -1) return raw;  // half-way bounce-back
-    const int c = -v - 2;
-    const int k = c & (kMaxIolets - 1);
-    slot = c >> 8;
+// Iolet rule for link I of a site next to iolet k (boundary slot `slot`); raw =
+// the site's own post-collision value leaving towards x - c_I (direction opp(I)),
+// in the collision variable.  Scaled storage (h = f~/w) drops the w_I factors
+// (w_I = w_opp(I)); its velocity coefficients are stored divided by w_I.
+template <int I, bool SC>
+__device__ __forceinline__ float iolet_rule(const DomDev &D, int k, int slot, float raw) {
     const float val = D.bcv[k];
-    if (D.io_kind[k] == 0) return -raw + 2.0f * W(I) * val;  // anti-bounce-back, drho_k
-    return raw + val * D.coef[(int64_t)slot * 18 + (I - 1)];  // moving wall, u_w = U phi (-a)
+    if (D.io_kind[k] == 0) return -raw + (SC ? 2.0f : 2.0f * W(I)) * val;  // anti-bounce-back
+    return raw + val * D.coef[(int64_t)slot * 18 + (I - 1)];              // moving wall
 }
 
 // LBGK collision in deviation form, in place on g[19]; returns (drho, u).
-__device__ __forceinline__ float4 collide(float g[19], float omega) {
-    float drho = 0.f;
-#pragma unroll
-    for (int i = 0; i < 19; ++i) drho += g[i];
-    const float d12 = g[1] - g[2], d34 = g[3] - g[4], d56 = g[5] - g[6];
-    const float d78 = g[7] - g[8], d910 = g[9] - g[10], d1112 = g[11] - g[12];
-    const float d1314 = g[13] - g[14], d1516 = g[15] - g[16], d1718 = g[17] - g[18];
-    const float jx = d12 + d78 + d910 + d1112 + d1314;
-    const float jy = d34 + d78 - d910 + d1516 + d1718;
-    const float jz = d56 + d1112 - d1314 + d1516 - d1718;
-    const float rho = 1.0f + drho;
-    const float inv = 1.0f / rho;
-    const float ux = jx * inv, uy = jy * inv, uz = jz * inv;
-    const float usq = ux * ux + uy * uy + uz * uz;
-    const float base = drho - 1.5f * rho * usq;
-    const float r45 = 4.5f * rho, r3 = 3.0f * rho;
-    g[0] += omega * (W(0) * base - g[0]);
+// Every product and sum is written with explicit rounding intrinsics (__fmul_rn,
+// __fadd_rn, __fmaf_rn), so the compiler cannot contract them differently in the
+// different kernels that inline this: all variants produce the same bits.
+#define HG_MUL __fmul_rn
+#define HG_ADD __fadd_rn
+#define HG_SUB __fsub_rn
+#define HG_FMA __fmaf_rn
+
+__device__ __forceinline__ void relax_pairs(float g[19], float omega, float base, float rho,
+                                            float ux, float uy, float uz, float w1, float w2) {
+    const float r45 = HG_MUL(4.5f, rho), r3 = HG_MUL(3.0f, rho);
     auto pair = [&](int a, int b, float w, float cu) {
-        const float sym = w * (base + r45 * cu * cu);
-        const float asym = w * r3 * cu;
-        g[a] += omega * (sym + asym - g[a]);
-        g[b] += omega * (sym - asym - g[b]);
+        const float q = HG_FMA(HG_MUL(r45, cu), cu, base);    // base + 4.5 rho cu^2
+        const float sym = HG_MUL(w, q);
+        const float asym = HG_MUL(w, HG_MUL(r3, cu));
+        g[a] = HG_FMA(omega, HG_SUB(HG_ADD(sym, asym), g[a]), g[a]);
+        g[b] = HG_FMA(omega, HG_SUB(HG_SUB(sym, asym), g[b]), g[b]);
     };
-    pair(1, 2, W(1), ux);
-    pair(3, 4, W(3), uy);
-    pair(5, 6, W(5), uz);
-    pair(7, 8, W(7), ux + uy);
-    pair(9, 10, W(9), ux - uy);
-    pair(11, 12, W(11), ux + uz);
-    pair(13, 14, W(13), ux - uz);
-    pair(15, 16, W(15), uy + uz);
-    pair(17, 18, W(17), uy - uz);
-    return make_float4(drho, ux, uy, uz);
+    pair(1, 2, w1, ux);
+    pair(3, 4, w1, uy);
+    pair(5, 6, w1, uz);
+    pair(7, 8, w2, HG_ADD(ux, uy));
+    pair(9, 10, w2, HG_SUB(ux, uy));
+    pair(11, 12, w2, HG_ADD(ux, uz));
+    pair(13, 14, w2, HG_SUB(ux, uz));
+    pair(15, 16, w2, HG_ADD(uy, uz));
+    pair(17, 18, w2, HG_SUB(uy, uz));
 }
 
-// Read-only (non-coherent) loads; 16-bit types go through __ldg on their bit
-// pattern so the compiler can still schedule them freely.
+struct Moments {
+    float drho, ux, uy, uz, rho, base;
+};
+
+// u, rho and the equilibrium's isotropic part from drho and j.
+__device__ __forceinline__ Moments finish_moments(float drho, float jx, float jy, float jz) {
+    Moments m;
+    m.drho = drho;
+    m.rho = HG_ADD(1.0f, drho);
+    const float inv = __frcp_rn(m.rho);
+    m.ux = HG_MUL(jx, inv);
+    m.uy = HG_MUL(jy, inv);
+    m.uz = HG_MUL(jz, inv);
+    const float usq = HG_FMA(m.ux, m.ux, HG_FMA(m.uy, m.uy, HG_MUL(m.uz, m.uz)));
+    m.base = HG_FMA(HG_MUL(-1.5f, m.rho), usq, drho);       // drho - 1.5 rho u.u
+    return m;
+}
+
+__device__ __forceinline__ float4 collide(float g[19], float omega) {
+    float drho = g[0];
+#pragma unroll
+    for (int i = 1; i < 19; ++i) drho = HG_ADD(drho, g[i]);
+    const float d12 = HG_SUB(g[1], g[2]), d34 = HG_SUB(g[3], g[4]), d56 = HG_SUB(g[5], g[6]);
+    const float d78 = HG_SUB(g[7], g[8]), d910 = HG_SUB(g[9], g[10]), d1112 = HG_SUB(g[11], g[12]);
+    const float d1314 = HG_SUB(g[13], g[14]), d1516 = HG_SUB(g[15], g[16]), d1718 = HG_SUB(g[17], g[18]);
+    const float jx = HG_ADD(HG_ADD(HG_ADD(d12, d78), HG_ADD(d910, d1112)), d1314);
+    const float jy = HG_ADD(HG_ADD(HG_SUB(HG_ADD(d34, d78), d910), d1516), d1718);
+    const float jz = HG_SUB(HG_ADD(HG_SUB(HG_ADD(d56, d1112), d1314), d1516), d1718);
+    const Moments m = finish_moments(drho, jx, jy, jz);
+    g[0] = HG_FMA(omega, HG_SUB(HG_MUL(W(0), m.base), g[0]), g[0]);
+    relax_pairs(g, omega, m.base, m.rho, m.ux, m.uy, m.uz, W(1), W(7));
+    return make_float4(m.drho, m.ux, m.uy, m.uz);
+}
+
+// The same collision in the scaled variable h_i = f~_i / w_i (16-bit storage):
+// moments weight h by w, the equilibrium h~eq_i = drho + rho (3 c.u + 4.5 (c.u)^2
+// - 1.5 u.u) carries no w.
+__device__ __forceinline__ float4 collide_scaled(float g[19], float omega) {
+    const float sa = HG_ADD(HG_ADD(HG_ADD(g[1], g[2]), HG_ADD(g[3], g[4])), HG_ADD(g[5], g[6]));
+    const float sd = HG_ADD(HG_ADD(HG_ADD(HG_ADD(g[7], g[8]), HG_ADD(g[9], g[10])),
+                                   HG_ADD(HG_ADD(g[11], g[12]), HG_ADD(g[13], g[14]))),
+                            HG_ADD(HG_ADD(g[15], g[16]), HG_ADD(g[17], g[18])));
+    const float drho = HG_FMA(W(0), g[0], HG_FMA(W(1), sa, HG_MUL(W(7), sd)));
+    const float d12 = HG_SUB(g[1], g[2]), d34 = HG_SUB(g[3], g[4]), d56 = HG_SUB(g[5], g[6]);
+    const float d78 = HG_SUB(g[7], g[8]), d910 = HG_SUB(g[9], g[10]), d1112 = HG_SUB(g[11], g[12]);
+    const float d1314 = HG_SUB(g[13], g[14]), d1516 = HG_SUB(g[15], g[16]), d1718 = HG_SUB(g[17], g[18]);
+    const float ex = HG_ADD(HG_ADD(d78, d910), HG_ADD(d1112, d1314));
+    const float ey = HG_ADD(HG_SUB(d78, d910), HG_ADD(d1516, d1718));
+    const float ez = HG_ADD(HG_SUB(d1112, d1314), HG_SUB(d1516, d1718));
+    const float jx = HG_FMA(W(1), d12, HG_MUL(W(7), ex));
+    const float jy = HG_FMA(W(1), d34, HG_MUL(W(7), ey));
+    const float jz = HG_FMA(W(1), d56, HG_MUL(W(7), ez));
+    const Moments m = finish_moments(drho, jx, jy, jz);
+    g[0] = HG_FMA(omega, HG_SUB(m.base, g[0]), g[0]);
+    relax_pairs(g, omega, m.base, m.rho, m.ux, m.uy, m.uz, 1.0f, 1.0f);
+    return make_float4(m.drho, m.ux, m.uy, m.uz);
+}
+
+template <int S> __device__ __forceinline__ float4 collide_s(float g[19], float omega) {
+    if constexpr (St<S>::kScaled) return collide_scaled(g, omega);
+    else return collide(g, omega);
+}
+
 template <typename T> __device__ __forceinline__ T ldg_nc(const T *p) { return __ldg(p); }
 template <> __device__ __forceinline__ __half ldg_nc(const __half *p) {
     return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p)));
@@ -137,29 +205,111 @@ template <> __device__ __forceinline__ __nv_bfloat16 ldg_nc(const __nv_bfloat16 
     return __ushort_as_bfloat16(__ldg(reinterpret_cast<const unsigned short *>(p)));
 }
 
-// ---- A/B pull: F_{t-1} in src, F_t to dst ----
+// Loads carrying an L2 prefetch-size hint (256 B): a miss fetches the whole
+// 256-byte span, which neighbouring warps' gathers then hit.  ld_ro: read-only
+// data (non-coherent path); ld_rw: data this kernel also writes (AA).
+template <typename T> struct HintLd;
+template <> struct HintLd<float> {
+    static __device__ __forceinline__ float ro(const float *p) {
+        float v;
+        asm("ld.global.nc.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p));
+        return v;
+    }
+    static __device__ __forceinline__ float rw(const float *p) {
+        float v;
+        asm("ld.global.L2::256B.f32 %0, [%1];" : "=f"(v) : "l"(p) : "memory");
+        return v;
+    }
+};
+template <> struct HintLd<int32_t> {
+    static __device__ __forceinline__ int32_t ro(const int32_t *p) {
+        int32_t v;
+        asm("ld.global.nc.L2::256B.s32 %0, [%1];" : "=r"(v) : "l"(p));
+        return v;
+    }
+};
+template <typename H> struct HintLd16 {
+    static __device__ __forceinline__ H ro(const H *p) {
+        unsigned short v;
+        asm("ld.global.nc.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p));
+        return *reinterpret_cast<H *>(&v);
+    }
+    static __device__ __forceinline__ H rw(const H *p) {
+        unsigned short v;
+        asm("ld.global.L2::256B.b16 %0, [%1];" : "=h"(v) : "l"(p) : "memory");
+        return *reinterpret_cast<H *>(&v);
+    }
+};
+template <> struct HintLd<__half> : HintLd16<__half> {};
+template <> struct HintLd<__nv_bfloat16> : HintLd16<__nv_bfloat16> {};
+
+template <bool HINT, typename T> __device__ __forceinline__ T load_ro(const T *p) {
+    if constexpr (HINT) return HintLd<T>::ro(p);
+    else return ldg_nc(p);
+}
+template <bool HINT> __device__ __forceinline__ int32_t load_nbr(const int32_t *p) {
+    if constexpr (HINT) return HintLd<int32_t>::ro(p);
+    else return __ldg(p);
+}
+template <bool HINT, typename T> __device__ __forceinline__ T load_rw(const T *p) {
+    if constexpr (HINT) return HintLd<T>::rw(p);
+    else return *p;
+}
+
+// ---- sites next to an iolet (rare path) ----
+// Neighbour table entries of non-fluid links hold a virtual index that makes
+// the ordinary address formula land on the site's own opposite slot, so a wall
+// needs no code at all.  Sites with a link into an iolet opening are flagged in
+// `iomask`; their slot is the rank of the flag (per-32-site prefix + popcount)
+// and their canonical link codes sit in io_codes[slot][18].
+__device__ __forceinline__ bool site_flag(const DomDev &D, int64_t s, uint32_t &word) {
+    word = __ldg(D.iomask + (s >> 5));
+    return (word >> (s & 31)) & 1u;
+}
+__device__ __forceinline__ int site_slot(const DomDev &D, int64_t s, uint32_t word) {
+    return __ldg(D.ioprefix + (s >> 5)) + __popc(word & ((1u << (s & 31)) - 1u));
+}
 template <int S>
+__device__ __forceinline__ void apply_iolet_links(const DomDev &D, int slot, float g[19]) {
+    const int32_t *codes = D.io_codes + (int64_t)slot * 18;
+    unroll<1, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        const int32_t c = __ldg(codes + (I - 1));
+        if (c < -1) g[I] = iolet_rule<I, St<S>::kScaled>(D, -c - 2, slot, g[I]);
+    });
+}
+template <int S>
+__device__ __forceinline__ int iolet_fixup(const DomDev &D, int64_t s, float g[19]) {
+    uint32_t word;
+    if (!site_flag(D, s, word)) return -1;
+    const int slot = site_slot(D, s, word);
+    apply_iolet_links<S>(D, slot, g);
+    return slot;
+}
+
+template <typename T> __device__ __forceinline__ T *opaque(T *p) {
+    T *q;
+    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
+    return q;
+}
+
+// ---- A/B pull: F_{t-1} in src, F_t to dst ----
+template <int S, bool HINT = false>
 __device__ __forceinline__ void site_ab(const DomDev &D, const typename St<S>::T *__restrict__ src,
                                         typename St<S>::T *__restrict__ dst, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
     int32_t nb[18];
 #pragma unroll
-    for (int i = 0; i < 18; ++i) nb[i] = __ldg(D.nbr + (int64_t)i * np + s);
+    for (int i = 0; i < 18; ++i) nb[i] = load_nbr<HINT>(D.nbr + (int64_t)i * np + s);
     float g[19];
-    g[0] = Tr::template ld<0>(ldg_nc(src + s));
-    int slot = -1;
-    unroll<1, 19>([&](auto ic) {
+    g[0] = Tr::template ld<0>(load_ro<HINT>(src + s));
+    unroll<1, 19>([&](auto ic) {  // virtual indices: walls read their own opposite value
         constexpr int I = decltype(ic)::v;
-        const int32_t v = nb[I - 1];
-        if (v >= 0) {
-            g[I] = Tr::template ld<I>(ldg_nc(src + (int64_t)I * np + v));
-        } else {
-            const float raw = Tr::template ld<OPP(I)>(ldg_nc(src + (int64_t)OPP(I) * np + s));
-            g[I] = link_rule<I>(D, v, raw, slot);
-        }
+        g[I] = Tr::template ld<I>(load_ro<HINT>(src + ((int64_t)I * np + nb[I - 1])));
     });
-    const float4 m = collide(g, D.omega);
+    const int slot = iolet_fixup<S>(D, s, g);
+    const float4 m = collide_s<S>(g, D.omega);
     unroll<0, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
         dst[(int64_t)I * np + s] = Tr::template st<I>(g[I]);
@@ -171,31 +321,17 @@ __device__ __forceinline__ void site_ab(const DomDev &D, const typename St<S>::T
 // The store base is passed through an opaque move so the compiler recomputes
 // the 19 store addresses after the collision instead of keeping the load
 // addresses alive across it (75 -> ~45 registers).
-template <typename T> __device__ __forceinline__ T *opaque(T *p) {
-    T *q;
-    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
-    return q;
-}
-
-template <int S>
-__device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T *buf, int64_t s,
-                                             bool flagged) {
+template <int S, bool HINT = false>
+__device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T *buf, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
     float g[19];
     unroll<0, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        g[I] = Tr::template ld<I>(buf[(int64_t)I * np + s]);
+        g[I] = Tr::template ld<I>(load_rw<HINT>(buf + (int64_t)I * np + s));
     });
-    int slot = -1;
-    if (flagged) {  // rare: the previous odd step left raw values on iolet links
-        unroll<1, 19>([&](auto ic) {
-            constexpr int I = decltype(ic)::v;
-            const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * np + s);
-            if (v < -1) g[I] = link_rule<I>(D, v, g[I], slot);
-        });
-    }
-    const float4 m = collide(g, D.omega);
+    const int slot = iolet_fixup<S>(D, s, g);  // the odd step left raw values on iolet links
+    const float4 m = collide_s<S>(g, D.omega);
     typename St<S>::T *wb = opaque(buf + s);
     unroll<0, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
@@ -205,35 +341,29 @@ __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T 
 }
 
 // ---- AA odd step: gather F_{t-1} (swapped) from x - c_i, scatter F_t to x + c_i ----
-template <int S>
+// Entry OPP(I) of the site's row is the site at x + c_I; its virtual index for
+// a non-fluid link turns the scatter into the raw write to the own slot OPP(I).
+template <int S, bool HINT = false>
 __device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s) {
     using Tr = St<S>;
-    const uint32_t np = (uint32_t)D.np;
-    const uint32_t su = (uint32_t)s;
+    const int64_t np = D.np;
     int32_t nb[18];
 #pragma unroll
-    for (int i = 0; i < 18; ++i) nb[i] = __ldg(D.nbr + (i * np + su));
+    for (int i = 0; i < 18; ++i) nb[i] = load_nbr<HINT>(D.nbr + (int64_t)i * np + s);
     float g[19];
-    g[0] = Tr::template ld<0>(buf[su]);
-    int slot = -1;
+    g[0] = Tr::template ld<0>(load_rw<HINT>(buf + s));
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int32_t v = nb[I - 1];
-        if (v >= 0) {
-            g[I] = Tr::template ld<I>(buf[OPP(I) * np + (uint32_t)v]);
-        } else {
-            const float raw = Tr::template ld<OPP(I)>(buf[I * np + su]);
-            g[I] = link_rule<I>(D, v, raw, slot);
-        }
+        g[I] = Tr::template ld<I>(load_rw<HINT>(buf + ((int64_t)OPP(I) * np + nb[I - 1])));
     });
-    const float4 m = collide(g, D.omega);
-    buf[su] = Tr::template st<0>(g[0]);
+    const int slot = iolet_fixup<S>(D, s, g);
+    const float4 m = collide_s<S>(g, D.omega);
+    typename St<S>::T *wb = opaque(buf);
+    const int32_t *nb2 = opaque(D.nbr);  // reread (L1 hits) instead of keeping 18 entries live
+    wb[s] = Tr::template st<0>(g[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        int32_t t;  // site at x + c_I (reloaded: keeps 18 entries from staying live)
-        asm volatile("ld.global.nc.s32 %0, [%1];" : "=r"(t) : "l"(D.nbr + ((OPP(I) - 1) * np + su)));
-        const uint32_t off = t >= 0 ? I * np + (uint32_t)t : OPP(I) * np + su;  // raw if not fluid
-        buf[off] = Tr::template st<I>(g[I]);
+        wb[(int64_t)I * np + __ldg(nb2 + (int64_t)(OPP(I) - 1) * np + s)] = Tr::template st<I>(g[I]);
     });
     if (slot >= 0) D.bnd[slot] = m;
 }
@@ -278,52 +408,32 @@ template <int S16> struct Word16 {
 template <> struct Word<kF16> : Word16<kF16> {};
 template <> struct Word<kBF16> : Word16<kBF16> {};
 
-// Issue the gathers of site s: incoming direction I from `src_row(I)` at the
-// pull source, or the own opposite value on non-fluid links.  AA odd reads the
-// swapped slot OPP(I) at the source and the natural slot I at the own site.
+// Issue the gathers of site s (virtual indices: one formula for every link).
+// A/B pulls slot I from x - c_I; AA odd pulls the swapped slot OPP(I).
 template <int S, bool AA>
-__device__ __forceinline__ void issue_gathers(const DomDev &D, const typename St<S>::T *src,
-                                              int64_t s, uint32_t stage, uint32_t rstride,
-                                              uint32_t &sel, uint32_t &wall, uint32_t &iol) {
+__device__ __forceinline__ uint32_t issue_gathers(const DomDev &D, const typename St<S>::T *src,
+                                                  int64_t s, uint32_t stage, uint32_t rstride) {
     const int64_t np = D.np;
+    uint32_t sel = 0;
     int32_t nb[18];
 #pragma unroll
     for (int i = 0; i < 18; ++i) nb[i] = __ldg(D.nbr + (int64_t)i * np + s);
     cp_async4(stage, Word<S>::src(src + s, sel, 0));
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int32_t v = nb[I - 1];
-        const typename St<S>::T *p;
-        if (v >= 0) {
-            p = src + (int64_t)(AA ? OPP(I) : I) * np + v;
-        } else {
-            p = src + (int64_t)(AA ? I : OPP(I)) * np + s;
-            if (v == -1) wall |= 1u << I;
-            else iol |= 1u << I;
-        }
+        const typename St<S>::T *p = src + ((int64_t)(AA ? OPP(I) : I) * np + nb[I - 1]);
         cp_async4(stage + I * rstride, Word<S>::src(p, sel, I));
     });
+    return sel;
 }
 
-// Read the staged values back, apply the boundary rules, collide.
 template <int S>
-__device__ __forceinline__ float4 staged_collide(const DomDev &D, const uint32_t *st,
-                                                 uint32_t rwords, int64_t s, uint32_t sel,
-                                                 uint32_t iol, float g[19], int &slot) {
+__device__ __forceinline__ void read_staged(const uint32_t *st, uint32_t rwords, uint32_t sel,
+                                            float g[19]) {
     unroll<0, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
         g[I] = Word<S>::template get<I>(st[I * rwords], sel);
     });
-    if (iol) {  // rare: links into an iolet opening
-        unroll<1, 19>([&](auto ic) {
-            constexpr int I = decltype(ic)::v;
-            if ((iol >> I) & 1u) {
-                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * D.np + s);
-                g[I] = link_rule<I>(D, v, g[I], slot);
-            }
-        });
-    }
-    return collide(g, D.omega);
 }
 
 template <int S, int SPT>
@@ -333,16 +443,13 @@ __device__ __forceinline__ void tile_ab_async(const DomDev &D, const TileDev &tl
     const T *src = (const T *)D.f[(t - 1) & 1];
     T *dst = (T *)D.f[t & 1];
     const uint32_t B = blockDim.x;
-    uint32_t sel[SPT], iol[SPT];
+    uint32_t sel[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
-        sel[j] = 0;
-        iol[j] = 0;
-        uint32_t wall = 0;
         const int r = j * B + threadIdx.x;
-        if (r < tl.count)
-            issue_gathers<S, false>(D, src, tl.start + r, smem_addr(stage_base + (j * 19) * B + threadIdx.x),
-                                    4 * B, sel[j], wall, iol[j]);
+        sel[j] = r < tl.count ? issue_gathers<S, false>(D, src, tl.start + r,
+                                                        smem_addr(stage_base + (j * 19) * B + threadIdx.x), 4 * B)
+                              : 0u;
     }
     cp_async_wait_all();
 #pragma unroll
@@ -351,9 +458,9 @@ __device__ __forceinline__ void tile_ab_async(const DomDev &D, const TileDev &tl
         if (r >= tl.count) continue;
         const int64_t s = tl.start + r;
         float g[19];
-        int slot = -1;
-        const float4 m = staged_collide<S>(D, stage_base + (j * 19) * B + threadIdx.x, B, s, sel[j],
-                                           iol[j], g, slot);
+        read_staged<S>(stage_base + (j * 19) * B + threadIdx.x, B, sel[j], g);
+        const int slot = iolet_fixup<S>(D, s, g);
+        const float4 m = collide_s<S>(g, D.omega);
         T *wb = opaque(dst + s);
         unroll<0, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
@@ -369,16 +476,13 @@ __device__ __forceinline__ void tile_aa_odd_async(const DomDev &D, const TileDev
     using T = typename St<S>::T;
     T *buf = (T *)D.f[0];
     const uint32_t B = blockDim.x;
-    uint32_t sel[SPT], iol[SPT];
+    uint32_t sel[SPT];
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
-        sel[j] = 0;
-        iol[j] = 0;
-        uint32_t wall = 0;
         const int r = j * B + threadIdx.x;
-        if (r < tl.count)
-            issue_gathers<S, true>(D, buf, tl.start + r, smem_addr(stage_base + (j * 19) * B + threadIdx.x),
-                                   4 * B, sel[j], wall, iol[j]);
+        sel[j] = r < tl.count ? issue_gathers<S, true>(D, buf, tl.start + r,
+                                                       smem_addr(stage_base + (j * 19) * B + threadIdx.x), 4 * B)
+                              : 0u;
     }
     cp_async_wait_all();
 #pragma unroll
@@ -387,9 +491,9 @@ __device__ __forceinline__ void tile_aa_odd_async(const DomDev &D, const TileDev
         if (r >= tl.count) continue;
         const int64_t s = tl.start + r;
         float g[19];
-        int slot = -1;
-        const float4 m = staged_collide<S>(D, stage_base + (j * 19) * B + threadIdx.x, B, s, sel[j],
-                                           iol[j], g, slot);
+        read_staged<S>(stage_base + (j * 19) * B + threadIdx.x, B, sel[j], g);
+        const int slot = iolet_fixup<S>(D, s, g);
+        const float4 m = collide_s<S>(g, D.omega);
         const int32_t *nb2 = opaque(D.nbr);  // fresh (L1-resident) reads for the scatter
         T *wb = opaque(buf);
         const int64_t np = D.np;
@@ -397,8 +501,7 @@ __device__ __forceinline__ void tile_aa_odd_async(const DomDev &D, const TileDev
         unroll<1, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
             const int32_t tg = __ldg(nb2 + (int64_t)(OPP(I) - 1) * np + s);  // site at x + c_I
-            const int64_t off = tg >= 0 ? (int64_t)I * np + tg : (int64_t)OPP(I) * np + s;
-            wb[off] = St<S>::template st<I>(g[I]);
+            wb[(int64_t)I * np + tg] = St<S>::template st<I>(g[I]);
         });
         if (slot >= 0) D.bnd[slot] = m;
     }
@@ -407,7 +510,6 @@ __device__ __forceinline__ void tile_aa_odd_async(const DomDev &D, const TileDev
 // AA even step on pairs of adjacent sites (2 per thread): vector loads/stores.
 template <int S> struct Pair;
 template <> struct Pair<kF32> {
-    using V = float2;
     template <int I> static __device__ __forceinline__ void ld(const float *p, float &a, float &b) {
         const float2 v = *(const float2 *)p;
         a = v.x;
@@ -448,8 +550,7 @@ __device__ __forceinline__ void tile_aa_even_pairs(const DomDev &D, const TileDe
     for (int r = 2 * threadIdx.x; r < tl.count; r += 2 * blockDim.x) {
         const int64_t s = tl.start + r;  // even: tiles start at multiples of 64
         if (r + 1 >= tl.count) {         // ragged tail: one site
-            const uint32_t word = __ldg(D.iomask + (s >> 5));
-            site_aa_even<S>(D, buf, s, (word >> (s & 31)) & 1u);
+            site_aa_even<S>(D, buf, s);
             continue;
         }
         float ga[19], gb[19];
@@ -457,24 +558,10 @@ __device__ __forceinline__ void tile_aa_even_pairs(const DomDev &D, const TileDe
             constexpr int I = decltype(ic)::v;
             Pair<S>::template ld<I>(buf + (int64_t)I * np + s, ga[I], gb[I]);
         });
-        const uint32_t word = __ldg(D.iomask + (s >> 5));
-        int slot_a = -1, slot_b = -1;
-        if ((word >> (s & 31)) & 1u) {
-            unroll<1, 19>([&](auto ic) {
-                constexpr int I = decltype(ic)::v;
-                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * np + s);
-                if (v < -1) ga[I] = link_rule<I>(D, v, ga[I], slot_a);
-            });
-        }
-        if ((word >> ((s + 1) & 31)) & 1u) {
-            unroll<1, 19>([&](auto ic) {
-                constexpr int I = decltype(ic)::v;
-                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * np + s + 1);
-                if (v < -1) gb[I] = link_rule<I>(D, v, gb[I], slot_b);
-            });
-        }
-        const float4 ma = collide(ga, D.omega);
-        const float4 mb = collide(gb, D.omega);
+        const int slot_a = iolet_fixup<S>(D, s, ga);
+        const int slot_b = iolet_fixup<S>(D, s + 1, gb);
+        const float4 ma = collide_s<S>(ga, D.omega);
+        const float4 mb = collide_s<S>(gb, D.omega);
         T *wb = opaque(buf + s);
         unroll<0, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
@@ -562,15 +649,8 @@ __device__ __forceinline__ void tile_aa_even_tma(const DomDev &D, const TileDev 
             constexpr int I = decltype(ic)::v;
             g[I] = St<S>::template ld<I>(rows[(size_t)I * cap + r]);
         });
-        int slot = -1;
-        if ((__ldg(D.iomask + (s >> 5)) >> (s & 31)) & 1u) {
-            unroll<1, 19>([&](auto ic) {
-                constexpr int I = decltype(ic)::v;
-                const int32_t v = __ldg(D.nbr + (int64_t)(I - 1) * np + s);
-                if (v < -1) g[I] = link_rule<I>(D, v, g[I], slot);
-            });
-        }
-        const float4 m = collide(g, D.omega);
+        const int slot = iolet_fixup<S>(D, s, g);
+        const float4 m = collide_s<S>(g, D.omega);
         unroll<0, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
             rows[(size_t)OPP(I) * cap + r] = St<S>::template st<I>(g[I]);
@@ -602,7 +682,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
     }
     __syncthreads();
     const int64_t t = t_now;
-    if constexpr (V >= 1) {
+    if constexpr (V == 1 || V == 2) {
         if constexpr (SCHEME == kAB) {
             tile_ab_async<S, SPT>(D, tl, t, stage);
         } else {
@@ -612,6 +692,7 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
             else tile_aa_even_pairs<S>(D, tl);
         }
     } else {
+    constexpr bool HINT = V == 3;
 #pragma unroll
     for (int j = 0; j < SPT; ++j) {
         const int r = j * blockDim.x + threadIdx.x;
@@ -621,16 +702,14 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
             if (live) {
                 const T *src = (const T *)D.f[(t - 1) & 1];
                 T *dst = (T *)D.f[t & 1];
-                site_ab<S>(D, src, dst, s);
+                site_ab<S, HINT>(D, src, dst, s);
             }
         } else {
             T *buf = (T *)D.f[0];
             const bool odd = PAR == 2 ? (t & 1) != 0 : PAR == 1;
-            if (odd) {
-                if (live) site_aa_odd<S>(D, buf, s);
-            } else {
-                const uint32_t word = live ? __ldg(D.iomask + (s >> 5)) : 0u;
-                if (live) site_aa_even<S>(D, buf, s, (word >> (s & 31)) & 1u);
+            if (live) {
+                if (odd) site_aa_odd<S, HINT>(D, buf, s);
+                else site_aa_even<S, HINT>(D, buf, s);
             }
         }
     }
@@ -755,8 +834,7 @@ __device__ __forceinline__ typename St<S>::T stored_F(const DomDev &D, int64_t t
     } else {
         const T *buf = (const T *)D.f[0];
         if (!(t & 1) || I == 0) return buf[(int64_t)OPP(I) * np + s];
-        const int32_t tg = D.nbr[(int64_t)(OPP(I) - 1) * np + s];
-        return tg >= 0 ? buf[(int64_t)I * np + tg] : buf[(int64_t)OPP(I) * np + s];
+        return buf[(int64_t)I * np + D.nbr[(int64_t)(OPP(I) - 1) * np + s]];  // x + c_I, or own raw
     }
 }
 
@@ -769,8 +847,7 @@ __device__ __forceinline__ typename St<S>::T *stored_F_ptr(const DomDev &D, int6
     } else {
         T *buf = (T *)D.f[0];
         if (!(t & 1) || I == 0) return buf + (int64_t)OPP(I) * np + s;
-        const int32_t tg = D.nbr[(int64_t)(OPP(I) - 1) * np + s];
-        return tg >= 0 ? buf + (int64_t)I * np + tg : buf + (int64_t)OPP(I) * np + s;
+        return buf + ((int64_t)I * np + D.nbr[(int64_t)(OPP(I) - 1) * np + s]);
     }
 }
 
@@ -785,7 +862,7 @@ __global__ void k_macroscopic(const DomDev *__restrict__ dd, int64_t n, const in
         float g[19];
         unroll<0, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
-            g[I] = Tr::template ld<I>(stored_F<S, SCHEME, I>(D, t, s));
+            g[I] = Tr::template phys<I>(stored_F<S, SCHEME, I>(D, t, s));
         });
         float drho = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
         unroll<0, 19>([&](auto ic) {
@@ -863,7 +940,7 @@ template <int S, int SCHEME, int PAR, int V, int SPT>
 cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                           int64_t n_tiles, int off, cudaStream_t st) {
     // V1: cp.async stage of 4-byte words; V2 also holds the even step's 19 rows + mbarrier
-    size_t smem = V >= 1 ? (size_t)SPT * 19 * cfg.block * 4 : 0;
+    size_t smem = (V == 1 || V == 2) ? (size_t)SPT * 19 * cfg.block * 4 : 0;
     if (V == 2) smem += 16;
     auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
     if (smem > 48 * 1024) {
@@ -881,6 +958,14 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
         switch (cfg.spt) {
             case 1: return launch_sc_one<S, SCHEME, PAR, 1, 1>(cfg, doms, tiles, n_tiles, off, st);
             case 2: return launch_sc_one<S, SCHEME, PAR, 1, 2>(cfg, doms, tiles, n_tiles, off, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (cfg.variant == 3) {
+        switch (cfg.spt) {
+            case 1: return launch_sc_one<S, SCHEME, PAR, 3, 1>(cfg, doms, tiles, n_tiles, off, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 3, 2>(cfg, doms, tiles, n_tiles, off, st);
+            case 4: return launch_sc_one<S, SCHEME, PAR, 3, 4>(cfg, doms, tiles, n_tiles, off, st);
             default: return cudaErrorInvalidValue;
         }
     }

@@ -256,10 +256,11 @@ def test_errors_are_reported(gpu):
 
 LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128, 2, 1),
             ("aa", 256, 1, 0), ("aa", 128, 4, 0), ("aa", 256, 1, 1), ("aa", 256, 2, 1),
-            ("aa", 64, 2, 1), ("aa", 128, 2, 2), ("aa", 256, 1, 2), ("aa", 64, 2, 2)]
+            ("aa", 64, 2, 1), ("aa", 128, 2, 2), ("aa", 256, 1, 2), ("aa", 64, 2, 2),
+            ("ab", 256, 1, 3), ("ab", 128, 4, 3), ("aa", 256, 1, 3), ("aa", 128, 2, 3)]
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_kernel_variants_bit_identical(gpu, storage):
     """Every scheme, launch shape and kernel variant computes the same bits per site."""
     geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
