@@ -313,3 +313,46 @@ def test_autotune_leaves_state_unchanged(gpu):
         finally:
             ctx.close()
             ref.close()
+
+
+def test_coupled_1toN_greedy_map(gpu, oracle_mod):
+    """1:N coupling (Section 3): 4 arterial outlets feed 8 venous inlets through the greedy map.
+
+    Map and factors come from the C ABI helper; the oracle runs the same pairs.  Imposed venous
+    inlet speeds must conserve each outlet's flux: sum_i A_i v_i = A_0 v_0.
+    """
+    art = S.tree(S.TreeSpec(depth=3, root_radius=4.0, seed=21), inlet_speed=0.04, period=300.0)
+    ven = S.tree(S.TreeSpec(depth=4, root_radius=3.0, seed=22), venous=True, venous_offset=6.0)
+    oa, ov = np.array(art.origin), np.array(ven.origin)
+    ac = [tuple(int(c) for c in np.array(io.centre) + 1024 * oa) for io in art.iolets[1:]]
+    vc = [tuple(int(c) for c in np.array(io.centre) + 1024 * ov) for io in ven.iolets[1:]]
+    aa = [io.area() for io in art.iolets[1:]]
+    va = [io.area() for io in ven.iolets[1:]]
+    u = S.uniform_draws(5, len(vc))
+    assign, dist, dp, fac = gpu.hg_coupling_factors(ac, aa, vc, va, u)
+    assert len(set(assign)) == len(ac) and len(vc) == 2 * len(ac)      # every artery, 1:N
+    for a in range(len(ac)):
+        idx = [v for v in range(len(vc)) if assign[v] == a]
+        assert abs(sum(va[v] * fac[v] for v in idx) - aa[a]) < 1e-12 * aa[a]
+    pairs = [(int(assign[v]) + 1, v + 1, float(fac[v])) for v in range(len(vc))]
+    for scheme in ("ab", "aa"):
+        ctx = gpu.Context(storage="f32", scheme=scheme)
+        try:
+            da = ctx.domain(art.xyz, art.iolets, tau=TAU)
+            dv = ctx.domain(ven.xyz, ven.iolets, tau=TAU)
+            ctx.couple(da, dv, pairs)
+            oa_ = oracle_mod.Domain(art.xyz, art.iolets, tau=TAU)
+            ov_ = oracle_mod.Domain(ven.xyz, ven.iolets, tau=TAU)
+            sysm = oracle_mod.System([oa_, ov_], [(0, a, 1, v, f) for (a, v, f) in pairs])
+            for n in (120, 381):
+                ctx.step(n)
+                sysm.step(n)
+                for d, od in ((da, oa_), (dv, ov_)):
+                    eu, ep = field_errors(d.macroscopic(), od.moments())
+                    assert eu < TOL["f32"] and ep < TOL["f32"], (scheme, n, eu, ep)
+            Ma, bv = da.iolet_stats(), dv.boundary_values()
+            assert np.any(Ma[1:, 0] != 0)
+            for (a, v, f) in pairs:
+                assert abs(bv[v] - np.float32(f * Ma[a, 0])) <= 1e-7 * max(abs(bv[v]), 1e-30)
+        finally:
+            ctx.close()
