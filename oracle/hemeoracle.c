@@ -36,6 +36,13 @@
  *   R6 time: step t (t = 1, 2, ...) streams the post-collision state F_{t-1}
  *      into G_t using the boundary values of time t, then collides G_t into
  *      F_t.  Iolet means M_t are taken over the moments of G_t.
+ *   R7 body force (Section 3, reverse coupling direction, which names the
+ *      forcing of Guo, Zheng and Shi, Phys. Rev. E 65, 046308, 2002): at a
+ *      site with force density F the velocity is u = (j + F/2)/rho, the
+ *      equilibrium is taken at that u, and the collision adds
+ *      (1 - 1/(2 tau)) w_i [3 (c_i - u) + 9 (c_i . u) c_i] . F.  Collision
+ *      then conserves mass and raises the momentum by exactly F.  Sites
+ *      without a force run the unforced update bit for bit.
  */
 #include <math.h>
 #include <stdint.h>
@@ -289,12 +296,47 @@ static void wall_velocity(const or_iolet *io, const int32_t x[3], int i, double 
     for (int d = 0; d < 3; ++d) uw[d] = -ah[d] * U * phi;
 }
 
+/* BGK collision of the streamed values g (R4); with force density F != NULL
+ * the Guo forcing of R7.  mom receives (drho, ux, uy, uz). */
+static void collide(const double g[19], double tau, const double *F, double out[19], double mom[4]) {
+    double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
+    for (int i = 0; i < 19; ++i) {
+        drho += g[i];
+        for (int d = 0; d < 3; ++d) j[d] += CV[i][d] * g[i];
+    }
+    double rho = 1.0 + drho;
+    double u[3];
+    for (int d = 0; d < 3; ++d) u[d] = F ? (j[d] + 0.5 * F[d]) / rho : j[d] / rho;
+    double feq[19];
+    equilibrium(drho, u, feq);
+    for (int i = 0; i < 19; ++i) out[i] = g[i] - (g[i] - feq[i]) / tau;
+    if (F) {
+        double pref = 1.0 - 0.5 / tau;
+        double uF = u[0] * F[0] + u[1] * F[1] + u[2] * F[2];
+        for (int i = 0; i < 19; ++i) {
+            double cu = CV[i][0] * u[0] + CV[i][1] * u[1] + CV[i][2] * u[2];
+            double cF = CV[i][0] * F[0] + CV[i][1] * F[1] + CV[i][2] * F[2];
+            out[i] += pref * weight(i) * (3.0 * (cF - uF) + 9.0 * cu * cF);
+        }
+    }
+    mom[0] = drho;
+    mom[1] = u[0];
+    mom[2] = u[1];
+    mom[3] = u[2];
+}
+
+/* The collision alone, for checks of its conservation laws. */
+void or_collide(const double *g, double tau, const double *F, double *out, double *mom) {
+    collide(g, tau, F, out, mom);
+}
+
 /* One site of step t (R5, R6): stream into g (pull from x - c_i, boundary
  * rules on non-fluid links), moments, BGK collision.  bcval[k] is the iolet's
- * value at time t (density deviation or speed). */
+ * value at time t (density deviation or speed); force (NULL = none) holds a
+ * force density per site, [n][3]. */
 static void site_update(int64_t n, int64_t s, const int32_t *nbr, const int32_t *xyz,
                         const double *Fin, double tau, const or_iolet *io, const double *bcval,
-                        double out[19], double mom[4]) {
+                        const double *force, double out[19], double mom[4]) {
     double g[19];
     g[0] = Fin[s];
     for (int i = 1; i < 19; ++i) {
@@ -317,30 +359,19 @@ static void site_update(int64_t n, int64_t s, const int32_t *nbr, const int32_t 
             }
         }
     }
-    double drho = 0.0, j[3] = {0.0, 0.0, 0.0};
-    for (int i = 0; i < 19; ++i) {
-        drho += g[i];
-        for (int d = 0; d < 3; ++d) j[d] += CV[i][d] * g[i];
-    }
-    double rho = 1.0 + drho;
-    double u[3] = {j[0] / rho, j[1] / rho, j[2] / rho};
-    double feq[19];
-    equilibrium(drho, u, feq);
-    for (int i = 0; i < 19; ++i) out[i] = g[i] - (g[i] - feq[i]) / tau;
-    mom[0] = drho;
-    mom[1] = u[0];
-    mom[2] = u[1];
-    mom[3] = u[2];
+    const double *F = force ? &force[3 * s] : NULL;
+    if (F && F[0] == 0.0 && F[1] == 0.0 && F[2] == 0.0) F = NULL;
+    collide(g, tau, F, out, mom);
 }
 
 /* Step t over all sites: Fin = F_{t-1} (SoA [19][n]) -> Fout = F_t; mom (if
- * non-NULL) receives (drho, ux, uy, uz) of G_t per site. */
+ * non-NULL) receives (drho, ux, uy, uz) of G_t per site; force as above. */
 void or_step(int64_t n, const int32_t *nbr, const int32_t *xyz, const double *Fin, double *Fout,
-             double tau, const or_iolet *io, const double *bcval, double *mom) {
+             double tau, const or_iolet *io, const double *bcval, const double *force, double *mom) {
 #pragma omp parallel for schedule(static)
     for (int64_t s = 0; s < n; ++s) {
         double out[19], m[4];
-        site_update(n, s, nbr, xyz, Fin, tau, io, bcval, out, m);
+        site_update(n, s, nbr, xyz, Fin, tau, io, bcval, force, out, m);
         for (int i = 0; i < 19; ++i) Fout[(int64_t)i * n + s] = out[i];
         if (mom)
             for (int c = 0; c < 4; ++c) mom[4 * s + c] = m[c];
@@ -349,11 +380,11 @@ void or_step(int64_t n, const int32_t *nbr, const int32_t *xyz, const double *Fi
 
 /* The same update for a list of sites only: out[p][19], mom[p][4]. */
 void or_step_sites(int64_t n, const int32_t *nbr, const int32_t *xyz, const double *Fin,
-                   double tau, const or_iolet *io, const double *bcval, const int64_t *sites,
-                   int64_t nsites, double *out, double *mom) {
+                   double tau, const or_iolet *io, const double *bcval, const double *force,
+                   const int64_t *sites, int64_t nsites, double *out, double *mom) {
 #pragma omp parallel for schedule(static)
     for (int64_t p = 0; p < nsites; ++p)
-        site_update(n, sites[p], nbr, xyz, Fin, tau, io, bcval, &out[19 * p], &mom[4 * p]);
+        site_update(n, sites[p], nbr, xyz, Fin, tau, io, bcval, force, &out[19 * p], &mom[4 * p]);
 }
 
 /* Moments (drho, ux, uy, uz) of a stored state F (SoA [19][n]). */
