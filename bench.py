@@ -311,11 +311,10 @@ def _geo_pool_gen(args):
     return (art, ven)
 
 
-def run_serve(args, H, device):
-    """Serving workload: seeded request stream, continuous batching, p50/p99 time-to-result."""
+def serve_requests(args):
+    """The seeded request stream and its voxelised geometries (spawned host processes)."""
     import multiprocessing as mp
 
-    from paper_2010_04144_gb300 import serve as SV
     from paper_2010_04144_gb300 import synth as S
 
     reqs = S.request_stream(n_requests=args.requests, rate_per_s=args.rate,
@@ -324,9 +323,18 @@ def run_serve(args, H, device):
     t0 = time.perf_counter()
     geos = pool.map(_geo_pool_gen, [(r.spec, r.coupled) for r in reqs], chunksize=1)
     pool.close()
-    gen_s = time.perf_counter() - t0
+    return reqs, geos, time.perf_counter() - t0
+
+
+def run_serve(args, H, device, prepared=None):
+    """Serving workload: seeded request stream, continuous batching, p50/p99 time-to-result."""
+    from paper_2010_04144_gb300 import serve as SV
+    from paper_2010_04144_gb300 import synth as S
+
+    reqs, geos, gen_s = prepared if prepared is not None else serve_requests(args)
     srv = SV.Server(device=device, storage=args.serve_storage, scheme="aa",
-                    budget_bytes=args.budget_gb * 1e9, chunk_steps=100)
+                    budget_bytes=args.budget_gb * 1e9, chunk_steps=100,
+                    build_workers=args.serve_build_workers, policy=args.serve_policy)
     try:
         for r, g in zip(reqs, geos):
             if r.coupled:
@@ -341,6 +349,11 @@ def run_serve(args, H, device):
         srv.close()
     sites = [sum(x.n for x in g) for g in geos]
     offered = sum(sites) * args.serve_steps / (reqs[-1].arrival_s or 1.0) / 1e6
+    # the request rate the measured aggregate throughput sustains (meaningful when the stream
+    # saturates the server, i.e. offered > aggregate): throughput / mean work per request
+    mean_work = sum(sites) * args.serve_steps / len(sites) / 1e6
+    st["max_sustainable_rate_per_s"] = st["aggregate_mflups"] / mean_work
+    st["saturated"] = offered > st["aggregate_mflups"]
     line = {"metric": "served time-to-result p50/p99 (s) and aggregate MFLUPS", "value": st["p50_s"],
             "unit": "s (p50 time-to-result)", "p99_s": st["p99_s"], "higher_is_better": False,
             "aggregate_mflups": st["aggregate_mflups"], "n_gpus": 1, "dtype": args.serve_storage + "-stored/f32-compute",
@@ -349,6 +362,7 @@ def run_serve(args, H, device):
                                    f"sites log-uniform [{args.min_sites:.0e}, {args.max_sites:.0e}], "
                                    f"half coupled pairs, {args.serve_steps} steps each",
                        "budget_gb": args.budget_gb, "tick_steps": 100, "scheme": "aa",
+                       "build_workers": args.serve_build_workers, "policy": args.serve_policy,
                        "total_sites": int(sum(sites)), "offered_mflups": offered,
                        "geometry_generation_s": gen_s},
             "serving": st}
@@ -362,19 +376,32 @@ def run_coupled(args, H, device):
     from paper_2010_04144_gb300 import synth as S
     from paper_2010_04144_gb300.autotune import autotune
 
+    from paper_2010_04144_gb300 import serve as SV
+
     spec = S.TreeSpec(depth=6, root_radius=24.0, seed=2010041442, scale=args.coupled_scale)
     art = S.tree(spec, inlet_speed=0.05, period=1000.0)
-    ven = S.tree(spec, venous=True)
+    one_to_n = args.coupled_venous_depth > 0
+    if one_to_n:  # an independent, deeper venous tree: the greedy 1:N map couples by proximity
+        vspec = S.TreeSpec(depth=args.coupled_venous_depth, root_radius=24.0, seed=2010041443,
+                           scale=args.coupled_scale)
+        ven = S.tree(vspec, venous=True)
+    else:
+        ven = S.tree(spec, venous=True)
     ctx = H.Context(device=device, storage="f32", scheme=args.coupled_scheme)
     try:
         da = ctx.domain(art.xyz, art.iolets)
         dv = ctx.domain(ven.xyz, ven.iolets)
-        pairs = []
-        for k in range(1, len(art.iolets)):  # mirrored leaf k feeds venous inlet k (1:1 map)
-            _, _, _, f = H.hg_coupling_factors([art.iolets[k].centre], [art.iolets[k].area()],
-                                               [ven.iolets[k].centre], [ven.iolets[k].area()], [0.5])
-            pairs.append((k, k, float(f[0])))
+        if one_to_n:
+            u = S.uniform_draws(2010041444, len(ven.iolets))
+            pairs = SV.coupled_job_from_trees(0, 0.0, 0, art, ven, u).pairs
+        else:
+            pairs = []
+            for k in range(1, len(art.iolets)):  # mirrored leaf k feeds venous inlet k (1:1 map)
+                _, _, _, f = H.hg_coupling_factors([art.iolets[k].centre], [art.iolets[k].area()],
+                                                   [ven.iolets[k].centre], [ven.iolets[k].area()], [0.5])
+                pairs.append((k, k, float(f[0])))
         ctx.couple(da, dv, pairs)
+        ctx.set_coupling_mode(args.coupled_mode)
         best, _ = autotune(ctx)
         ctx.step(args.warmup)
         barrier(None)
@@ -391,20 +418,45 @@ def run_coupled(args, H, device):
         peak, kind = hbm_peak()
         Mv = dv.iolet_stats()
         Ma = da.iolet_stats()
-        ratio = [float(-Mv[k, 0] / Ma[k, 0]) if Ma[k, 0] else None for k in range(1, len(art.iolets))]
+        # the venous inlets' next boundary values against factor x source outlet mean (exact up to
+        # FP32 rounding), and the venous inlet flow they produce against the same product
+        bv = dv.boundary_values()
+        forces = da.iolet_forces()
+        vva = {}
+        if args.velocity_area:  # Section 3.3's speed-against-vessel-area plot, per tree level
+            from paper_2010_04144_gb300 import analysis as AN
+
+            for name, d, g in (("arterial", da, art), ("venous", dv, ven)):
+                rows = AN.velocity_vs_area(g, d.macroscopic(), d.sites(), arterial_negative=name == "arterial")
+                lvl = np.floor(np.log2(rows[:, 0] + 1)).astype(int)
+                vva[name] = [[int(L), float(np.median(rows[lvl == L, 1])), float(np.median(rows[lvl == L, 2])),
+                              int((lvl == L).sum())] for L in np.unique(lvl)]
+        bc_dev = (max(abs(abs(float(bv[vk])) / abs(f * Ma[ak, 0]) - 1.0) for ak, vk, f in pairs if Ma[ak, 0])
+                  if args.coupled_mode == "forward" else None)  # alternate: may hold the previous value
+        ratio = [float(abs(Mv[vk, 0]) / abs(f * Ma[ak, 0])) for ak, vk, f in pairs if Ma[ak, 0]]
+        fan = np.bincount([ak for ak, _, _ in pairs])
         line = {"metric": "MFLUPS, coupled arterial+venous pair in one launch sequence",
                 "value": n * args.steps / (ms / 1e3) / 1e6, "unit": "MFLUPS", "n_gpus": 1,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
                 "higher_is_better": True, "dtype": "f32", "data": "synthetic (seeded tree pair)",
-                "config": {"workload": f"arterial tree d=6 R=24x{args.coupled_scale} + venous twin (radii x1.2)",
+                "config": {"workload": (f"arterial tree d=6 R=24x{args.coupled_scale} + "
+                                        + (f"independent venous tree d={args.coupled_venous_depth} "
+                                           f"(radii x1.2), greedy 1:N map" if one_to_n
+                                           else "venous twin (radii x1.2), 1:1 map")),
                            "arterial_sites": da.n, "venous_sites": dv.n, "pairs": len(pairs),
-                           "factor": pairs[0][2], "scheme": args.coupled_scheme,
+                           "arterial_outlets": len(art.iolets) - 1, "venous_inlets": len(ven.iolets) - 1,
+                           "fan_out_max": int(fan.max()), "fan_out_min": int(fan[1:].min()),
+                           "factor_range": [min(p[2] for p in pairs), max(p[2] for p in pairs)],
+                           "scheme": args.coupled_scheme, "exchange": args.coupled_mode,
                            "launch": {"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]}},
                 "roofline": {"bound": "hbm", "achieved": B * n / (per / 1e3) / 1e9, "peak": peak,
                              "unit": "GB/s", "frac": B * n / (per / 1e3) / 1e9 / peak,
                              "bytes_per_update": B},
                 "iolet_update_ms": ms_io / min(args.steps, 200),
-                "venous_over_arterial_mean_u": ratio[:8]}
+                "boundary_value_rel_dev_max": bc_dev,
+                "arterial_outlet_force_max": float(np.abs(forces).max()),
+                "velocity_vs_area_by_level": vva or None,
+                "venous_inlet_flow_over_imposed": [min(ratio), float(np.median(ratio)), max(ratio)]}
         print(json.dumps(line))
     finally:
         ctx.close()
@@ -485,6 +537,13 @@ def main():
     ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve"])
     ap.add_argument("--coupled-scale", type=float, default=2.12)
     ap.add_argument("--coupled-scheme", default="ab")
+    ap.add_argument("--velocity-area", action="store_true",
+                    help="coupled config: add mean speed vs vessel area per tree level (Section 3.3)")
+    ap.add_argument("--coupled-mode", default="forward", choices=["forward", "alternate"],
+                    help="coupling exchange: forward every step, or alternating forward/reverse (Guo force)")
+    ap.add_argument("--coupled-venous-depth", type=int, default=0,
+                    help="0: mirrored venous twin, 1:1 pairs; d > 6: independent venous tree of depth d "
+                         "coupled by the greedy 1:N map")
     ap.add_argument("--precision-scale", type=float, default=1.84)
     ap.add_argument("--error-scale", type=float, default=0.54)
     ap.add_argument("--error-steps", type=int, default=500)
@@ -494,6 +553,9 @@ def main():
     ap.add_argument("--max-sites", type=float, default=4e7)
     ap.add_argument("--serve-steps", type=int, default=2000)
     ap.add_argument("--serve-storage", default="f16")
+    ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "backfill"])
+    ap.add_argument("--serve-build-workers", type=int, default=1,
+                    help="0: build admitted requests inline between ticks; 1: on a worker thread")
     ap.add_argument("--budget-gb", type=float, default=180.0)
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)

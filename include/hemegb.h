@@ -13,7 +13,7 @@
  *
  * Conventions (every function):
  *   - returns HG_OK (0) or a negative HG_ERR_* code; hg_last_error(ctx) then
- *     holds a message owned by the context (valid until the next call);
+ *     holds a message for the calling thread (valid until its next call);
  *   - sizes and counts are int64_t; handles are opaque;
  *   - host arrays passed in are owned by the caller and copied during the
  *     call; host arrays passed out are caller-allocated;
@@ -21,7 +21,10 @@
  *     allocator callback, else cudaMalloc);
  *   - work is ordered on the context's CUDA stream; hg_step* only enqueue,
  *     hg_read_* / hg_save_state / hg_mass synchronise the stream;
- *   - a context and its domains are not thread-safe.
+ *   - one thread at a time drives a context and its domains, except that
+ *     hg_domain_create may run on a second thread meanwhile (its host build
+ *     and uploads overlap the first thread's steps; the new domain joins the
+ *     context only when complete); hg_ctx_destroy must not overlap a build.
  *
  * Lattice conventions (identical on every entry point):
  *   - velocities: i = 0 rest; 1..6 = +x,-x,+y,-y,+z,-z; 7..18 = (1,1,0),
@@ -73,6 +76,10 @@ extern "C" {
 /* ---- site orderings (device layout; exported data is always canonical) ---- */
 #define HG_ORDER_MORTON 0 /* canonical order */
 
+/* Coupling exchange direction (Section 3 alternates forward and reverse). */
+#define HG_COUPLE_FORWARD 0   /* forward after every step (default) */
+#define HG_COUPLE_ALTERNATE 1 /* forward after even steps, reverse after odd steps */
+
 typedef struct hg_ctx hg_ctx;
 typedef struct hg_domain hg_domain;
 
@@ -88,8 +95,15 @@ typedef struct {
     int32_t block_size;       /* stream-collide threads per block (multiple of 32, <= 512); 0 = 256 */
     int32_t sites_per_thread; /* 1, 2 or 4; 0 = 1 */
     int32_t graph_steps;      /* steps captured per CUDA graph; 0 = 16; negative = no graphs */
-    int32_t kernel_variant;   /* 0 = gathers into registers; 1 = gathers staged in shared memory
-                                 by cp.async (sites_per_thread 1 or 2) */
+    int32_t kernel_variant;   /* stream-collide form; every form gives bit-identical results:
+                                 0 = gathers into registers;
+                                 1 = gathers staged in shared memory by cp.async, AA even step
+                                     on site pairs (sites_per_thread 1 or 2);
+                                 2 = 1, with the AA even step moved by TMA bulk copies (AA only,
+                                     sites_per_thread 1 or 2);
+                                 3 = 0, with L2 256-byte prefetch hints on every load;
+                                 4 = 1, with the AA odd step's stores staged in shared memory
+                                     and written coalesced (AA only, sites_per_thread 1) */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */
@@ -140,7 +154,8 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out);
 /* Destroy a context and every domain still attached to it. */
 int hg_ctx_destroy(hg_ctx *ctx);
 
-/* Message of the last failed call on this context (or its domains); "" if none. */
+/* Message of the calling thread's last failed call, if that call concerned
+ * this context (or its domains); "" otherwise. */
 const char *hg_last_error(hg_ctx *ctx);
 
 /* Wait for all work enqueued on the context's stream. */
@@ -181,6 +196,22 @@ int hg_domain_neighbours(hg_domain *d, int32_t *nbr_out);
  * effect from the next step.  Both domains must then be stepped together.
  * Errors: HG_ERR_ARG. */
 int hg_couple(hg_ctx *ctx, hg_domain *src, hg_domain *dst, const hg_pair *pairs, int32_t n_pairs);
+
+/* Exchange schedule of every coupling pair of the context (Section 3: the
+ * exchange alternates between the forward and the reverse direction).
+ * HG_COUPLE_FORWARD: after every step each coupled venous inlet takes factor
+ * x the mean u.n of its arterial outlet.  HG_COUPLE_ALTERNATE: the exchange
+ * after step e is that forward one when e is even; when e is odd it is the
+ * reverse one instead: every arterial outlet k that feeds inlets J_k gets
+ * v_k = mean over j in J_k of (inflow speed at j, i.e. -mean u.n) / factor_j
+ * and the body-force density F_k = -(1/2) v_k |v_k| n_k (n_k its unit outward
+ * axis), which acts on every site next to outlet k through Guo, Zheng and Shi
+ * forcing (u = (j + F/2)/rho, source (1 - 1/(2 tau)) w_i [3 (c_i - u) +
+ * 9 (c_i.u) c_i].F) until the next reverse exchange.  Each exchange leaves
+ * the other direction's values unchanged.  The paper describes the reverse
+ * direction in words only; this is the library's reading of it.  Setting a
+ * mode zeroes every force.  Synchronises the stream.  Errors: HG_ERR_ARG. */
+int hg_set_coupling_mode(hg_ctx *ctx, int32_t mode);
 
 /* Host helper for Section 3's coupling map and scale factors.
  * Map: arteries in ascending order each take the closest venous inlet not yet
@@ -245,6 +276,10 @@ int hg_read_iolet_stats(hg_domain *d, double *out);
 /* Boundary values the next step will use, n_iolets FP32 (host). */
 int hg_read_boundary_values(hg_domain *d, float *out);
 
+/* Body-force densities the next step applies next to each iolet (reverse
+ * coupling exchange, see hg_set_coupling_mode), n_iolets x 3 FP32 (host). */
+int hg_read_iolet_forces(hg_domain *d, float *out);
+
 /* Total mass deviation sum_s sum_i f~_i(s) of the current state, FP64. */
 int hg_mass(hg_domain *d, double *out);
 
@@ -273,8 +308,11 @@ int hg_mass_noalloc(const void *f_dev, int32_t storage, int64_t n, int64_t row_s
 /* Bytes needed by hg_save_state for this domain. */
 int hg_state_bytes(hg_domain *d, int64_t *bytes);
 
-/* Save the current state (step count, boundary values, iolet means, and F_t
- * in canonical order in the storage type) to a host buffer. */
+/* Save the current state to a host buffer.  Layout (version 2): a 40-byte
+ * header (magic "HEMEGB1\0", n_sites, step, n_iolets, storage, scheme,
+ * version), boundary values (n_iolets FP32), iolet means (n_iolets x 3 FP64),
+ * F_t in canonical order in the storage type (19 x n_sites), iolet forces
+ * (n_iolets x 4 FP32). */
 int hg_save_state(hg_domain *d, void *host_buf, int64_t bytes);
 
 /* Restore a state written by hg_save_state of a domain with the same

@@ -1,0 +1,101 @@
+"""Post-processing of read-back fields (Section 3.3 analysis and unit mapping).
+
+Nothing here runs on the device or touches the stepping path: these helpers
+take the macroscopic fields a domain returns (``Domain.macroscopic()``:
+(drho, ux, uy, uz) per canonical site) and the seeded geometry they came from.
+
+* ``lattice_parameters`` / ``physical_step``: the two relations Section 3.3
+  states for single-relaxation-time LB, nu = (tau - 1/2) dx^2 / (3 dt) and
+  Ma = sqrt(3) v_max dt / dx (< 0.1), solved for whichever quantity is asked.
+* ``velocity_vs_area``: mean speed against vessel cross-section area, the
+  quantity Section 3.3 plots for the coupled arterial and venous trees.  The
+  paper cuts measurement planes through the whole domain and separates them
+  into vessels; a synthetic tree knows its centrelines, so each segment is cut
+  by the plane through its mid-point normal to its axis.  The cross-section is
+  the set of sites within half a lattice unit of that plane and within the
+  segment radius (+1) of the axis; area = number of those sites (lattice
+  units^2, the discrete counterpart of the paper's convex hull), speed = mean
+  |u| over them.  Arterial areas are returned negative, as the paper plots
+  them, when ``arterial_negative`` is set.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+from . import synth as S
+
+
+def lattice_parameters(dx, dt, nu, v_max):
+    """(tau, Ma) of a run with spacing dx [m], step dt [s], viscosity nu [m^2/s] and peak
+    speed v_max [m/s]: tau = 1/2 + 3 nu dt / dx^2, Ma = sqrt(3) v_max dt / dx."""
+    tau = 0.5 + 3.0 * nu * dt / (dx * dx)
+    ma = math.sqrt(3.0) * v_max * dt / dx
+    return tau, ma
+
+
+def physical_step(dx, nu, tau):
+    """Time step [s] that makes relaxation time tau reproduce viscosity nu at spacing dx."""
+    if not tau > 0.5:
+        raise ValueError("tau must exceed 1/2")
+    return (tau - 0.5) * dx * dx / (3.0 * nu)
+
+
+def lattice_speed(v_phys, dx, dt):
+    """A physical speed [m/s] in lattice units (dx per dt)."""
+    return v_phys * dt / dx
+
+
+class _CellIndex:
+    """Sites bucketed into cubes of side C for bounding-box queries."""
+
+    C = 16
+
+    def __init__(self, xyz):
+        c = (np.asarray(xyz, np.int64) // self.C)
+        self.key = (c[:, 0] << 42) | (c[:, 1] << 21) | c[:, 2]
+        self.order = np.argsort(self.key, kind="stable")
+        self.sorted = self.key[self.order]
+
+    def query(self, lo, hi):
+        lo = np.floor(np.asarray(lo) / self.C).astype(np.int64)
+        hi = np.floor(np.asarray(hi) / self.C).astype(np.int64)
+        out = []
+        for cx in range(lo[0], hi[0] + 1):
+            for cy in range(lo[1], hi[1] + 1):
+                for cz in range(lo[2], hi[2] + 1):
+                    k = (cx << 42) | (cy << 21) | cz
+                    a, b = np.searchsorted(self.sorted, [k, k + 1])
+                    if b > a:
+                        out.append(self.order[a:b])
+        return np.concatenate(out) if out else np.zeros(0, np.int64)
+
+
+def velocity_vs_area(geo, fields, xyz, arterial_negative=False):
+    """Rows (segment, area, mean |u|, sites) for every segment of a seeded tree.
+
+    geo: the synth.tree geometry (its segment end points in the lattice frame are
+    in ``geo.meta["segments"]``); fields: (n, 4) macroscopic fields in canonical
+    order; xyz: (n, 3) canonical site coordinates (``Domain.sites()``)."""
+    if geo.meta.get("kind") != "tree":
+        raise ValueError("velocity_vs_area needs a seeded tree geometry")
+    fields = np.asarray(fields)
+    cells = _CellIndex(xyz)
+    rows = []
+    for n, ((p, q), r) in enumerate(zip(geo.meta["segments"], geo.meta["radii"])):
+        p, q = np.array(p), np.array(q)
+        a = (q - p) / np.linalg.norm(q - p)
+        mid = 0.5 * (p + q)
+        cand = cells.query(mid - (r + 2.0), mid + (r + 2.0))
+        rel = xyz[cand].astype(np.float64) - mid
+        along = rel @ a
+        near = np.abs(along) <= 0.5
+        perp2 = (rel[near] ** 2).sum(1) - along[near] ** 2
+        sel = cand[near][perp2 <= (r + 1.0) ** 2]
+        if sel.size == 0:
+            continue
+        speed = np.linalg.norm(fields[sel, 1:4].astype(np.float64), axis=1)
+        area = float(sel.size)
+        rows.append((n, -area if arterial_negative else area, float(speed.mean()), int(sel.size)))
+    return np.array(rows, dtype=np.float64).reshape(-1, 4)

@@ -15,6 +15,7 @@ same shape as the plain run before it).
 """
 from __future__ import annotations
 
+import hashlib
 import json
 import os
 
@@ -23,7 +24,9 @@ DEFAULT_CANDIDATES = (
     (128, 1, 1), (128, 2, 1), (256, 2, 1), (64, 2, 1),
     (128, 2, 2), (256, 2, 2), (256, 1, 2),  # variant 2: AA scheme only
     (256, 1, 3), (128, 1, 3), (256, 2, 3),
+    (128, 1, 4), (256, 1, 4), (512, 1, 4),  # variant 4: AA scheme only
 )
+AA_ONLY = (2, 4)
 
 
 def _cache_path():
@@ -31,7 +34,7 @@ def _cache_path():
                           os.path.join(os.path.expanduser("~"), ".cache", "hemegb", "tune.json"))
 
 
-def _key(ctx):
+def _key(ctx, candidates):
     try:
         import torch
 
@@ -39,7 +42,8 @@ def _key(ctx):
     except Exception:
         dev = "cuda"
     sizes = ",".join(str(d.n) for d in ctx.domains)
-    return f"{dev}|storage={ctx.storage}|scheme={ctx.scheme}|sites={sizes}"
+    cands = hashlib.sha1(repr(sorted(tuple(c) for c in candidates)).encode()).hexdigest()[:8]
+    return f"{dev}|storage={ctx.storage}|scheme={ctx.scheme}|sites={sizes}|candidates={cands}"
 
 
 def _load():
@@ -68,15 +72,15 @@ def autotune(ctx, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2, use_cache=T
     """Pick the fastest launch shape for `ctx`; returns (best, {candidate: ms per launch})."""
     if not ctx.domains:
         raise ValueError("autotune needs at least one domain in the context")
-    key = _key(ctx)
+    if ctx.scheme != 1:
+        candidates = [c for c in candidates if c[2] not in AA_ONLY]
+    key = _key(ctx, candidates)
     if use_cache:
         hit = _load().get(key)
         if hit:
             best = tuple(hit["best"])
             ctx.set_launch(*best)
             return best, {tuple(int(x) for x in k.split("x")): v for k, v in hit["ms"].items()}
-    if ctx.scheme != 1:
-        candidates = [c for c in candidates if c[2] != 2]
     steps += steps & 1  # balance odd and even steps of the AA scheme
     saved = [(d, d.save_state()) for d in ctx.domains]
     timing = {}

@@ -9,6 +9,12 @@
 // Stepping: per set of domains a plan holds the stream-collide tile table,
 // the per-iolet update table and a captured CUDA graph of G steps; kernels
 // read the step parity from device counters, so the graph replays unchanged.
+//
+// Threads: hg_domain_create may run on one thread while another drives the
+// same context (steps, reads, destroys).  The context's mutex guards the slot
+// table and the coupling map; a build uploads on a stream of its own and
+// publishes its slot only once every copy has landed.  Error messages are kept
+// per thread.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -19,6 +25,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -251,8 +258,9 @@ struct PlanKey {
 
 struct Plan {
     std::vector<int32_t> doms;
-    DevBuf tiles, ios, adv, chunks, partials, counters;
+    DevBuf tiles, ios, adv, chunks, partials, counters, rev, fslots;
     int64_t n_tiles = 0;
+    int n_fslots = 0;  // (domain, slot) pairs the body-force pass visits
     int n_ios = 0;
     int n_chunks = 0;
     cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};  // by parity mode
@@ -272,16 +280,18 @@ struct hg_ctx {
     hg_alloc_fn alloc = nullptr;
     hg_free_fn free_fn = nullptr;
     void *alloc_user = nullptr;
-    std::string err;
+    std::mutex mu;                  // guards doms, reserved, coupled
     std::vector<hg_domain *> doms;  // by index (nullptr = free slot)
+    std::vector<char> reserved;     // slots held by builds in progress
     DevBuf dom_table;               // DomDev[capacity]
     DevBuf errw;                    // device error word (bounded waits that gave up)
     DevBuf steps;                   // int64[capacity]
     int capacity = 0;
     std::map<std::pair<int32_t, int32_t>, CoupleSrc> coupled;  // (dst dom, dst k) -> source
+    int couple_mode = HG_COUPLE_FORWARD;
     std::map<PlanKey, std::unique_ptr<Plan>> plans;
     DevBuf scratch;                 // mass partials, read-back staging
-    int64_t device_bytes = 0;
+    std::atomic<int64_t> device_bytes{0};
 };
 
 struct hg_domain {
@@ -296,6 +306,9 @@ struct hg_domain {
     std::vector<hg_iolet> io;
     std::vector<int32_t> io_ptr;        // CSR over slots per iolet
     DevBuf f[2], nbr, iomask, ioprefix, io_codes, bnd, coef, bcv, io_kind, M, slots;
+    DevBuf force;                        // per iolet: body-force density (float4), reverse exchange
+    DevBuf slot_site;                    // per slot: device site index
+    std::vector<int32_t> slots_host;     // per-iolet CSR of slots (io_ptr), host copy
     std::vector<int32_t> io_codes_host;  // per slot x 18, canonical codes
     std::vector<int32_t> slot_of_site;   // canonical site -> slot or -1
     int64_t bytes = 0;
@@ -303,15 +316,18 @@ struct hg_domain {
 
 namespace {
 
+// last failure of the calling thread and the context it concerned
+thread_local const hg_ctx *t_err_ctx = nullptr;
+thread_local std::string t_err;
+
 int fail(hg_ctx *ctx, int code, const char *fmt, ...) {
-    if (ctx) {
-        char buf[512];
-        va_list ap;
-        va_start(ap, fmt);
-        vsnprintf(buf, sizeof buf, fmt, ap);
-        va_end(ap);
-        ctx->err = buf;
-    }
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    t_err_ctx = ctx;
+    t_err = buf;
     return code;
 }
 
@@ -356,7 +372,7 @@ void drop_plans(hg_ctx *ctx) {
         Plan &p = *kv.second;
         for (auto &g : p.graph)
             if (g) cudaGraphExecDestroy(g);
-        for (DevBuf *b : {&p.tiles, &p.ios, &p.adv, &p.chunks, &p.partials, &p.counters})
+        for (DevBuf *b : {&p.tiles, &p.ios, &p.adv, &p.chunks, &p.partials, &p.counters, &p.rev, &p.fslots})
             dev_free(ctx, *b);
     }
     ctx->plans.clear();
@@ -371,10 +387,17 @@ DomDev make_domdev(hg_ctx *ctx, hg_domain *d) {
     D.iomask = (const uint32_t *)d->iomask.p;
     D.ioprefix = (const int32_t *)d->ioprefix.p;
     D.io_codes = (const int32_t *)d->io_codes.p;
+    D.slot_site = (const int32_t *)d->slot_site.p;
     D.bnd = (float4 *)d->bnd.p;
     D.coef = (const float *)d->coef.p;
     D.bcv = (const float *)d->bcv.p;
     D.io_kind = (const int8_t *)d->io_kind.p;
+    D.io_force = nullptr;
+    if (ctx->couple_mode == HG_COUPLE_ALTERNATE) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (const auto &kv : ctx->coupled)
+            if (kv.second.src_dom == d->idx) D.io_force = (const float4 *)d->force.p;
+    }
     D.step = (const int64_t *)ctx->steps.p + d->idx;
     D.err = (int32_t *)ctx->errw.p;
     D.n = d->n;
@@ -384,11 +407,40 @@ DomDev make_domdev(hg_ctx *ctx, hg_domain *d) {
     return D;
 }
 
+// Rewrite every live domain's descriptor (stream-ordered): after a change of
+// coupling or coupling mode, which decides whether a domain is forced.
+cudaError_t refresh_domdevs(hg_ctx *ctx) {
+    std::vector<hg_domain *> live;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (hg_domain *d : ctx->doms)
+            if (d) live.push_back(d);
+    }
+    for (hg_domain *d : live) {
+        const DomDev D = make_domdev(ctx, d);
+        cudaError_t e = cudaMemcpyAsync((DomDev *)ctx->dom_table.p + d->idx, &D, sizeof D,
+                                        cudaMemcpyHostToDevice, ctx->stream);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaStreamSynchronize(ctx->stream);
+}
+
 const DomDev *domdev_ptr(hg_domain *d) {
     return (const DomDev *)d->ctx->dom_table.p + d->idx;
 }
 
 size_t elem_bytes(int storage) { return storage == HG_STORE_F32 ? 4 : 2; }
+
+// Kernel variants and the launch shapes each supports (see hg_ctx_params).
+bool variant_ok(int scheme, int spt, int variant) {
+    switch (variant) {
+        case 0: case 3: return true;
+        case 1: return spt != 4;
+        case 2: return spt != 4 && scheme == HG_SCHEME_AA;
+        case 4: return spt == 1 && scheme == HG_SCHEME_AA;
+        default: return false;
+    }
+}
 
 int ensure_scratch(hg_ctx *ctx, size_t bytes) {
     if (ctx->scratch.bytes >= bytes) return HG_OK;
@@ -411,10 +463,7 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     int spt = p->sites_per_thread ? p->sites_per_thread : 1;
     if (block < 32 || block > 512 || block % 32) return HG_ERR_ARG;
     if (spt != 1 && spt != 2 && spt != 4) return HG_ERR_ARG;
-    if (p->kernel_variant < 0 || p->kernel_variant > 3 ||
-        ((p->kernel_variant == 1 || p->kernel_variant == 2) && spt == 4) ||
-        (p->kernel_variant == 2 && p->scheme != HG_SCHEME_AA))
-        return HG_ERR_ARG;
+    if (!variant_ok(p->scheme, spt, p->kernel_variant)) return HG_ERR_ARG;
     if ((p->alloc == nullptr) != (p->free == nullptr)) return HG_ERR_ARG;
     std::unique_ptr<hg_ctx> c(new hg_ctx);
     c->device = p->device;
@@ -449,6 +498,8 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     if (cudaMemsetAsync(c->steps.p, 0, c->steps.bytes, c->stream) != cudaSuccess) return HG_ERR_CUDA;
     if (cudaMemsetAsync(c->errw.p, 0, c->errw.bytes, c->stream) != cudaSuccess) return HG_ERR_CUDA;
     c->doms.assign(c->capacity, nullptr);
+    c->reserved.assign(c->capacity, 0);
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HG_ERR_CUDA;
     *out = c.release();
     return HG_OK;
 }
@@ -471,15 +522,20 @@ int hg_ctx_destroy(hg_ctx *ctx) {
     return HG_OK;
 }
 
-const char *hg_last_error(hg_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+const char *hg_last_error(hg_ctx *ctx) {
+    if (!ctx) return "null context";
+    return t_err_ctx == ctx ? t_err.c_str() : "";
+}
 
 int hg_sync(hg_ctx *ctx) {
     if (!ctx) return HG_ERR_ARG;
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     int32_t e = 0;
-    CU(ctx, cudaMemcpy(&e, ctx->errw.p, sizeof e, cudaMemcpyDeviceToHost));
+    CU(ctx, cudaMemcpyAsync(&e, ctx->errw.p, sizeof e, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
     if (e) {
-        CU(ctx, cudaMemset(ctx->errw.p, 0, sizeof e));
+        CU(ctx, cudaMemsetAsync(ctx->errw.p, 0, sizeof e, ctx->stream));
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
         return fail(ctx, HG_ERR_TIMEOUT, "a bounded device wait gave up (code %d); the state is not trusted", e);
     }
     return HG_OK;
@@ -500,14 +556,27 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     if (lb && lb->ordering != HG_ORDER_MORTON) return fail(ctx, HG_ERR_ARG, "unknown ordering");
     for (int k = 0; k < nio; ++k)
         if (!iolet_ok(iolets[k])) return fail(ctx, HG_ERR_ARG, "iolet %d out of range", k);
-    int slot_idx = -1;
-    for (int i = 0; i < ctx->capacity; ++i)
-        if (!ctx->doms[i]) {
-            slot_idx = i;
-            break;
-        }
-    if (slot_idx < 0) return fail(ctx, HG_ERR_STATE, "context holds too many domains");
     CU(ctx, cudaSetDevice(ctx->device));
+    int slot_idx = -1;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (int i = 0; i < ctx->capacity; ++i)
+            if (!ctx->doms[i] && !ctx->reserved[i]) {
+                slot_idx = i;
+                ctx->reserved[i] = 1;
+                break;
+            }
+    }
+    if (slot_idx < 0) return fail(ctx, HG_ERR_STATE, "context holds too many domains");
+    // the slot returns to the pool unless the build publishes it
+    struct SlotGuard {
+        hg_ctx *ctx;
+        int idx;
+        ~SlotGuard() {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->reserved[idx] = 0;
+        }
+    } slot_guard{ctx, slot_idx};
 
     std::unique_ptr<hg_domain> d(new hg_domain);
     d->ctx = ctx;
@@ -665,8 +734,12 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
                 v = (int32_t)(s + d * np);
             }
     });
+    std::vector<int32_t> slot_site((size_t)std::max<int64_t>(1, n_adj), 0);
+    for (int64_t s = 0; s < n; ++s)
+        if (slot_of[s] >= 0) slot_site[slot_of[s]] = (int32_t)s;
     d->io_codes_host = codes;
     d->slot_of_site = slot_of;
+    d->slots_host = slots;
 
     // --- device buffers
     hg_ctx *c = ctx;
@@ -688,9 +761,12 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     A(d->io_kind, (size_t)std::max(1, nio));
     A(d->M, (size_t)std::max(1, nio) * 24);
     A(d->slots, slots.size() * 4);
+    A(d->force, (size_t)std::max(1, nio) * 16);
+    A(d->slot_site, slot_site.size() * 4);
     auto cleanup = [&] {
         DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
-                        &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots};
+                        &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force,
+                        &d->slot_site};
         for (DevBuf *b : bs) dev_free(c, *b);
     };
     if (rc != HG_OK) {
@@ -698,7 +774,8 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         return rc;
     }
     for (DevBuf *b : {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
-                      &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots})
+                      &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force,
+                        &d->slot_site})
         d->bytes += (int64_t)b->bytes;
     std::vector<float> bcv(std::max(1, nio), 0.0f);
     std::vector<int8_t> kinds(std::max(1, nio), 0);
@@ -706,9 +783,12 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         bcv[k] = (float)(iolets[k].value * pulse(iolets[k].pulse, 1.0, iolets[k].period));
         kinds[k] = (int8_t)iolets[k].kind;
     }
-    cudaError_t e = cudaSuccess;
+    // uploads run on a stream of this build, so a build on another thread
+    // neither waits for nor races with the context's stream
+    cudaStream_t up = nullptr;
+    cudaError_t e = cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking);
     auto H2D = [&](DevBuf &b, const void *src, size_t bytes) {
-        if (e == cudaSuccess) e = cudaMemcpy(b.p, src, bytes, cudaMemcpyHostToDevice);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, up);
     };
     H2D(d->nbr, nbr.data(), nbr.size() * 4);
     H2D(d->iomask, mask.data(), mask.size() * 4);
@@ -718,19 +798,29 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     H2D(d->bcv, bcv.data(), bcv.size() * 4);
     H2D(d->io_kind, kinds.data(), kinds.size());
     H2D(d->slots, slots.data(), slots.size() * 4);
-    if (e == cudaSuccess) e = cudaMemset(d->f[0].p, 0, d->f[0].bytes);
-    if (e == cudaSuccess && d->f[1].p) e = cudaMemset(d->f[1].p, 0, d->f[1].bytes);
-    if (e == cudaSuccess) e = cudaMemset(d->bnd.p, 0, d->bnd.bytes);
-    if (e == cudaSuccess) e = cudaMemset(d->M.p, 0, d->M.bytes);
-    if (e == cudaSuccess) e = cudaMemset((int64_t *)ctx->steps.p + slot_idx, 0, sizeof(int64_t));
+    H2D(d->slot_site, slot_site.data(), slot_site.size() * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->f[0].p, 0, d->f[0].bytes, up);
+    if (e == cudaSuccess && d->f[1].p) e = cudaMemsetAsync(d->f[1].p, 0, d->f[1].bytes, up);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->bnd.p, 0, d->bnd.bytes, up);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->M.p, 0, d->M.bytes, up);
+    if (e == cudaSuccess) e = cudaMemsetAsync(d->force.p, 0, d->force.bytes, up);
+    if (e == cudaSuccess) e = cudaMemsetAsync((int64_t *)ctx->steps.p + slot_idx, 0, sizeof(int64_t), up);
     DomDev D = make_domdev(ctx, d.get());
     if (e == cudaSuccess)
-        e = cudaMemcpy((DomDev *)ctx->dom_table.p + slot_idx, &D, sizeof D, cudaMemcpyHostToDevice);
+        e = cudaMemcpyAsync((DomDev *)ctx->dom_table.p + slot_idx, &D, sizeof D, cudaMemcpyHostToDevice, up);
+    if (up) {
+        const cudaError_t es = cudaStreamSynchronize(up);
+        if (e == cudaSuccess) e = es;
+        cudaStreamDestroy(up);
+    }
     if (e != cudaSuccess) {
         cleanup();
         return fail(ctx, HG_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
     }
-    ctx->doms[slot_idx] = d.get();
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        ctx->doms[slot_idx] = d.get();
+    }
     *out = d.release();
     return HG_OK;
 }
@@ -741,14 +831,19 @@ int hg_domain_destroy(hg_domain *d) {
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
     drop_plans(ctx);
-    for (auto it = ctx->coupled.begin(); it != ctx->coupled.end();) {
-        if (it->first.first == d->idx || it->second.src_dom == d->idx) it = ctx->coupled.erase(it);
-        else ++it;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (auto it = ctx->coupled.begin(); it != ctx->coupled.end();) {
+            if (it->first.first == d->idx || it->second.src_dom == d->idx) it = ctx->coupled.erase(it);
+            else ++it;
+        }
+        ctx->doms[d->idx] = nullptr;
     }
     DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
-                    &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots};
+                    &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force,
+                        &d->slot_site};
     for (DevBuf *b : bs) dev_free(ctx, *b);
-    ctx->doms[d->idx] = nullptr;
+    if (ctx->couple_mode == HG_COUPLE_ALTERNATE) refresh_domdevs(ctx);  // a source may have lost its pairs
     delete d;
     return HG_OK;
 }
@@ -800,8 +895,12 @@ int hg_couple(hg_ctx *ctx, hg_domain *src, hg_domain *dst, const hg_pair *pairs,
             return fail(ctx, HG_ERR_ARG, "pair %d: iolet index out of range", j);
         if (dst->io[p.dst_iolet].kind != HG_VELOCITY)
             return fail(ctx, HG_ERR_ARG, "pair %d: destination iolet is not a velocity iolet", j);
-        if (ctx->coupled.count({dst->idx, p.dst_iolet}))
-            return fail(ctx, HG_ERR_ARG, "pair %d: destination iolet already coupled", j);
+        bool taken;
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            taken = ctx->coupled.count({dst->idx, p.dst_iolet}) != 0;
+        }
+        if (taken) return fail(ctx, HG_ERR_ARG, "pair %d: destination iolet already coupled", j);
         for (int q = 0; q < j; ++q)
             if (pairs[q].dst_iolet == p.dst_iolet)
                 return fail(ctx, HG_ERR_ARG, "pair %d: destination iolet repeated", j);
@@ -811,14 +910,40 @@ int hg_couple(hg_ctx *ctx, hg_domain *src, hg_domain *dst, const hg_pair *pairs,
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     // the next step's value follows the source's current mean at once
     std::vector<double> Ms((size_t)std::max(1, src->nio) * 3);
-    CU(ctx, cudaMemcpy(Ms.data(), src->M.p, Ms.size() * 8, cudaMemcpyDeviceToHost));
+    CU(ctx, cudaMemcpyAsync(Ms.data(), src->M.p, Ms.size() * 8, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<float> v(std::max(1, n));
     for (int j = 0; j < n; ++j) {
         const hg_pair &p = pairs[j];
-        ctx->coupled[{dst->idx, p.dst_iolet}] = {src->idx, p.src_iolet, p.factor};
-        const float v = (float)(p.factor * Ms[3 * p.src_iolet]);
-        CU(ctx, cudaMemcpy((float *)dst->bcv.p + p.dst_iolet, &v, 4, cudaMemcpyHostToDevice));
+        {
+            std::lock_guard<std::mutex> lk(ctx->mu);
+            ctx->coupled[{dst->idx, p.dst_iolet}] = {src->idx, p.src_iolet, p.factor};
+        }
+        v[j] = (float)(p.factor * Ms[3 * p.src_iolet]);
+        CU(ctx, cudaMemcpyAsync((float *)dst->bcv.p + p.dst_iolet, &v[j], 4, cudaMemcpyHostToDevice, ctx->stream));
     }
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
     drop_plans(ctx);
+    CU(ctx, refresh_domdevs(ctx));
+    return HG_OK;
+}
+
+int hg_set_coupling_mode(hg_ctx *ctx, int32_t mode) {
+    if (!ctx) return HG_ERR_ARG;
+    if (mode != HG_COUPLE_FORWARD && mode != HG_COUPLE_ALTERNATE)
+        return fail(ctx, HG_ERR_ARG, "unknown coupling mode %d", mode);
+    CU(ctx, cudaSetDevice(ctx->device));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<hg_domain *> live;
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (hg_domain *d : ctx->doms)
+            if (d) live.push_back(d);
+    }
+    for (hg_domain *d : live) CU(ctx, cudaMemsetAsync(d->force.p, 0, d->force.bytes, ctx->stream));
+    ctx->couple_mode = mode;
+    drop_plans(ctx);
+    CU(ctx, refresh_domdevs(ctx));
     return HG_OK;
 }
 
@@ -914,6 +1039,15 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     std::vector<IoDev> ios;
     std::vector<int2> chunks;
     std::vector<std::pair<int32_t, int32_t>> io_key;  // (domain, iolet) of each IoDev
+    std::vector<RevSrc> rev;
+    std::vector<int2> forced;                          // (domain, slot) under a body force
+    std::vector<std::pair<size_t, int32_t>> rev_of;    // per IoDev: (first RevSrc, count)
+    std::map<std::pair<int32_t, int32_t>, std::vector<std::pair<int32_t, int32_t>>> fed;  // source -> inlets
+    if (ctx->couple_mode == HG_COUPLE_ALTERNATE) {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (const auto &kv : ctx->coupled)
+            fed[{kv.second.src_dom, kv.second.src_k}].push_back(kv.first);
+    }
     for (int32_t di : doms) {
         hg_domain *d = ctx->doms[di];
         for (int64_t s = 0; s < d->n; s += ts) {
@@ -944,18 +1078,52 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
             I.n_chunks = std::max(1, (I.n_slots + kIoChunk - 1) / kIoChunk);
             I.part0 = (int32_t)chunks.size();
             for (int c = 0; c < I.n_chunks; ++c) chunks.push_back(make_int2((int)ios.size(), c));
-            auto cp = ctx->coupled.find({di, k});
-            if (cp != ctx->coupled.end()) {
-                hg_domain *sd = ctx->doms[cp->second.src_dom];
-                if (std::find(doms.begin(), doms.end(), cp->second.src_dom) == doms.end())
+            bool is_coupled = false;
+            CoupleSrc cs{};
+            {
+                std::lock_guard<std::mutex> lk(ctx->mu);
+                auto cp = ctx->coupled.find({di, k});
+                if (cp != ctx->coupled.end()) {
+                    is_coupled = true;
+                    cs = cp->second;
+                }
+            }
+            if (is_coupled) {
+                hg_domain *sd = ctx->doms[cs.src_dom];
+                if (std::find(doms.begin(), doms.end(), cs.src_dom) == doms.end())
                     return fail(ctx, HG_ERR_ARG, "a coupled source domain is not being stepped");
                 I.coupled = 1;
-                I.factor = cp->second.factor;
-                I.src_M = (const double *)sd->M.p + 3 * cp->second.src_k;
+                I.factor = cs.factor;
+                I.src_M = (const double *)sd->M.p + 3 * cs.src_k;
             }
+            I.force = (float4 *)d->force.p + k;
+            I.alternate = ctx->couple_mode == HG_COUPLE_ALTERNATE;
+            auto fd = fed.find({di, k});
+            size_t r0 = rev.size();
+            if (fd != fed.end()) {
+                for (const auto &dst : fd->second) {
+                    if (std::find(doms.begin(), doms.end(), dst.first) == doms.end())
+                        return fail(ctx, HG_ERR_ARG, "a coupled destination domain is not being stepped");
+                    double f;
+                    {
+                        std::lock_guard<std::mutex> lk(ctx->mu);
+                        f = ctx->coupled.at(dst).factor;
+                    }
+                    rev.push_back(RevSrc{(const double *)ctx->doms[dst.first]->M.p + 3 * dst.second, f});
+                }
+            }
+            rev_of.push_back({r0, (int32_t)(rev.size() - r0)});
+            if (fd != fed.end())  // the outlet's adjacent slots take its body force
+                for (int64_t q = d->io_ptr[k]; q < d->io_ptr[k + 1]; ++q)
+                    forced.push_back(make_int2(di, d->slots_host[q]));
             ios.push_back(I);
         }
     }
+    std::sort(forced.begin(), forced.end(),
+              [](int2 a, int2 b) { return a.x != b.x ? a.x < b.x : a.y < b.y; });
+    forced.erase(std::unique(forced.begin(), forced.end(),
+                             [](int2 a, int2 b) { return a.x == b.x && a.y == b.y; }),
+                 forced.end());
     p->n_tiles = (int64_t)tiles.size();
     p->n_ios = (int)ios.size();
     p->n_chunks = (int)chunks.size();
@@ -965,18 +1133,38 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     if (rc == HG_OK) rc = dev_alloc(ctx, p->chunks, std::max<size_t>(1, chunks.size()) * sizeof(int2));
     if (rc == HG_OK) rc = dev_alloc(ctx, p->partials, std::max<size_t>(1, chunks.size()) * sizeof(double2));
     if (rc == HG_OK) rc = dev_alloc(ctx, p->counters, (ios.size() + 1) * sizeof(unsigned));
+    if (rc == HG_OK) rc = dev_alloc(ctx, p->rev, std::max<size_t>(1, rev.size()) * sizeof(RevSrc));
+    if (rc == HG_OK) rc = dev_alloc(ctx, p->fslots, std::max<size_t>(1, forced.size()) * sizeof(int2));
+    p->n_fslots = (int)forced.size();
     if (rc != HG_OK) {
-        for (DevBuf *b : {&p->tiles, &p->ios, &p->adv, &p->chunks, &p->partials, &p->counters})
+        for (DevBuf *b : {&p->tiles, &p->ios, &p->adv, &p->chunks, &p->partials, &p->counters, &p->rev, &p->fslots})
             dev_free(ctx, *b);
         return rc;
     }
-    cudaError_t e = cudaMemset(p->counters.p, 0, p->counters.bytes);
-    if (!tiles.empty()) e = cudaMemcpy(p->tiles.p, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess && !ios.empty()) e = cudaMemcpy(p->ios.p, ios.data(), ios.size() * sizeof(IoDev), cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaMemcpy(p->adv.p, doms.data(), doms.size() * 4, cudaMemcpyHostToDevice);
+    for (size_t q = 0; q < ios.size(); ++q) {
+        ios[q].rev = (const RevSrc *)p->rev.p + rev_of[q].first;
+        ios[q].n_rev = rev_of[q].second;
+    }
+    // stream-ordered before the plan's first launch (pageable sources are staged on the call)
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(p->counters.p, 0, p->counters.bytes, st);
+    if (e == cudaSuccess && !tiles.empty())
+        e = cudaMemcpyAsync(p->tiles.p, tiles.data(), tiles.size() * sizeof(TileDev), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !ios.empty())
+        e = cudaMemcpyAsync(p->ios.p, ios.data(), ios.size() * sizeof(IoDev), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->adv.p, doms.data(), doms.size() * 4, cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess && !chunks.empty())
-        e = cudaMemcpy(p->chunks.p, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice);
-    if (e != cudaSuccess) return fail(ctx, HG_ERR_CUDA, "plan upload failed: %s", cudaGetErrorString(e));
+        e = cudaMemcpyAsync(p->chunks.p, chunks.data(), chunks.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !rev.empty())
+        e = cudaMemcpyAsync(p->rev.p, rev.data(), rev.size() * sizeof(RevSrc), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess && !forced.empty())
+        e = cudaMemcpyAsync(p->fslots.p, forced.data(), forced.size() * sizeof(int2), cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        for (DevBuf *b : {&p->tiles, &p->ios, &p->adv, &p->chunks, &p->partials, &p->counters, &p->rev, &p->fslots})
+            dev_free(ctx, *b);
+        return fail(ctx, HG_ERR_CUDA, "plan upload failed: %s", cudaGetErrorString(e));
+    }
     out = p.get();
     ctx->plans[key] = std::move(p);
     return HG_OK;
@@ -1006,6 +1194,9 @@ cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
         cudaError_t e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p,
                                               (const TileDev *)p->tiles.p, p->n_tiles, (int)off,
                                               step_parity(ctx, mode, off), ctx->stream);
+        if (e != cudaSuccess) return e;
+        e = launch_guo_force(ctx->storage, ctx->scheme, (const DomDev *)ctx->dom_table.p,
+                             (const int2 *)p->fslots.p, p->n_fslots, (int)off, ctx->stream);
         if (e != cudaSuccess) return e;
         e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (const int2 *)p->chunks.p, p->n_chunks,
                                 (double2 *)p->partials.p, (unsigned *)p->counters.p, (int)off, ctx->stream);
@@ -1069,8 +1260,11 @@ extern "C" {
 int hg_step(hg_ctx *ctx, int64_t n) {
     if (!ctx) return HG_ERR_ARG;
     std::vector<int32_t> doms;
-    for (int i = 0; i < ctx->capacity; ++i)
-        if (ctx->doms[i]) doms.push_back(i);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (int i = 0; i < ctx->capacity; ++i)
+            if (ctx->doms[i]) doms.push_back(i);
+    }
     return step_set(ctx, doms, n);
 }
 
@@ -1089,8 +1283,11 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float
     if (!ctx) return HG_ERR_ARG;
     if (n < 0) return fail(ctx, HG_ERR_ARG, "negative step count");
     std::vector<int32_t> doms;
-    for (int i = 0; i < ctx->capacity; ++i)
-        if (ctx->doms[i]) doms.push_back(i);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        for (int i = 0; i < ctx->capacity; ++i)
+            if (ctx->doms[i]) doms.push_back(i);
+    }
     if (ms_sc) *ms_sc = 0.0;
     if (ms_io) *ms_io = 0.0;
     if (doms.empty() || n == 0) return HG_OK;
@@ -1108,6 +1305,9 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float
         e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
                                   p->n_tiles, (int)j, step_parity(ctx, mode, j), ctx->stream);
         cudaEventRecord(ev[3 * j + 1], ctx->stream);
+        if (e == cudaSuccess)  // the body-force pass (if any) is timed with the iolet update
+            e = launch_guo_force(ctx->storage, ctx->scheme, (const DomDev *)ctx->dom_table.p,
+                                 (const int2 *)p->fslots.p, p->n_fslots, (int)j, ctx->stream);
         if (e == cudaSuccess)
             e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (const int2 *)p->chunks.p, p->n_chunks,
                                     (double2 *)p->partials.p, (unsigned *)p->counters.p, (int)j, ctx->stream);
@@ -1142,9 +1342,9 @@ int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) 
     if (!ctx) return HG_ERR_ARG;
     if (block < 32 || block > 512 || block % 32) return fail(ctx, HG_ERR_ARG, "block size must be a multiple of 32 in [32, 512]");
     if (spt != 1 && spt != 2 && spt != 4) return fail(ctx, HG_ERR_ARG, "sites per thread must be 1, 2 or 4");
-    if (variant < 0 || variant > 3 || ((variant == 1 || variant == 2) && spt == 4) ||
-        (variant == 2 && ctx->scheme != HG_SCHEME_AA))
-        return fail(ctx, HG_ERR_ARG, "kernel variant must be 0 or 3, or 1/2 with 1 or 2 sites per thread (2: AA only)");
+    if (!variant_ok(ctx->scheme, spt, variant))
+        return fail(ctx, HG_ERR_ARG, "kernel variant must be 0 or 3, 1 or 2 with 1 or 2 sites per thread "
+                                     "(2: AA only), or 4 with 1 site per thread (AA only)");
     if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1188,6 +1388,21 @@ int hg_read_iolet_stats(hg_domain *d, double *out) {
     return HG_OK;
 }
 
+int hg_read_iolet_forces(hg_domain *d, float *out) {
+    if (!d || (!out && d->nio)) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    std::vector<float4> f((size_t)std::max(1, d->nio));
+    if (d->nio) CU(ctx, cudaMemcpyAsync(f.data(), d->force.p, (size_t)d->nio * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    for (int k = 0; k < d->nio; ++k) {
+        out[3 * k] = f[k].x;
+        out[3 * k + 1] = f[k].y;
+        out[3 * k + 2] = f[k].z;
+    }
+    return HG_OK;
+}
+
 int hg_read_boundary_values(hg_domain *d, float *out) {
     if (!d || (!out && d->nio)) return HG_ERR_ARG;
     hg_ctx *ctx = d->ctx;
@@ -1211,7 +1426,8 @@ int hg_mass(hg_domain *d, double *out) {
     return HG_OK;
 }
 
-// checkpoint layout: header | bcv[nio] f32 | M[nio*3] f64 | F[19][n] storage
+// checkpoint layout: header | bcv[nio] f32 | M[nio*3] f64 | F[19][n] storage |
+// force[nio] float4 (body-force densities of the reverse coupling exchange)
 struct StateHeader {
     char magic[8];
     int64_t n, step;
@@ -1221,7 +1437,7 @@ struct StateHeader {
 int hg_state_bytes(hg_domain *d, int64_t *bytes) {
     if (!d || !bytes) return HG_ERR_ARG;
     *bytes = (int64_t)sizeof(StateHeader) + (int64_t)d->nio * 4 + (int64_t)d->nio * 24 +
-             19 * d->n * (int64_t)elem_bytes(d->ctx->storage);
+             19 * d->n * (int64_t)elem_bytes(d->ctx->storage) + (int64_t)d->nio * 16;
     return HG_OK;
 }
 
@@ -1253,19 +1469,20 @@ int hg_save_state(hg_domain *d, void *buf, int64_t bytes) {
     h.nio = d->nio;
     h.storage = ctx->storage;
     h.scheme = ctx->scheme;
-    h.version = 1;
+    h.version = 2;
     char *p = (char *)buf;
     memcpy(p, &h, sizeof h);
     p += sizeof h;
     CU(ctx, cudaSetDevice(ctx->device));
-    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    const size_t fb = 19 * (size_t)d->n * elem_bytes(ctx->storage);
     if (d->nio) {
-        CU(ctx, cudaMemcpy(p, d->bcv.p, (size_t)d->nio * 4, cudaMemcpyDeviceToHost));
+        CU(ctx, cudaMemcpyAsync(p, d->bcv.p, (size_t)d->nio * 4, cudaMemcpyDeviceToHost, ctx->stream));
         p += (size_t)d->nio * 4;
-        CU(ctx, cudaMemcpy(p, d->M.p, (size_t)d->nio * 24, cudaMemcpyDeviceToHost));
+        CU(ctx, cudaMemcpyAsync(p, d->M.p, (size_t)d->nio * 24, cudaMemcpyDeviceToHost, ctx->stream));
         p += (size_t)d->nio * 24;
+        CU(ctx, cudaMemcpyAsync(p + fb, d->force.p, (size_t)d->nio * 16, cudaMemcpyDeviceToHost, ctx->stream));
     }
-    return hg_read_state(d, p);
+    return hg_read_state(d, p);  // synchronises the stream
 }
 
 int hg_load_state(hg_domain *d, const void *buf, int64_t bytes) {
@@ -1276,26 +1493,28 @@ int hg_load_state(hg_domain *d, const void *buf, int64_t bytes) {
     if (bytes < need) return fail(ctx, HG_ERR_ARG, "buffer too small");
     StateHeader h;
     memcpy(&h, buf, sizeof h);
-    if (memcmp(h.magic, "HEMEGB1", 8) != 0 || h.version != 1)
+    if (memcmp(h.magic, "HEMEGB1", 8) != 0 || h.version != 2)
         return fail(ctx, HG_ERR_ARG, "not a hemegb state");
     if (h.n != d->n || h.nio != d->nio || h.storage != ctx->storage || h.scheme != ctx->scheme)
         return fail(ctx, HG_ERR_ARG, "state does not match this domain (sites, iolets, storage or scheme)");
     if (h.step < 0) return fail(ctx, HG_ERR_ARG, "negative step");
     const char *p = (const char *)buf + sizeof h;
     CU(ctx, cudaSetDevice(ctx->device));
-    CU(ctx, cudaStreamSynchronize(ctx->stream));
-    if (d->nio) {
-        CU(ctx, cudaMemcpy(d->bcv.p, p, (size_t)d->nio * 4, cudaMemcpyHostToDevice));
-        p += (size_t)d->nio * 4;
-        CU(ctx, cudaMemcpy(d->M.p, p, (size_t)d->nio * 24, cudaMemcpyHostToDevice));
-        p += (size_t)d->nio * 24;
-    }
-    CU(ctx, cudaMemcpy((int64_t *)ctx->steps.p + d->idx, &h.step, 8, cudaMemcpyHostToDevice));
-    d->step = h.step;
     const size_t fb = 19 * (size_t)d->n * elem_bytes(ctx->storage);
     int rc = ensure_scratch(ctx, std::max<size_t>(fb, 16));
     if (rc != HG_OK) return rc;
-    if (fb) CU(ctx, cudaMemcpy(ctx->scratch.p, p, fb, cudaMemcpyHostToDevice));
+    // every copy is ordered on the context's stream ahead of the import kernel
+    if (d->nio) {
+        CU(ctx, cudaMemcpyAsync(d->bcv.p, p, (size_t)d->nio * 4, cudaMemcpyHostToDevice, ctx->stream));
+        p += (size_t)d->nio * 4;
+        CU(ctx, cudaMemcpyAsync(d->M.p, p, (size_t)d->nio * 24, cudaMemcpyHostToDevice, ctx->stream));
+        p += (size_t)d->nio * 24;
+        CU(ctx, cudaMemcpyAsync(d->force.p, p + fb, (size_t)d->nio * 16, cudaMemcpyHostToDevice, ctx->stream));
+    }
+    const int64_t step = h.step;
+    CU(ctx, cudaMemcpyAsync((int64_t *)ctx->steps.p + d->idx, &step, 8, cudaMemcpyHostToDevice, ctx->stream));
+    d->step = h.step;
+    if (fb) CU(ctx, cudaMemcpyAsync(ctx->scratch.p, p, fb, cudaMemcpyHostToDevice, ctx->stream));
     CU(ctx, launch_import_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, nullptr, ctx->scratch.p,
                                 ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));

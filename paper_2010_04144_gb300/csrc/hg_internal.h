@@ -26,10 +26,12 @@ struct DomDev {
     const uint32_t *iomask;   // bit s: site s has an iolet link
     const int32_t *ioprefix;  // per 32-site word: flagged sites before it (slot = rank of the flag)
     const int32_t *io_codes;  // per slot x 18: canonical codes (-1 wall, -(2+k) iolet, >= 0 fluid)
+    const int32_t *slot_site; // per slot: the site's device index
     float4 *bnd;              // per adjacent slot: (drho, ux, uy, uz) of the step's G_t
     const float *coef;        // per adjacent slot x 18: velocity-link coefficient 6 w_i c_i.(-a) phi
     const float *bcv;         // per iolet: boundary value of the step being run
     const int8_t *io_kind;    // per iolet: 0 pressure, 1 velocity
+    const float4 *io_force;   // per iolet: body-force density on its adjacent sites (null = none)
     const int64_t *step;      // completed steps before the current launch group
     int32_t *err;             // context error word: set when a bounded device wait gives up
     int64_t n;                // sites
@@ -45,6 +47,12 @@ struct TileDev {
     int64_t start;
 };
 
+// A venous inlet fed by an arterial outlet, seen from the outlet (reverse exchange).
+struct RevSrc {
+    const double *M;          // the inlet's means (mean u.n first)
+    double factor;            // the pair's velocity factor
+};
+
 // Per-iolet work of the iolet-update kernel (reduction + next boundary value).
 struct IoDev {
     const int32_t *slots;     // adjacent-site slots of this iolet, canonical order
@@ -53,6 +61,8 @@ struct IoDev {
     double *M;                // out: (mean u.n, mean drho, count)
     float *bcv;               // out: boundary value for the next step
     const int64_t *step;      // owner's completed-step counter
+    const RevSrc *rev;        // inlets this outlet feeds (reverse exchange), n_rev of them
+    float4 *force;            // out (reverse exchange): this iolet's body-force density
     double nx, ny, nz;        // unit outward axis
     double value, period, factor;
     int32_t n_slots;
@@ -60,6 +70,8 @@ struct IoDev {
     int32_t part0;            // first partial of this iolet in the plan's partials array
     int32_t pulse;
     int32_t coupled;
+    int32_t n_rev;
+    int32_t alternate;        // 1: exchanges alternate forward (even step) / reverse (odd step)
     int32_t pad;
 };
 
@@ -73,7 +85,9 @@ struct CollideCfg {
     int block;
     int spt;
     int variant;  // 0 = gathers into registers, 1 = gathers staged by cp.async (spt 1 or 2),
-                  // 2 = as 1, and the AA even step moves whole rows with TMA bulk copies
+                  // 2 = as 1, and the AA even step moves whole rows with TMA bulk copies,
+                  // 3 = as 0 with L2 prefetch hints, 4 = as 1 with the AA odd step's
+                  // stores staged in shared memory (spt 1)
 };
 
 // parity (AA only): 0 = every domain runs an even step, 1 = odd, 2 = per-domain
@@ -86,6 +100,10 @@ cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, const int2 *chunks,
                                 double2 *partials, unsigned *counters, int off, cudaStream_t st);
 cudaError_t launch_advance_list(int64_t *steps_base, const int32_t *idx, int n, int64_t by,
                                 cudaStream_t st);
+// Body force on the listed boundary slots ((domain, slot) pairs), right after the
+// stream-collide launch of step offset `off` and before the iolet update.
+cudaError_t launch_guo_force(int storage, int scheme, const DomDev *doms, const int2 *fslots, int n,
+                             int off, cudaStream_t st);
 // Reconstruct F_t of one domain (device order) and write macroscopic fields
 // (drho, ux, uy, uz) to out[perm ? perm[s] : s].
 cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, int64_t n,

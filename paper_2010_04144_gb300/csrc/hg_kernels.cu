@@ -197,6 +197,7 @@ template <int S> __device__ __forceinline__ float4 collide_s(float g[19], float 
     else return collide(g, omega);
 }
 
+
 template <typename T> __device__ __forceinline__ T ldg_nc(const T *p) { return __ldg(p); }
 template <> __device__ __forceinline__ __half ldg_nc(const __half *p) {
     return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p)));
@@ -507,6 +508,70 @@ __device__ __forceinline__ void tile_aa_odd_async(const DomDev &D, const TileDev
     }
 }
 
+// ==== staged-scatter AA odd step (V = 4, one site per thread) ===============
+// The odd step stores the value of direction I at x + c_I.  Most of those
+// targets lie in the same tile: their values are parked in the gather stage
+// (free once every thread has read its gathers) at the target's position and
+// then written row by row with coalesced stores.  A target outside the tile
+// gets its value directly; a non-fluid target parks the raw value at the own
+// site's slot OPP(I).  Position p's row-I value comes from the pull source of
+// direction I at p (its own neighbour-table entry I), or from p itself when
+// that entry is virtual; entry I is also the target entry of p's own
+// direction OPP(I), so the scatter pass records in one bit per row whether the
+// tile holds position p's value.  Each location is read and written by one
+// site only (the AA property), so the deferred stores race with no other tile.
+template <int S>
+__device__ __forceinline__ void tile_aa_odd_staged(const DomDev &D, const TileDev &tl, uint32_t *stage) {
+    using T = typename St<S>::T;
+    T *buf = (T *)D.f[0];
+    const uint32_t B = blockDim.x;
+    const int r = threadIdx.x;
+    const bool live = r < tl.count;
+    const int64_t s = tl.start + r;
+    const int64_t np = D.np;
+    const uint32_t sel = live ? issue_gathers<S, true>(D, buf, s, smem_addr(stage + r), 4 * B) : 0u;
+    cp_async_wait_all();
+    float g[19];
+    int slot = -1;
+    float4 m = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+        read_staged<S>(stage + r, B, sel, g);
+        slot = iolet_fixup<S>(D, s, g);
+        m = collide_s<S>(g, D.omega);
+    }
+    __syncthreads();  // every gather has been read: the stage now takes outputs
+    uint32_t held = 0;  // bit J: the tile holds this position's row-J value
+    if (live) {
+        const int32_t *nb2 = opaque(D.nbr);
+        T *wb = opaque(buf);
+        wb[s] = St<S>::template st<0>(g[0]);
+        unroll<1, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            const int32_t tg = __ldg(nb2 + (int64_t)(OPP(I) - 1) * np + s);  // site at x + c_I
+            const int64_t rel = (int64_t)tg - tl.start;
+            if ((uint64_t)rel < (uint64_t)tl.count) {
+                stage[I * B + (uint32_t)rel] = __float_as_uint(g[I]);
+                held |= 1u << OPP(I);
+            } else if (tg < 0 || tg >= np) {
+                stage[OPP(I) * B + r] = __float_as_uint(g[I]);
+                held |= 1u << OPP(I);
+            } else {
+                wb[(int64_t)I * np + tg] = St<S>::template st<I>(g[I]);
+            }
+        });
+        if (slot >= 0) D.bnd[slot] = m;
+    }
+    __syncthreads();
+    if (live) {
+        T *wb = opaque(buf);
+        unroll<1, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            if ((held >> I) & 1u)
+                wb[(int64_t)I * np + s] = St<S>::template st<I>(__uint_as_float(stage[I * B + r]));
+        });
+    }
+}
+
 // AA even step on pairs of adjacent sites (2 per thread): vector loads/stores.
 template <int S> struct Pair;
 template <> struct Pair<kF32> {
@@ -682,14 +747,19 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
     }
     __syncthreads();
     const int64_t t = t_now;
-    if constexpr (V == 1 || V == 2) {
+    if constexpr (V == 1 || V == 2 || V == 4) {
         if constexpr (SCHEME == kAB) {
             tile_ab_async<S, SPT>(D, tl, t, stage);
         } else {
             const bool odd = PAR == 2 ? (t & 1) != 0 : PAR == 1;
-            if (odd) tile_aa_odd_async<S, SPT>(D, tl, stage);
-            else if constexpr (V == 2) tile_aa_even_tma<S>(D, tl, (uint32_t)(SPT * blockDim.x), (unsigned char *)stage);
-            else tile_aa_even_pairs<S>(D, tl);
+            if (odd) {
+                if constexpr (V == 4) tile_aa_odd_staged<S>(D, tl, stage);
+                else tile_aa_odd_async<S, SPT>(D, tl, stage);
+            } else if constexpr (V == 2) {
+                tile_aa_even_tma<S>(D, tl, (uint32_t)(SPT * blockDim.x), (unsigned char *)stage);
+            } else {
+                tile_aa_even_pairs<S>(D, tl);
+            }
         }
     } else {
     constexpr bool HINT = V == 3;
@@ -801,20 +871,30 @@ __global__ void __launch_bounds__(kIoChunk) k_iolet_update(const IoDev *__restri
     __threadfence();
     for (int k = threadIdx.x; k < n_ios; k += blockDim.x) {
         const IoDev &J = ios[k];
-        double val;
+        // the exchange after step e is forward unless exchanges alternate and e is odd
+        const int64_t e = *J.step + off + 1;
+        const bool forward = !J.alternate || (e & 1) == 0;
         if (J.coupled) {
-            val = J.factor * __ldcg(J.src_M);
+            if (forward) *J.bcv = (float)(J.factor * __ldcg(J.src_M));
         } else {
             // phase of the next step in [0, 1): exact remainder first, so the FP64
             // cosine only ever sees an argument in [0, 2 pi)
-            const double tn = (double)(*J.step + off + 2);
+            const double tn = (double)(e + 1);
             const double ph = J.pulse ? fmod(tn, J.period) / J.period : 0.0;
             double p = 1.0;
             if (J.pulse == 1) p = 0.5 * (1.0 - cos(2.0 * 3.141592653589793 * ph));
             else if (J.pulse == 2) p = sin(2.0 * 3.141592653589793 * ph);
-            val = J.value * p;
+            *J.bcv = (float)(J.value * p);
         }
-        *J.bcv = (float)val;
+        if (!forward && J.n_rev > 0) {
+            // reverse: mean over the fed inlets of inflow speed / factor; the outlet's force
+            // density is the dynamic pressure of that speed, against the outward axis
+            double v = 0.0;
+            for (int r = 0; r < J.n_rev; ++r) v += -__ldcg(J.rev[r].M) / J.rev[r].factor;
+            v /= (double)J.n_rev;
+            const double q = -0.5 * v * fabs(v);
+            *J.force = make_float4((float)(q * J.nx), (float)(q * J.ny), (float)(q * J.nz), 0.0f);
+        }
     }
     if (threadIdx.x == 0) counters[n_ios] = 0u;
 }
@@ -822,6 +902,102 @@ __global__ void __launch_bounds__(kIoChunk) k_iolet_update(const IoDev *__restri
 __global__ void k_advance_list(int64_t *base, const int32_t *idx, int n, int64_t by) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) base[idx[i]] += by;
+}
+
+// ---- body force next to forced iolets (reverse coupling direction) ----
+// Guo, Zheng and Shi forcing: with force density F the velocity is
+// u_F = (j + F/2)/rho, the equilibrium is taken at u_F and the collision adds
+// (1 - omega/2) S_i, S_i = w_i [3 (c_i - u_F) + 9 (c_i.u_F) c_i] . F.  The
+// forced result differs from the unforced one, which the stream-collide kernel
+// has just stored, by omega (feq(u_F) - feq(u)) + (1 - omega/2) S_i(u_F): a
+// function of (drho, u, F) alone.  This pass runs right after stream-collide,
+// one thread per boundary slot listed as forced, adds that difference to the
+// 19 stored values where the step left them (scaled storage drops the w_i) and
+// rewrites the slot's moments with u_F, before the iolet reductions read them.
+// Keeping it out of stream-collide leaves that kernel's registers untouched.
+// A site takes the summed force of the distinct iolets it touches.
+template <bool SC>
+__device__ __forceinline__ void guo_delta(float4 m, float fx, float fy, float fz, float omega, float d[19],
+                                          float4 &mf) {
+    const float rho = HG_ADD(1.0f, m.x);
+    const float h = HG_MUL(0.5f, __frcp_rn(rho));
+    const float vx = HG_FMA(h, fx, m.y), vy = HG_FMA(h, fy, m.z), vz = HG_FMA(h, fz, m.w);
+    const float usq = HG_FMA(m.y, m.y, HG_FMA(m.z, m.z, HG_MUL(m.w, m.w)));
+    const float vsq = HG_FMA(vx, vx, HG_FMA(vy, vy, HG_MUL(vz, vz)));
+    const float vf = HG_FMA(vx, fx, HG_FMA(vy, fy, HG_MUL(vz, fz)));
+    const float a = HG_MUL(omega, rho);
+    const float b = HG_FMA(-0.5f, omega, 1.0f);
+    // isotropic part shared by every direction: a (-1.5 (u_F^2 - u^2)) + b (-3 u_F.F)
+    const float iso = HG_FMA(a, HG_MUL(-1.5f, HG_SUB(vsq, usq)), HG_MUL(b, HG_MUL(-3.0f, vf)));
+    d[0] = HG_MUL(SC ? 1.0f : W(0), iso);
+    auto pair = [&](int A, int B, float w, float cu, float cv, float cf) {
+        const float sym = HG_FMA(a, HG_MUL(4.5f, HG_SUB(HG_MUL(cv, cv), HG_MUL(cu, cu))),
+                                 HG_FMA(b, HG_MUL(9.0f, HG_MUL(cv, cf)), iso));
+        const float asym = HG_MUL(3.0f, HG_FMA(a, HG_SUB(cv, cu), HG_MUL(b, cf)));
+        d[A] = HG_MUL(w, HG_ADD(sym, asym));
+        d[B] = HG_MUL(w, HG_SUB(sym, asym));
+    };
+    const float w1 = SC ? 1.0f : W(1), w2 = SC ? 1.0f : W(7);
+    pair(1, 2, w1, m.y, vx, fx);
+    pair(3, 4, w1, m.z, vy, fy);
+    pair(5, 6, w1, m.w, vz, fz);
+    pair(7, 8, w2, HG_ADD(m.y, m.z), HG_ADD(vx, vy), HG_ADD(fx, fy));
+    pair(9, 10, w2, HG_SUB(m.y, m.z), HG_SUB(vx, vy), HG_SUB(fx, fy));
+    pair(11, 12, w2, HG_ADD(m.y, m.w), HG_ADD(vx, vz), HG_ADD(fx, fz));
+    pair(13, 14, w2, HG_SUB(m.y, m.w), HG_SUB(vx, vz), HG_SUB(fx, fz));
+    pair(15, 16, w2, HG_ADD(m.z, m.w), HG_ADD(vy, vz), HG_ADD(fy, fz));
+    pair(17, 18, w2, HG_SUB(m.z, m.w), HG_SUB(vy, vz), HG_SUB(fy, fz));
+    mf = make_float4(m.x, vx, vy, vz);
+}
+
+template <int S, int SCHEME>
+__global__ void __launch_bounds__(128) k_guo_force(const DomDev *__restrict__ doms,
+                                                   const int2 *__restrict__ fslots, int n, int off) {
+    using T = typename St<S>::T;
+    const int q = blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n) return;
+    const int2 e = fslots[q];
+    const DomDev &D = doms[e.x];
+    const int slot = e.y;
+    const int32_t *codes = D.io_codes + (int64_t)slot * 18;
+    float fx = 0.0f, fy = 0.0f, fz = 0.0f;
+    for (int i = 0; i < 18; ++i) {
+        const int32_t c = codes[i];
+        if (c >= -1) continue;
+        bool first = true;
+        for (int j = 0; j < i; ++j) first = first && (codes[j] != c);
+        if (!first) continue;
+        const float4 f = D.io_force[-c - 2];
+        fx = HG_ADD(fx, f.x);
+        fy = HG_ADD(fy, f.y);
+        fz = HG_ADD(fz, f.z);
+    }
+    if (fx == 0.0f && fy == 0.0f && fz == 0.0f) return;
+    float d[19];
+    float4 mf;
+    guo_delta<St<S>::kScaled>(D.bnd[slot], fx, fy, fz, D.omega, d, mf);
+    const int64_t s = D.slot_site[slot];
+    const int64_t np = D.np;
+    const int64_t t = *D.step + off + 1;  // the step stream-collide just ran
+    T *base;
+    if constexpr (SCHEME == kAB) base = (T *)D.f[t & 1];
+    else base = (T *)D.f[0];
+    unroll<0, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        int64_t at;
+        if constexpr (SCHEME == kAB) {
+            at = (int64_t)I * np + s;                            // own slot I
+        } else if (I == 0) {
+            at = s;
+        } else if ((t & 1) == 0) {
+            at = (int64_t)OPP(I) * np + s;                       // even: swapped, own site
+        } else {
+            at = (int64_t)I * np + D.nbr[(int64_t)(OPP(I) - 1) * np + s];  // odd: at x + c_I
+        }
+        const float v = St<S>::template ld<I>(base[at]);
+        base[at] = St<S>::template st<I>(HG_ADD(v, d[I]));
+    });
+    D.bnd[slot] = mf;
 }
 
 // ---- read-back: F_t of site s, direction I (raw storage value) ----
@@ -939,8 +1115,9 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_final(const double *parti
 template <int S, int SCHEME, int PAR, int V, int SPT>
 cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                           int64_t n_tiles, int off, cudaStream_t st) {
-    // V1: cp.async stage of 4-byte words; V2 also holds the even step's 19 rows + mbarrier
-    size_t smem = (V == 1 || V == 2) ? (size_t)SPT * 19 * cfg.block * 4 : 0;
+    // V1/V4: cp.async stage of 4-byte words (V4 reuses it for the odd step's outputs);
+    // V2 also holds the even step's 19 rows + mbarrier
+    size_t smem = (V == 1 || V == 2 || V == 4) ? (size_t)SPT * 19 * cfg.block * 4 : 0;
     if (V == 2) smem += 16;
     auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
     if (smem > 48 * 1024) {
@@ -968,6 +1145,11 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
             case 4: return launch_sc_one<S, SCHEME, PAR, 3, 4>(cfg, doms, tiles, n_tiles, off, st);
             default: return cudaErrorInvalidValue;
         }
+    }
+    if (cfg.variant == 4) {
+        if constexpr (SCHEME == kAB) return cudaErrorInvalidValue;
+        else if (cfg.spt != 1) return cudaErrorInvalidValue;
+        else return launch_sc_one<S, SCHEME, PAR, 4, 1>(cfg, doms, tiles, n_tiles, off, st);
     }
     if (cfg.variant == 2) {
         if (SCHEME == kAB) return cudaErrorInvalidValue;
@@ -1037,6 +1219,14 @@ cudaError_t launch_advance_list(int64_t *steps_base, const int32_t *idx, int n, 
             else { constexpr int S_ = kBF16, C_ = kAA; CALL; }                 \
         }                                                                      \
     } while (0)
+
+cudaError_t launch_guo_force(int storage, int scheme, const DomDev *doms, const int2 *fslots, int n,
+                             int off, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    HG_DISPATCH_SS(storage, scheme, (k_guo_force<S_, C_><<<grid, 128, 0, st>>>(doms, fslots, n, off)));
+    return cudaGetLastError();
+}
 
 cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, int64_t n,
                                const int64_t *canon_of, float4 *out, cudaStream_t st) {

@@ -21,6 +21,7 @@ LIB_PATH = os.path.join(_HERE, "libhemegb.so")
 HG_OK, HG_ERR_ARG, HG_ERR_OOM, HG_ERR_CUDA, HG_ERR_TIMEOUT, HG_ERR_STATE = 0, -1, -2, -3, -4, -5
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 SCHEME = {"ab": 0, "aa": 1}
+COUPLE = {"forward": 0, "alternate": 1}
 STORE_DTYPE = {0: np.float32, 1: np.float16, 2: None}  # bf16 is returned as uint16 bits
 
 
@@ -71,6 +72,7 @@ _SIGS = {
     "hg_domain_sites": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_domain_neighbours": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_couple": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
+    "hg_set_coupling_mode": ([C.c_void_p, C.c_int32], C.c_int),
     "hg_coupling_factors": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hg_step": ([C.c_void_p, C.c_int64], C.c_int),
@@ -80,6 +82,7 @@ _SIGS = {
     "hg_read_macroscopic_device": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_read_iolet_stats": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_read_boundary_values": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_read_iolet_forces": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_mass": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_state_bytes": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_save_state": ([C.c_void_p, C.c_void_p, C.c_int64], C.c_int),
@@ -213,6 +216,11 @@ class Context:
             arr[j].src_iolet, arr[j].dst_iolet, arr[j].factor = int(sk), int(dk), float(f)
         self._ck(lib().hg_couple(self.h, src.h, dst.h, arr, len(pairs)))
 
+    def set_coupling_mode(self, mode):
+        """"forward" (every step) or "alternate" (forward / reverse exchanges, Section 3)."""
+        m = COUPLE[mode] if isinstance(mode, str) else int(mode)
+        self._ck(lib().hg_set_coupling_mode(self.h, m))
+
     def set_launch(self, block_size, sites_per_thread, kernel_variant=0):
         self._ck(lib().hg_ctx_set_launch(self.h, int(block_size), int(sites_per_thread),
                                          int(kernel_variant)))
@@ -309,6 +317,12 @@ class Domain:
     def boundary_values(self):
         out = np.zeros(max(1, self.n_iolets), np.float32)
         self.ctx._ck(lib().hg_read_boundary_values(self.h, _p(out)))
+        return out[: self.n_iolets]
+
+    def iolet_forces(self):
+        """Body-force density per iolet for the next step, (n_iolets, 3) float32."""
+        out = np.zeros((max(1, self.n_iolets), 3), np.float32)
+        self.ctx._ck(lib().hg_read_iolet_forces(self.h, _p(out)))
         return out[: self.n_iolets]
 
     def mass(self):

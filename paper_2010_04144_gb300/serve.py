@@ -6,10 +6,14 @@ request's distributions resident in HBM and advances all of them together:
 each tick is one hg_step_domains call, i.e. one stream-collide launch per step
 whose tile table spans every active domain (plus one iolet-update launch),
 captured as a CUDA graph per active set.  Requests that arrive while others
-run are admitted, first come first served, as soon as their HBM footprint
-fits the budget; their host-side build (site order, neighbour table, upload)
-runs while the GPU executes the current tick.  Finished requests are read
-back and retired, freeing their memory for the queue.
+run are admitted, first come first served, as soon as their estimated HBM
+footprint fits the budget (policy "fifo"); policy "backfill" also lets a
+later request start early when it cannot delay the blocked head (EASY
+backfilling on memory, counted in ticks).  Their host-side build (site order, neighbour
+table, upload) runs on a worker thread while the GPU keeps executing ticks;
+a built request joins the active set at the next tick boundary, so builds
+never stall the GPU.  Finished requests are read back and retired, freeing
+their memory for the queue.
 
 Time-to-result of a request = completion time - arrival time.  Each domain's
 arithmetic does not depend on which other domains share its launches, so a
@@ -19,6 +23,7 @@ from __future__ import annotations
 
 import math
 import time
+from concurrent.futures import FIRST_COMPLETED, ThreadPoolExecutor, wait
 from dataclasses import dataclass, field
 
 import numpy as np
@@ -51,6 +56,7 @@ class Job:
     # filled by the server
     domains: list = field(default_factory=list)
     admitted_s: float = math.nan
+    start_tick: int = -1                # tick count when the request joined the active set
     finished_s: float = math.nan
     done_steps: int = 0
     bytes: int = 0
@@ -70,7 +76,8 @@ class Server:
     """FIFO continuous-batching server on one GPU."""
 
     def __init__(self, device=0, storage="f16", scheme="aa", budget_bytes=180e9, chunk_steps=100,
-                 block_size=0, sites_per_thread=0, kernel_variant=None, graph_steps=0):
+                 block_size=0, sites_per_thread=0, kernel_variant=None, graph_steps=0,
+                 build_workers=1, policy="fifo"):
         st = H.STORAGE[storage] if isinstance(storage, str) else storage
         sc = H.SCHEME[scheme] if isinstance(scheme, str) else scheme
         if kernel_variant is None:
@@ -84,6 +91,7 @@ class Server:
         self.budget = float(budget_bytes)
         self.chunk = int(chunk_steps)
         self.queue: list[Job] = []
+        self.building: list[tuple[Job, object]] = []   # (job, future) in admission order
         self.active: list[Job] = []
         self.finished: list[Job] = []
         self.in_use = 0
@@ -91,6 +99,16 @@ class Server:
         self.admit_order: list[int] = []
         self.site_steps = 0
         self.ticks = 0
+        if policy not in ("fifo", "backfill"):
+            raise ValueError("policy must be 'fifo' or 'backfill'")
+        self.policy = policy
+        self.backfilled = 0
+        self.build_s = 0.0        # host time spent building domains (worker or inline)
+        self.wait_s = 0.0         # main-thread time blocked on the GPU
+        self.idle_s = 0.0         # main-thread time with nothing to step
+        # one worker: builds complete in admission order, and the hg_domain_create
+        # calls never overlap one another (each already uses every host core)
+        self._pool = ThreadPoolExecutor(max_workers=1) if build_workers else None
 
     # ---- admission -------------------------------------------------------------
     def submit(self, job: Job):
@@ -107,6 +125,10 @@ class Server:
                 j.cancelled = True
                 self.queue.remove(j)
                 return True
+        for j, _ in self.building:
+            if j.rid == rid:
+                j.cancelled = True    # released when its build completes
+                return True
         for j in list(self.active):
             if j.rid == rid:
                 j.cancelled = True
@@ -117,32 +139,110 @@ class Server:
     def _estimate(self, job):
         return sum(footprint_bytes(g.n, self.storage, self.scheme, len(g.iolets)) for g in job.geoms)
 
+    def _build(self, job):
+        """Host build and upload of a job's domains (worker thread; touches no server state)."""
+        t = time.perf_counter()
+        doms = []
+        try:
+            for g in job.geoms:
+                doms.append(self.ctx.domain(g.xyz, g.iolets, tau=job.tau))
+        except Exception as e:  # noqa: BLE001 -- handed to the main thread
+            return doms, e, time.perf_counter() - t
+        return doms, None, time.perf_counter() - t
+
     def _admit(self, now_s):
-        admitted = []
+        """Reserve memory for arrived queue heads and start their builds; with the backfill
+        policy, then let later arrivals that cannot delay the head go ahead of it."""
         while self.queue and self.queue[0].arrival_s <= now_s:
             job = self.queue[0]
             if self.in_use + self._estimate(job) > self.budget:
-                break  # FIFO: the head waits for memory; nobody overtakes it
+                break  # the head waits for memory
             self.queue.pop(0)
-            doms = []
-            try:
-                for g in job.geoms:
-                    doms.append(self.ctx.domain(g.xyz, g.iolets, tau=job.tau))
-                if job.pairs:
+            self._start(job, now_s)
+        if self.policy == "backfill" and self.queue and self.queue[0].arrival_s <= now_s:
+            self._backfill(now_s)
+
+    def _ticks_left(self, job):
+        left = job.steps - job.done_steps
+        return -(-left // self.chunk)
+
+    def _backfill(self, now_s):
+        """EASY backfilling on memory, counted in ticks: the blocked head's start (its shadow
+        tick) is when enough resident requests have retired; a later request may start now if it
+        fits and either finishes by the shadow tick or fits in the memory the head leaves spare."""
+        head = self.queue[0]
+        free = self.budget - self.in_use
+        need = self._estimate(head)
+        holders = [(self._ticks_left(j), j.bytes) for j in self.active]
+        holders += [(self._ticks_left(j) + 1, j.bytes) for j, _ in self.building]  # +1: the build
+        holders.sort()
+        shadow, extra, freed = None, 0.0, 0.0
+        for ticks, b in holders:
+            freed += b
+            if free + freed >= need:
+                shadow, extra = ticks, free + freed - need
+                break
+        if shadow is None:
+            return
+        for job in list(self.queue[1:]):
+            if job.arrival_s > now_s:
+                break
+            m = self._estimate(job)
+            if self.in_use + m > self.budget:
+                continue
+            done_by_shadow = self._ticks_left(job) + 1 <= shadow
+            if not done_by_shadow and m > extra:
+                continue
+            if not done_by_shadow:
+                extra -= m
+            self.queue.remove(job)
+            self.backfilled += 1
+            self._start(job, now_s)
+
+    def _start(self, job, now_s):
+        """Reserve the request's estimated memory and start its build."""
+        job.bytes = self._estimate(job)
+        self.in_use += job.bytes
+        self.peak_in_use = max(self.peak_in_use, self.in_use)
+        job.admitted_s = now_s
+        self.admit_order.append(job.rid)
+        if self._pool is not None:
+            self.building.append((job, self._pool.submit(self._build, job)))
+        else:
+            self.building.append((job, _Done(self._build(job))))
+
+    def _activate(self, block=False, timeout=None):
+        """Move completed builds (in admission order) into the active set; the GPU is idle."""
+        if block and self.building and not self.building[0][1].done():
+            t = time.perf_counter()
+            wait([self.building[0][1]], timeout=timeout, return_when=FIRST_COMPLETED)
+            self.idle_s += time.perf_counter() - t
+        joined = []
+        while self.building and self.building[0][1].done():
+            job, fut = self.building.pop(0)
+            doms, err, secs = fut.result()
+            self.build_s += secs
+            if err is None and job.pairs and not job.cancelled:
+                try:
                     self.ctx.couple(doms[0], doms[1], job.pairs)
-            except H.HgError:
+                except H.HgError as e:
+                    err = e
+            if err is not None or job.cancelled:
                 for d in doms:
                     d.destroy()
-                raise
+                self.in_use -= job.bytes
+                if err is not None:
+                    raise err
+                continue
+            self.in_use -= job.bytes
             job.domains = doms
             job.bytes = sum(d.info()["device_bytes"] for d in doms)
             self.in_use += job.bytes
             self.peak_in_use = max(self.peak_in_use, self.in_use)
-            job.admitted_s = now_s
+            job.start_tick = self.ticks
             self.active.append(job)
-            self.admit_order.append(job.rid)
-            admitted.append(job)
-        return admitted
+            joined.append(job)
+        return joined
 
     def _retire(self, job, read=True, now_s=None):
         if read:
@@ -167,28 +267,33 @@ class Server:
         """Serve every submitted job; returns the finished jobs."""
         t0 = clock()
         self.queue.sort(key=lambda j: (j.arrival_s, j.rid))
-        while self.queue or self.active:
-            now = clock() - t0
-            stepping = []
+        while self.queue or self.active or self.building:
+            self._activate()
+            self._admit(clock() - t0)
             if self.active:
                 stepping = [d for j in self.active for d in j.domains]
-                k = min(self.chunk, min(j.steps - j.done_steps for j in self.active))
-                self.ctx.step_domains(stepping, k)  # asynchronous: host work below overlaps it
-            newly = self._admit(now)
-            if stepping:
+                ticking = list(self.active)
+                k = min(self.chunk, min(j.steps - j.done_steps for j in ticking))
+                self.ctx.step_domains(stepping, k)  # asynchronous: builds run meanwhile
+                t = time.perf_counter()
                 self.ctx.sync()
+                self.wait_s += time.perf_counter() - t
                 self.ticks += 1
                 self.site_steps += sum(d.n for d in stepping) * k
-                for j in list(self.active):
-                    if j in newly:
+                for j in ticking:
+                    if j.cancelled:
                         continue
                     j.done_steps += k
                     if j.done_steps >= j.steps:
                         self._retire(j, read=True, now_s=clock() - t0)
-            elif not newly and self.queue:
-                wait = self.queue[0].arrival_s - (clock() - t0)
-                if wait > 0:
-                    sleep(min(wait, 0.05))
+            elif self.building:
+                # nothing to step: wait for the oldest build, or for the next arrival if sooner
+                gap = self.queue[0].arrival_s - (clock() - t0) if self.queue else 0.0
+                self._activate(block=True, timeout=gap if gap > 0 else None)
+            elif self.queue:
+                gap = self.queue[0].arrival_s - (clock() - t0)
+                if gap > 0:
+                    sleep(min(gap, 0.05))
             if max_ticks is not None and self.ticks >= max_ticks:
                 break
         self.elapsed_s = clock() - t0
@@ -199,14 +304,31 @@ class Server:
         out = {"requests": len(self.finished), "ticks": self.ticks,
                "elapsed_s": getattr(self, "elapsed_s", float("nan")),
                "aggregate_mflups": self.site_steps / max(getattr(self, "elapsed_s", 1e-9), 1e-9) / 1e6,
-               "peak_hbm_gb": self.peak_in_use / 1e9}
+               "peak_hbm_gb": self.peak_in_use / 1e9, "build_s": self.build_s,
+               "policy": self.policy, "backfilled": self.backfilled,
+               "gpu_wait_s": self.wait_s, "idle_s": self.idle_s}
         if ttr.size:
             out.update(p50_s=float(np.percentile(ttr, 50)), p99_s=float(np.percentile(ttr, 99)),
                        mean_s=float(ttr.mean()), max_s=float(ttr.max()))
         return out
 
     def close(self):
+        if self._pool is not None:
+            self._pool.shutdown(wait=True)   # no build may overlap the context's destruction
         self.ctx.close()
+
+
+class _Done:
+    """A completed build in the shape of a future (builds run inline without a worker)."""
+
+    def __init__(self, value):
+        self.value = value
+
+    def done(self):
+        return True
+
+    def result(self):
+        return self.value
 
 
 def coupled_job_from_trees(rid, arrival_s, steps, art, ven, uniforms, tau=0.8):

@@ -366,7 +366,9 @@ def tree(spec: TreeSpec = TreeSpec(), venous: bool = False, radius_factor: float
     origin = tuple(int(v) for v in (-shift + np.array([venous_offset, 0.0, 0.0])))
     meta = dict(kind="tree", depth=spec.depth, root_radius=spec.root_radius, seed=spec.seed,
                 scale=spec.scale, venous=venous, n_segments=nseg, leaves=leaves,
-                radii=[float(x) for x in r])
+                radii=[float(x) for x in r], shift=[float(x) for x in shift],
+                segments=[(tuple(float(x) for x in Pq[n]), tuple(float(x) for x in Qq[n]))
+                          for n in range(nseg)])
     return Geometry(xyz=xyz, iolets=io, origin=origin, meta=meta)
 
 

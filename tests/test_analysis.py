@@ -1,0 +1,62 @@
+"""Analysis helpers (Section 3.3), CPU only.
+
+  * unit relations against the worked numbers of Section 3.3
+    (tests/golden/units_section33.txt) and their round trip;
+  * velocity against vessel area: on a single steady tube fed by a parabolic
+    inlet of peak U, mass conservation fixes the cross-section mean speed at
+    the inlet profile's mean over the inlet's lattice points (U/2 in the
+    continuum; 0.4805 U on the 81 points of a radius-5 disc); the moving-wall
+    rule evaluates the profile at link mid-points, which loses ~2 % at the rim,
+    so the bar is 4 % (the oracle supplies the flow field).
+"""
+import os
+
+import numpy as np
+import pytest
+
+from paper_2010_04144_gb300 import analysis as A
+from paper_2010_04144_gb300 import synth as S
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden", "units_section33.txt")
+
+
+def _cases():
+    for line in open(GOLD):
+        if line.strip() and not line.startswith("#"):
+            name, dx, dt, v, ma, bound = line.split()
+            yield name, float(dx), float(dt), float(v), float(ma), float(bound)
+
+
+@pytest.mark.parametrize("case", list(_cases()), ids=lambda c: c[0])
+def test_mach_numbers_of_section_3_3(case):
+    _, dx, dt, v, ma, bound = case
+    _, got = A.lattice_parameters(dx, dt, 4e-6, v)
+    assert abs(got - ma) < 1e-9 and got < bound
+
+
+def test_unit_round_trip():
+    for dx, nu, tau in [(25e-6, 4e-6, 0.52), (75e-6, 3.5e-6, 0.8), (1e-3, 1e-6, 1.0)]:
+        dt = A.physical_step(dx, nu, tau)
+        t2, _ = A.lattice_parameters(dx, dt, nu, 1.0)
+        assert abs(t2 - tau) < 1e-12
+        assert abs(A.lattice_speed(dx / dt, dx, dt) - 1.0) < 1e-15
+    with pytest.raises(ValueError):
+        A.physical_step(1e-4, 1e-6, 0.5)
+
+
+def test_mean_speed_of_steady_tube_is_half_the_peak(oracle_mod):
+    U = 0.02
+    geo = S.tree(S.TreeSpec(depth=1, root_radius=5.0, seed=11), inlet_speed=U,
+                 pulse=S.PULSE_CONST)
+    d = oracle_mod.Domain(geo.xyz, geo.iolets, tau=0.8)
+    oracle_mod.System([d]).step(1500)
+    rows = A.velocity_vs_area(geo, d.moments(), d.xyz)
+    assert rows.shape[0] == 1
+    _, area, speed, n = rows[0]
+    x, y = np.meshgrid(np.arange(-5, 6), np.arange(-5, 6))
+    r2 = (x ** 2 + y ** 2)[x ** 2 + y ** 2 <= 25]
+    assert area == r2.size                                # the disc's lattice points
+    expect = U * np.mean(1.0 - r2 / 25.0)
+    assert abs(speed - expect) / expect < 0.04
+    neg = A.velocity_vs_area(geo, d.moments(), d.xyz, arterial_negative=True)
+    assert neg[0, 1] == -area

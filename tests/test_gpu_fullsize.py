@@ -76,7 +76,7 @@ def test_fullsize_sampled(gpu, oracle_mod, bench_case, storage, scheme):
         nio = len(geo.iolets)
         buf[16:24] = np.frombuffer(np.int64(t).tobytes(), np.uint8)
         buf[40:40 + 4 * nio] = np.frombuffer(bc.astype(np.float32).tobytes(), np.uint8)
-        buf[40 + 28 * nio:] = np.frombuffer(raw.tobytes(), np.uint8)
+        buf[40 + 28 * nio:40 + 28 * nio + raw.nbytes] = np.frombuffer(raw.tobytes(), np.uint8)
         d.load_state(buf)
         assert d.step == t
         assert np.array_equal(d.state_f64(), F_in)          # import into the scheme's layout

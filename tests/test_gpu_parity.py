@@ -257,7 +257,8 @@ def test_errors_are_reported(gpu):
 LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128, 2, 1),
             ("aa", 256, 1, 0), ("aa", 128, 4, 0), ("aa", 256, 1, 1), ("aa", 256, 2, 1),
             ("aa", 64, 2, 1), ("aa", 128, 2, 2), ("aa", 256, 1, 2), ("aa", 64, 2, 2),
-            ("ab", 256, 1, 3), ("ab", 128, 4, 3), ("aa", 256, 1, 3), ("aa", 128, 2, 3)]
+            ("ab", 256, 1, 3), ("ab", 128, 4, 3), ("aa", 256, 1, 3), ("aa", 128, 2, 3),
+            ("aa", 256, 1, 4), ("aa", 64, 1, 4), ("aa", 512, 1, 4)]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
@@ -288,6 +289,22 @@ def test_variant1_against_oracle(gpu, oracle_mod):
                                      checkpoints=(50, 101), sites_per_thread=2, kernel_variant=1)
         for eu, ep in errs:
             assert eu < TOL["f32"] and ep < TOL["f32"], (scheme, errs)
+
+
+def test_variant4_against_oracle_and_launch_rules(gpu, oracle_mod):
+    """The staged-scatter odd step against the oracle; its launch-shape rules."""
+    geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
+    errs, _, _, _, _ = _run_pair(gpu, oracle_mod, geo, 151, scheme="aa", checkpoints=(50, 101),
+                                 block_size=128, sites_per_thread=1, kernel_variant=4)
+    for eu, ep in errs:
+        assert eu < TOL["f32"] and ep < TOL["f32"], errs
+    for scheme, spt in (("ab", 1), ("aa", 2)):
+        ctx = gpu.Context(storage="f32", scheme=scheme)
+        try:
+            with pytest.raises(gpu.HgError):
+                ctx.set_launch(256, spt, 4)
+        finally:
+            ctx.close()
 
 
 def test_autotune_leaves_state_unchanged(gpu):

@@ -65,3 +65,51 @@ def test_alone_vs_mixed_bit_identical(gpu, storage, scheme):
         assert mix.in_use == 0
     finally:
         mix.close()
+
+
+def test_build_on_second_thread_while_stepping(gpu):
+    """hg_domain_create on one thread while another steps the same context."""
+    import threading
+
+    a = _tree(11, inlet_speed=0.04, period=300.0)
+    big = _tree(21, depth=5, r=6.0)
+    ctx = gpu.Context(storage="f32", scheme="aa")
+    try:
+        da = ctx.domain(a.xyz, a.iolets)
+        ctx.step(200)
+        ref = da.state()
+        ref_stats = da.iolet_stats()
+        db0 = ctx.domain(big.xyz, big.iolets)
+        nbr_ref, sites_ref = db0.neighbours(), db0.sites()
+    finally:
+        ctx.close()
+
+    ctx = gpu.Context(storage="f32", scheme="aa")
+    try:
+        da = ctx.domain(a.xyz, a.iolets)
+        out = {}
+
+        def build():
+            try:
+                out["d"] = ctx.domain(big.xyz, big.iolets)
+            except Exception as e:  # noqa: BLE001 -- reported below
+                out["e"] = e
+
+        th = threading.Thread(target=build)
+        th.start()
+        for _ in range(20):
+            ctx.step_domains([da], 10)
+            ctx.sync()
+        th.join()
+        assert "e" not in out, out.get("e")
+        db = out["d"]
+        assert np.array_equal(da.state(), ref)
+        assert np.array_equal(da.iolet_stats(), ref_stats)
+        assert db.step == 0 and not np.any(db.state())
+        assert np.array_equal(db.sites(), sites_ref)
+        assert np.array_equal(db.neighbours(), nbr_ref)
+        ctx.step_domains([da, db], 16)      # the new domain joins the context's launches
+        ctx.sync()
+        assert da.step == 216 and db.step == 16
+    finally:
+        ctx.close()

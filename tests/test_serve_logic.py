@@ -67,14 +67,20 @@ class _Clock:
         self.t += s
 
 
-@pytest.fixture
-def server(monkeypatch):
+@pytest.fixture(params=[0, 1], ids=["inline-build", "worker-build"])
+def server(monkeypatch, request):
     monkeypatch.setattr(SV.H, "Context", lambda **kw: _Ctx(**kw))
+    made = []
 
     def make(budget):
-        return SV.Server(storage="f16", scheme="aa", budget_bytes=budget, chunk_steps=50)
+        srv = SV.Server(storage="f16", scheme="aa", budget_bytes=budget, chunk_steps=50,
+                        build_workers=request.param)
+        made.append(srv)
+        return srv
 
-    return make
+    yield make
+    for srv in made:
+        srv.close()
 
 
 def _job(rid, t, n=1000, steps=200):
@@ -134,3 +140,127 @@ def test_cancel_queued_and_active(server):
     srv.run(clock=clk, sleep=clk.sleep)
     assert [j.rid for j in srv.finished] == [1]
     assert not srv.cancel(7)
+
+
+class _SlowCtx(_Ctx):
+    """Stub whose domain builds take real time (a large request's host build)."""
+
+    delay = 0.3
+
+    def domain(self, xyz, iolets, tau=0.8):
+        if len(xyz) >= 2000:
+            import time
+
+            time.sleep(self.delay)
+        if len(xyz) == 1234:
+            raise SV.H.HgError(-1, "build failed")
+        return super().domain(xyz, iolets, tau)
+
+    def sync(self):
+        import time
+
+        time.sleep(0.02)   # a tick's GPU time
+
+
+@pytest.fixture
+def slow_server(monkeypatch):
+    monkeypatch.setattr(SV.H, "Context", lambda **kw: _SlowCtx(**kw))
+    made = []
+
+    def make(budget, workers=1):
+        srv = SV.Server(storage="f16", scheme="aa", budget_bytes=budget, chunk_steps=50,
+                        build_workers=workers)
+        made.append(srv)
+        return srv
+
+    yield make
+    for srv in made:
+        srv.close()
+
+
+def test_worker_build_overlaps_ticks(slow_server):
+    srv = slow_server(budget=1e12)
+    srv.submit(_job(0, 0.0, steps=2000))             # 40 ticks of ~20 ms
+    srv.submit(_job(1, 0.0, n=2000, steps=100))       # slow build, admitted at once
+    clk = _Clock()
+    srv.run(clock=clk, sleep=clk.sleep)
+    steps = [c for c in srv.ctx.calls if c[0] == "step"]
+    # request 0 keeps ticking alone while request 1 builds; then both share launches
+    assert steps[0] == ("step", 1, 50)
+    assert any(c[1] == 2 for c in steps)
+    assert [j.done_steps for j in sorted(srv.finished, key=lambda j: j.rid)] == [2000, 100]
+    assert srv.in_use == 0 and srv.stats()["build_s"] >= _SlowCtx.delay
+
+
+def test_inline_build_blocks_first_tick(slow_server):
+    srv = slow_server(budget=1e12, workers=0)
+    srv.submit(_job(0, 0.0, steps=400))
+    srv.submit(_job(1, 0.0, n=2000, steps=100))
+    clk = _Clock()
+    srv.run(clock=clk, sleep=clk.sleep)
+    steps = [c for c in srv.ctx.calls if c[0] == "step"]
+    assert steps[0] == ("step", 2, 50)                # both built before the first tick
+
+
+def test_cancel_while_building_releases_memory(slow_server):
+    srv = slow_server(budget=1e12)
+    srv.submit(_job(0, 0.0, n=2000))
+    srv._admit(0.0)
+    assert srv.building and srv.in_use > 0
+    assert srv.cancel(0)
+    clk = _Clock()
+    srv.run(clock=clk, sleep=clk.sleep)
+    assert srv.finished == [] and srv.in_use == 0
+    assert all(not d.alive for d in srv.ctx.live)
+
+
+def test_build_error_propagates_and_releases(slow_server):
+    for workers in (0, 1):
+        srv = slow_server(budget=1e12, workers=workers)
+        srv.submit(_job(0, 0.0, n=1234))
+        clk = _Clock()
+        with pytest.raises(SV.H.HgError):
+            srv.run(clock=clk, sleep=clk.sleep)
+        assert srv.in_use == 0 and not srv.active
+
+
+def _run_policy(monkeypatch, policy, jobs, budget):
+    monkeypatch.setattr(SV.H, "Context", lambda **kw: _Ctx(**kw))
+    srv = SV.Server(storage="f16", scheme="aa", budget_bytes=budget, chunk_steps=50,
+                    build_workers=0, policy=policy)
+    for j in jobs:
+        srv.submit(j)
+    clk = _Clock()
+    srv.run(clock=clk, sleep=clk.sleep)
+    srv.close()
+    return srv
+
+
+def test_backfill_lets_short_requests_pass_without_delaying_the_head(monkeypatch):
+    one = SV.footprint_bytes(1000, 1, 1, 2)
+    big = SV.footprint_bytes(2500, 1, 1, 2)
+    budget = 1.2 * big                         # the big head cannot start while 0 runs
+
+    def jobs():
+        return [_job(0, 0.0, steps=1000), _job(1, 0.001, n=2500, steps=200),
+                _job(2, 0.002, steps=100), _job(3, 0.003, steps=5000)]
+
+    fifo = _run_policy(monkeypatch, "fifo", jobs(), budget)
+    bf = _run_policy(monkeypatch, "backfill", jobs(), budget)
+    assert fifo.admit_order == [0, 1, 2, 3] and fifo.backfilled == 0
+    # request 2 (short) passes the blocked head; request 3 (long) may not
+    assert bf.admit_order.index(2) < bf.admit_order.index(1) < bf.admit_order.index(3)
+    assert bf.backfilled >= 1
+    done_f = {j.rid: j for j in fifo.finished}
+    done_b = {j.rid: j for j in bf.finished}
+    assert all(j.done_steps == j.steps for j in bf.finished) and len(done_b) == 4
+    assert done_b[2].finished_s < done_f[2].finished_s
+    # the head starts no later (in ticks) than under FIFO
+    assert 0 <= done_b[1].start_tick <= done_f[1].start_tick
+    assert bf.peak_in_use <= budget
+
+
+def test_unknown_policy_rejected(monkeypatch):
+    monkeypatch.setattr(SV.H, "Context", lambda **kw: _Ctx(**kw))
+    with pytest.raises(ValueError):
+        SV.Server(policy="lifo")
