@@ -143,7 +143,7 @@ def kernel_source_sha():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("hg_kernels.cu", "hg_internal.h"):
+    for f in ("hg_device.cuh", "hg_sc_f32.cu", "hg_sc_f16.cu", "hg_sc_bf16.cu", "hg_internal.h"):
         with open(os.path.join(ROOT, "paper_2010_04144_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -192,8 +192,8 @@ def whole_job_mflups(sites_per_rank, world_size, steps, max_ms):
     return sites_per_rank * world_size * steps / (max_ms / 1e3) / 1e6
 
 
-def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler):
-    """Autotuned launch shape, device-timed steps (graphs), per-kernel times, e2e job."""
+def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, launch=None):
+    """Autotuned (or given) launch shape, device-timed steps (graphs), per-kernel times, e2e job."""
     import torch
 
     from paper_2010_04144_gb300.autotune import autotune
@@ -206,7 +206,11 @@ def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler):
         nvtx = torch.cuda.nvtx
         tag = f"{storage}:{scheme}"
         nvtx.range_push(f"{tag}-autotune")
-        best, timing = autotune(ctx)
+        if launch is None:
+            best, timing = autotune(ctx)
+        else:  # a fixed shape (profiling one kernel form), no tuning
+            ctx.set_launch(*launch)
+            best, timing = tuple(launch), {}
         nvtx.range_pop()
         # warm-up, then the timed region: exactly `steps` steps, barrier + sync on both sides
         ctx.step(warmup)
@@ -267,10 +271,22 @@ def cpu_baseline(geo, budget_s=20.0):
     s.step(k)
     dt = time.perf_counter() - t0
     steps = k
-    return {"value": od.n * steps / dt / 1e6, "unit": "MFLUPS", "cores": oracle.num_threads(),
-            "kind": "oracle",
+    cores = oracle.num_threads()
+    # one core: the same update on a seeded sample of 200k sites of the current state
+    sample = np.sort(np.random.default_rng(1).choice(od.n, size=min(od.n, 200_000), replace=False))
+    bc = s.bc_values(0, s.t + 1)
+    oracle.set_threads(1)
+    try:
+        t0 = time.perf_counter()
+        od.step_sites(od.F, bc, sample)
+        one_core = sample.size / (time.perf_counter() - t0) / 1e6
+    finally:
+        oracle.set_threads(cores)
+    return {"value": od.n * steps / dt / 1e6, "unit": "MFLUPS", "cores": cores,
+            "kind": "oracle", "single_core_mflups": one_core,
             "sample": f"{steps} steps over all {od.n} sites of the same tree (after 1 untimed step; "
-                      f"table build {build_s:.1f} s untimed)"}
+                      f"table build {build_s:.1f} s untimed); single core: one step of "
+                      f"{sample.size} seeded sites"}
 
 
 def run_reference(args):
@@ -403,6 +419,8 @@ def run_coupled(args, H, device):
         ctx.couple(da, dv, pairs)
         ctx.set_coupling_mode(args.coupled_mode)
         best, _ = autotune(ctx)
+        # let the inlet's wave reach every outlet (and the coupled inlets) before timing
+        ctx.step(args.coupled_settle)
         ctx.step(args.warmup)
         barrier(None)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -431,8 +449,8 @@ def run_coupled(args, H, device):
                 lvl = np.floor(np.log2(rows[:, 0] + 1)).astype(int)
                 vva[name] = [[int(L), float(np.median(rows[lvl == L, 1])), float(np.median(rows[lvl == L, 2])),
                               int((lvl == L).sum())] for L in np.unique(lvl)]
-        bc_dev = (max(abs(abs(float(bv[vk])) / abs(f * Ma[ak, 0]) - 1.0) for ak, vk, f in pairs if Ma[ak, 0])
-                  if args.coupled_mode == "forward" else None)  # alternate: may hold the previous value
+        devs = [abs(abs(float(bv[vk])) / abs(f * Ma[ak, 0]) - 1.0) for ak, vk, f in pairs if Ma[ak, 0]]
+        bc_dev = max(devs) if devs and args.coupled_mode == "forward" else None  # alternate: may hold
         ratio = [float(abs(Mv[vk, 0]) / abs(f * Ma[ak, 0])) for ak, vk, f in pairs if Ma[ak, 0]]
         fan = np.bincount([ak for ak, _, _ in pairs])
         line = {"metric": "MFLUPS, coupled arterial+venous pair in one launch sequence",
@@ -448,6 +466,7 @@ def run_coupled(args, H, device):
                            "fan_out_max": int(fan.max()), "fan_out_min": int(fan[1:].min()),
                            "factor_range": [min(p[2] for p in pairs), max(p[2] for p in pairs)],
                            "scheme": args.coupled_scheme, "exchange": args.coupled_mode,
+                           "settle_steps": args.coupled_settle,
                            "launch": {"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]}},
                 "roofline": {"bound": "hbm", "achieved": B * n / (per / 1e3) / 1e9, "peak": peak,
                              "unit": "GB/s", "frac": B * n / (per / 1e3) / 1e9 / peak,
@@ -456,7 +475,9 @@ def run_coupled(args, H, device):
                 "boundary_value_rel_dev_max": bc_dev,
                 "arterial_outlet_force_max": float(np.abs(forces).max()),
                 "velocity_vs_area_by_level": vva or None,
-                "venous_inlet_flow_over_imposed": [min(ratio), float(np.median(ratio)), max(ratio)]}
+                "venous_inlet_flow_over_imposed": ([min(ratio), float(np.median(ratio)), max(ratio)]
+                                                   if ratio else None),
+                "outlets_with_flow": len(ratio)}
         print(json.dumps(line))
     finally:
         ctx.close()
@@ -531,12 +552,15 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="hemegb", choices=["hemegb", "reference"])
     ap.add_argument("--scale", type=float, default=1.71)
-    ap.add_argument("--variants", default="f32:ab,f32:aa,f16:ab,f16:aa,bf16:aa")
+    ap.add_argument("--variants", default="f32:ab,f32:aa,f16:ab,f16:aa,bf16:aa",
+                    help="storage:scheme list; append @BLOCKxSPTvVARIANT to fix a launch shape")
     ap.add_argument("--headline", default="f32:best")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve"])
     ap.add_argument("--coupled-scale", type=float, default=2.12)
     ap.add_argument("--coupled-scheme", default="ab")
+    ap.add_argument("--coupled-settle", type=int, default=4000,
+                    help="untimed steps before the coupled timing, so flow reaches the outlets")
     ap.add_argument("--velocity-area", action="store_true",
                     help="coupled config: add mean speed vs vessel area per tree level (Section 3.3)")
     ap.add_argument("--coupled-mode", default="forward", choices=["forward", "alternate"],
@@ -581,12 +605,21 @@ def main():
     geo, cfg = workload(scale=args.scale)
     cfg["steps_per_job"] = args.steps
     peak, peak_kind = hbm_peak()
-    variants = [tuple(v.split(":")) for v in args.variants.split(",")]
+    variants = []
+    for v in args.variants.split(","):  # "storage:scheme", optionally "@BLOCKxSPTvVARIANT" (no tuning)
+        form, _, shape = v.partition("@")
+        launch = None
+        if shape:
+            b, rest = shape.split("x")
+            spt, var = rest.split("v")
+            launch = (int(b), int(spt), int(var))
+        variants.append((*form.split(":"), launch))
     results = {}
     sampler = ClockSampler(device).start()
     try:
-        for (storage, scheme) in variants:
-            r = time_variant(H, geo, storage, scheme, args.steps, args.warmup, dist, device, sampler)
+        for (storage, scheme, launch) in variants:
+            r = time_variant(H, geo, storage, scheme, args.steps, args.warmup, dist, device, sampler,
+                             launch=launch)
             B = BYTES_PER_UPDATE[(storage, scheme)]
             r["mflups"] = r["n"] * ws * args.steps / (r["ms"] / 1e3) / 1e6
             r["achieved_gbs"] = B * r["n"] / (r["ms_sc"] / args.steps / 1e3) / 1e9

@@ -76,6 +76,7 @@ def lib():
         L.or_mass.argtypes = [C.c_int64, P]
         L.or_mass.restype = C.c_double
         L.or_num_threads.restype = C.c_int
+        L.or_set_threads.argtypes = [C.c_int]
         _lib = L
     return _lib
 
@@ -296,3 +297,7 @@ class System:
 
 def num_threads():
     return int(lib().or_num_threads())
+
+
+def set_threads(n):
+    lib().or_set_threads(int(n))

@@ -447,3 +447,13 @@ int or_num_threads(void) {
     return 1;
 #endif
 }
+
+/* Thread count of the per-site loops (timing of one core vs all cores). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
+}

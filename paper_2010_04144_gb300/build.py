@@ -17,8 +17,8 @@ LIB = os.path.join(PKG, "libhemegb.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hg_kernels.cu", "hg_host.cpp", "hg_noalloc.cu"]
-HEADERS = ["hg_internal.h", os.path.join("..", "..", "include", "hemegb.h")]
+SOURCES = ["hg_sc_f32.cu", "hg_sc_f16.cu", "hg_sc_bf16.cu", "hg_kernels.cu", "hg_host.cpp", "hg_noalloc.cu"]
+HEADERS = ["hg_internal.h", "hg_device.cuh", os.path.join("..", "..", "include", "hemegb.h")]
 
 
 def _stale() -> bool:

@@ -1183,8 +1183,8 @@ int parity_mode(hg_ctx *ctx, const std::vector<int32_t> &doms) {
 }
 
 // Kernel parity argument for the step at offset `off` of a group starting in `mode`.
-inline int step_parity(hg_ctx *ctx, int mode, int64_t off) {
-    if (ctx->scheme == HG_SCHEME_AB || mode == 2) return 2;
+inline int step_parity(hg_ctx *, int mode, int64_t off) {
+    if (mode == 2) return 2;
     return (int)((mode + off + 1) & 1);  // 1 when the executed step is odd
 }
 

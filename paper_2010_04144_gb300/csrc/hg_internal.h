@@ -90,7 +90,7 @@ struct CollideCfg {
                   // stores staged in shared memory (spt 1)
 };
 
-// parity (AA only): 0 = every domain runs an even step, 1 = odd, 2 = per-domain
+// parity: 0 = every domain runs an even step, 1 = odd, 2 = per-domain
 // parity read from the step counters.
 cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                                   int64_t n_tiles, int off, int parity, cudaStream_t st);

@@ -1,0 +1,11 @@
+// hg_sc_f16.cu -- stream-collide instantiations for F16 storage (see hg_device.cuh).
+#include "hg_device.cuh"
+
+namespace hg {
+
+cudaError_t launch_sc_f16(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
+                          int off, int parity, cudaStream_t st) {
+    return launch_sc_storage<kF16>(cfg, doms, tiles, n_tiles, off, parity, st);
+}
+
+}  // namespace hg
