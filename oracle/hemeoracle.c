@@ -409,26 +409,43 @@ void or_moments(int64_t n, const double *F, double *out) {
  * mean drho, out[3k+2] = number of sites.  Means of an empty set are 0. */
 void or_iolet_means(int64_t n, const int32_t *nbr, const double *mom, const or_iolet *io,
                     int32_t nio, double *out) {
+    if (nio <= 0) return;
+    double *nh = (double *)calloc((size_t)nio * 3, sizeof(double));
+    double *su = (double *)calloc((size_t)nio, sizeof(double));
+    double *sr = (double *)calloc((size_t)nio, sizeof(double));
+    int64_t *cnt = (int64_t *)calloc((size_t)nio, sizeof(int64_t));
     for (int k = 0; k < nio; ++k) {
         double a[3] = {(double)io[k].axis[0], (double)io[k].axis[1], (double)io[k].axis[2]};
         double an = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
-        double nh[3] = {a[0] / an, a[1] / an, a[2] / an};
-        double su = 0.0, sr = 0.0;
-        int64_t cnt = 0;
-        for (int64_t s = 0; s < n; ++s) {
-            int adj = 0;
-            for (int i = 0; i < 18; ++i)
-                if (nbr[(int64_t)i * n + s] == -(2 + k)) adj = 1;
-            if (!adj) continue;
-            const double *m = &mom[4 * s];
-            su += m[1] * nh[0] + m[2] * nh[1] + m[3] * nh[2];
-            sr += m[0];
-            cnt += 1;
-        }
-        out[3 * k] = cnt ? su / (double)cnt : 0.0;
-        out[3 * k + 1] = cnt ? sr / (double)cnt : 0.0;
-        out[3 * k + 2] = (double)cnt;
+        for (int d = 0; d < 3; ++d) nh[3 * k + d] = a[d] / an;
     }
+    /* one pass in canonical order: each iolet's sums take its sites in that order */
+    for (int64_t s = 0; s < n; ++s) {
+        int seen[18], n_seen = 0;
+        for (int i = 0; i < 18; ++i) {
+            int32_t v = nbr[(int64_t)i * n + s];
+            if (v >= -1) continue;
+            int k = -v - 2, dup = 0;
+            for (int q = 0; q < n_seen; ++q) dup |= seen[q] == k;
+            if (!dup) seen[n_seen++] = k;
+        }
+        const double *m = &mom[4 * s];
+        for (int q = 0; q < n_seen; ++q) {
+            int k = seen[q];
+            su[k] += m[1] * nh[3 * k] + m[2] * nh[3 * k + 1] + m[3] * nh[3 * k + 2];
+            sr[k] += m[0];
+            cnt[k] += 1;
+        }
+    }
+    for (int k = 0; k < nio; ++k) {
+        out[3 * k] = cnt[k] ? su[k] / (double)cnt[k] : 0.0;
+        out[3 * k + 1] = cnt[k] ? sr[k] / (double)cnt[k] : 0.0;
+        out[3 * k + 2] = (double)cnt[k];
+    }
+    free(nh);
+    free(su);
+    free(sr);
+    free(cnt);
 }
 
 /* Total mass deviation: sum over sites and directions, canonical order. */
