@@ -131,9 +131,10 @@ def profiled_traffic(variant_key, launch):
     try:
         with open(path) as f:
             t = json.load(f)
-        e = t.get(variant_key)
-        if e and e.get("launch") == launch and e.get("kernel_source_sha") == kernel_source_sha():
-            return e["bytes_per_launch"], e.get("scaled_from")
+        entries = t.get(variant_key) or []
+        for e in entries if isinstance(entries, list) else [entries]:  # one record per launch shape
+            if e.get("launch") == launch and e.get("kernel_source_sha") == kernel_source_sha():
+                return e["bytes_per_launch"], e.get("scaled_from")
     except Exception:
         pass
     return None, None

@@ -20,10 +20,10 @@ import json
 import os
 
 DEFAULT_CANDIDATES = (
-    (256, 1, 0), (128, 1, 0), (512, 1, 0), (256, 2, 0),
-    (128, 1, 1), (128, 2, 1), (256, 2, 1), (64, 2, 1),
+    (256, 1, 0), (128, 1, 0), (512, 1, 0), (256, 2, 0), (128, 2, 0), (512, 2, 0),
+    (128, 1, 1), (256, 1, 1), (128, 2, 1), (256, 2, 1), (64, 2, 1),
     (128, 2, 2), (256, 2, 2), (256, 1, 2),  # variant 2: AA scheme only
-    (256, 1, 3), (128, 1, 3), (256, 2, 3),
+    (256, 1, 3), (128, 1, 3), (256, 2, 3), (128, 2, 3), (512, 2, 3), (128, 4, 3), (256, 4, 3),
 )
 # Variant 4 (staged AA odd-step stores) is measured slower than variant 1 on
 # every workload tried; it stays available through Context.set_launch.

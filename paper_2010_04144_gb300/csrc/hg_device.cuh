@@ -714,26 +714,14 @@ __device__ __forceinline__ void tile_aa_even_tma(const DomDev &D, const TileDev 
     }
 }
 
-// PAR is the parity of the step this launch executes: 0 = even, 1 = odd (AA:
-// the step kind; A/B: which buffer is the source), 2 = read from the domain's
-// step counter per block (batches whose domains are at different parities).
-// A static parity spares every block a dependent load before its first gather.
+// PAR is the parity of the step this launch executes: 0 = even, 1 = odd (the
+// AA step kind), 2 = read from the domain's step counter per block (A/B, and AA
+// batches whose domains are at different parities).
+// One tile of one domain, after the prologue has located it.
 template <int S, int SCHEME, int SPT, int PAR, int V>
-__device__ __forceinline__ void stream_collide_block(const DomDev *__restrict__ doms,
-                                                     const TileDev *__restrict__ tiles, int off) {
+__device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileDev &tl, bool odd,
+                                                    uint32_t *stage) {
     using T = typename St<S>::T;
-    __shared__ DomDev D;
-    __shared__ int64_t t_now;
-    extern __shared__ __align__(128) uint32_t stage[];
-    const TileDev tl = tiles[blockIdx.x];
-    if (threadIdx.x == 0) {
-        D = doms[tl.dom];
-        // the step this launch executes (1-based); only its parity matters, and a
-        // launch whose domains all share it gets it as a template argument
-        if constexpr (PAR == 2) t_now = *D.step + off + 1;
-    }
-    __syncthreads();
-    const bool odd = PAR == 2 ? (t_now & 1) != 0 : PAR == 1;
     if constexpr (V == 1 || V == 2 || V == 4) {
         if constexpr (SCHEME == kAB) {
             tile_ab_async<S, SPT>(D, tl, odd, stage);
@@ -748,113 +736,156 @@ __device__ __forceinline__ void stream_collide_block(const DomDev *__restrict__ 
             }
         }
     } else {
-    constexpr bool HINT = V == 3;
+        constexpr bool HINT = V == 3;
 #pragma unroll
-    for (int j = 0; j < SPT; ++j) {
-        const int r = j * blockDim.x + threadIdx.x;
-        const int64_t s = tl.start + r;
-        const bool live = r < tl.count;
-        if constexpr (SCHEME == kAB) {
-            if (live) {
-                const T *src = (const T *)D.f[odd ? 0 : 1];
-                T *dst = (T *)D.f[odd ? 1 : 0];
-                site_ab<S, HINT>(D, src, dst, s);
-            }
-        } else {
-            T *buf = (T *)D.f[0];
-            if (live) {
-                if (odd) site_aa_odd<S, HINT>(D, buf, s);
-                else site_aa_even<S, HINT>(D, buf, s);
+        for (int j = 0; j < SPT; ++j) {
+            const int r = j * blockDim.x + threadIdx.x;
+            const int64_t s = tl.start + r;
+            const bool live = r < tl.count;
+            if constexpr (SCHEME == kAB) {
+                if (live) {
+                    const T *src = (const T *)D.f[odd ? 0 : 1];
+                    T *dst = (T *)D.f[odd ? 1 : 0];
+                    site_ab<S, HINT>(D, src, dst, s);
+                }
+            } else {
+                T *buf = (T *)D.f[0];
+                if (live) {
+                    if (odd) site_aa_odd<S, HINT>(D, buf, s);
+                    else site_aa_even<S, HINT>(D, buf, s);
+                }
             }
         }
     }
-    }
 }
 
+// Many domains per launch: each block finds its tile in the tile table; the
+// first threads copy the tile's domain descriptor into shared memory, one
+// 8-byte word each, while thread 0 reads the domain's step counter.
 template <int S, int SCHEME, int SPT, int PAR, int V>
 __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict__ doms,
                                                         const TileDev *__restrict__ tiles,
-                                                        int off) {
-    stream_collide_block<S, SCHEME, SPT, PAR, V>(doms, tiles, off);
+                                                        const int64_t *__restrict__ steps, int off) {
+    static_assert(sizeof(DomDev) % 8 == 0, "descriptor copied in 8-byte words");
+    constexpr int kWords = (int)(sizeof(DomDev) / 8);
+    __shared__ DomDev D;
+    __shared__ int64_t t_now;
+    extern __shared__ __align__(128) uint32_t stage[];
+    const TileDev tl = tiles[blockIdx.x];
+    if (threadIdx.x < kWords)
+        reinterpret_cast<uint64_t *>(&D)[threadIdx.x] =
+            __ldg(reinterpret_cast<const uint64_t *>(doms + tl.dom) + threadIdx.x);
+    // the step this launch executes (1-based); only its parity matters, and a
+    // launch whose domains all share it gets it as a template argument
+    if constexpr (PAR == 2)
+        if (threadIdx.x == 0) t_now = __ldg(steps + tl.dom) + off + 1;
+    __syncthreads();
+    const bool odd = PAR == 2 ? (t_now & 1) != 0 : PAR == 1;
+    stream_collide_tile<S, SCHEME, SPT, PAR, V>(D, tl, odd, stage);
+}
+
+// One domain per launch: the descriptor is a kernel parameter (constant bank)
+// and block b takes sites [b*T, b*T + T) with T = SPT * blockDim, so no block
+// waits on a table load or a barrier before its first neighbour-table load.
+template <int S, int SCHEME, int SPT, int PAR, int V>
+__global__ void __launch_bounds__(512) k_stream_collide_one(const __grid_constant__ DomDev D, int64_t n,
+                                                            int off) {
+    extern __shared__ __align__(128) uint32_t stage[];
+    const int64_t ts = (int64_t)SPT * blockDim.x;
+    TileDev tl;
+    tl.dom = 0;
+    tl.start = (int64_t)blockIdx.x * ts;
+    tl.count = (int32_t)(n - tl.start < ts ? n - tl.start : ts);
+    bool odd;
+    if constexpr (PAR == 2) odd = ((__ldg(D.step) + off + 1) & 1) != 0;
+    else odd = PAR == 1;
+    stream_collide_tile<S, SCHEME, SPT, PAR, V>(D, tl, odd, stage);
 }
 
 
 template <int S, int SCHEME, int PAR, int V, int SPT>
 cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                          int64_t n_tiles, int off, cudaStream_t st) {
+                          int64_t n_tiles, int off, const OneDomain &one, cudaStream_t st) {
     // V1/V4: cp.async stage of 4-byte words (V4 reuses it for the odd step's outputs);
     // V2 also holds the even step's 19 rows + mbarrier
     size_t smem = (V == 1 || V == 2 || V == 4) ? (size_t)SPT * 19 * cfg.block * 4 : 0;
     if (V == 2) smem += 16;
+    if (one.d) {
+        auto k = k_stream_collide_one<S, SCHEME, SPT, PAR, V>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        k<<<(unsigned)n_tiles, cfg.block, smem, st>>>(*one.d, one.n, off);
+        return cudaGetLastError();
+    }
     auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)n_tiles, cfg.block, smem, st>>>(doms, tiles, off);
+    k<<<(unsigned)n_tiles, cfg.block, smem, st>>>(doms, tiles, one.steps, off);
     return cudaGetLastError();
 }
 
 template <int S, int SCHEME, int PAR>
 cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                          int64_t n_tiles, int off, cudaStream_t st) {
+                          int64_t n_tiles, int off, const OneDomain &one, cudaStream_t st) {
     if (cfg.variant == 1) {
         switch (cfg.spt) {
-            case 1: return launch_sc_one<S, SCHEME, PAR, 1, 1>(cfg, doms, tiles, n_tiles, off, st);
-            case 2: return launch_sc_one<S, SCHEME, PAR, 1, 2>(cfg, doms, tiles, n_tiles, off, st);
+            case 1: return launch_sc_one<S, SCHEME, PAR, 1, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 1, 2>(cfg, doms, tiles, n_tiles, off, one, st);
             default: return cudaErrorInvalidValue;
         }
     }
     if (cfg.variant == 3) {
         switch (cfg.spt) {
-            case 1: return launch_sc_one<S, SCHEME, PAR, 3, 1>(cfg, doms, tiles, n_tiles, off, st);
-            case 2: return launch_sc_one<S, SCHEME, PAR, 3, 2>(cfg, doms, tiles, n_tiles, off, st);
-            case 4: return launch_sc_one<S, SCHEME, PAR, 3, 4>(cfg, doms, tiles, n_tiles, off, st);
+            case 1: return launch_sc_one<S, SCHEME, PAR, 3, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 3, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 4: return launch_sc_one<S, SCHEME, PAR, 3, 4>(cfg, doms, tiles, n_tiles, off, one, st);
             default: return cudaErrorInvalidValue;
         }
     }
     if (cfg.variant == 4) {
         if constexpr (SCHEME == kAB) return cudaErrorInvalidValue;
         else if (cfg.spt != 1) return cudaErrorInvalidValue;
-        else return launch_sc_one<S, SCHEME, PAR, 4, 1>(cfg, doms, tiles, n_tiles, off, st);
+        else return launch_sc_one<S, SCHEME, PAR, 4, 1>(cfg, doms, tiles, n_tiles, off, one, st);
     }
     if (cfg.variant == 2) {
         if (SCHEME == kAB) return cudaErrorInvalidValue;
         switch (cfg.spt) {
-            case 1: return launch_sc_one<S, SCHEME, PAR, 2, 1>(cfg, doms, tiles, n_tiles, off, st);
-            case 2: return launch_sc_one<S, SCHEME, PAR, 2, 2>(cfg, doms, tiles, n_tiles, off, st);
+            case 1: return launch_sc_one<S, SCHEME, PAR, 2, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 2, 2>(cfg, doms, tiles, n_tiles, off, one, st);
             default: return cudaErrorInvalidValue;
         }
     }
     switch (cfg.spt) {
-        case 1: return launch_sc_one<S, SCHEME, PAR, 0, 1>(cfg, doms, tiles, n_tiles, off, st);
-        case 2: return launch_sc_one<S, SCHEME, PAR, 0, 2>(cfg, doms, tiles, n_tiles, off, st);
-        case 4: return launch_sc_one<S, SCHEME, PAR, 0, 4>(cfg, doms, tiles, n_tiles, off, st);
+        case 1: return launch_sc_one<S, SCHEME, PAR, 0, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+        case 2: return launch_sc_one<S, SCHEME, PAR, 0, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+        case 4: return launch_sc_one<S, SCHEME, PAR, 0, 4>(cfg, doms, tiles, n_tiles, off, one, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 template <int S>
 cudaError_t launch_sc_storage(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                              int64_t n_tiles, int off, int parity, cudaStream_t st) {
-    if (cfg.scheme == kAB) {
-        if (parity == 0) return launch_sc_spt<S, kAB, 0>(cfg, doms, tiles, n_tiles, off, st);
-        if (parity == 1) return launch_sc_spt<S, kAB, 1>(cfg, doms, tiles, n_tiles, off, st);
-        return launch_sc_spt<S, kAB, 2>(cfg, doms, tiles, n_tiles, off, st);
-    }
-    if (parity == 0) return launch_sc_spt<S, kAA, 0>(cfg, doms, tiles, n_tiles, off, st);
-    if (parity == 1) return launch_sc_spt<S, kAA, 1>(cfg, doms, tiles, n_tiles, off, st);
-    return launch_sc_spt<S, kAA, 2>(cfg, doms, tiles, n_tiles, off, st);
+                              int64_t n_tiles, int off, int parity, const OneDomain &one, cudaStream_t st) {
+    // A/B reads its buffer parity per block: specialising it measured slower (the
+    // compile-time buffer choice raised the variant-3 kernel from 52 to 58 registers)
+    if (cfg.scheme == kAB) return launch_sc_spt<S, kAB, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+    if (parity == 0) return launch_sc_spt<S, kAA, 0>(cfg, doms, tiles, n_tiles, off, one, st);
+    if (parity == 1) return launch_sc_spt<S, kAA, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+    return launch_sc_spt<S, kAA, 2>(cfg, doms, tiles, n_tiles, off, one, st);
 }
 
 }  // namespace
 
 // One per storage type, each in its own translation unit.
 cudaError_t launch_sc_f32(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
-                          int off, int parity, cudaStream_t st);
+                          int off, int parity, const OneDomain &one, cudaStream_t st);
 cudaError_t launch_sc_f16(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
-                          int off, int parity, cudaStream_t st);
+                          int off, int parity, const OneDomain &one, cudaStream_t st);
 cudaError_t launch_sc_bf16(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
-                           int off, int parity, cudaStream_t st);
+                           int off, int parity, const OneDomain &one, cudaStream_t st);
 
 }  // namespace hg

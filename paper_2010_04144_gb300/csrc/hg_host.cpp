@@ -259,6 +259,8 @@ struct PlanKey {
 struct Plan {
     std::vector<int32_t> doms;
     DevBuf tiles, ios, adv, chunks, partials, counters, rev, fslots;
+    DomDev one{};       // single-domain plans: the descriptor passed by value to stream-collide
+    bool single = false;
     int64_t n_tiles = 0;
     int n_fslots = 0;  // (domain, slot) pairs the body-force pass visits
     int n_ios = 0;
@@ -1126,6 +1128,10 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
                  forced.end());
     p->n_tiles = (int64_t)tiles.size();
     p->n_ios = (int)ios.size();
+    if (doms.size() == 1) {
+        p->single = true;
+        p->one = make_domdev(ctx, ctx->doms[doms[0]]);
+    }
     p->n_chunks = (int)chunks.size();
     int rc = dev_alloc(ctx, p->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TileDev));
     if (rc == HG_OK) rc = dev_alloc(ctx, p->ios, std::max<size_t>(1, ios.size()) * sizeof(IoDev));
@@ -1183,17 +1189,19 @@ int parity_mode(hg_ctx *ctx, const std::vector<int32_t> &doms) {
 }
 
 // Kernel parity argument for the step at offset `off` of a group starting in `mode`.
-inline int step_parity(hg_ctx *, int mode, int64_t off) {
-    if (mode == 2) return 2;
+inline int step_parity(hg_ctx *ctx, int mode, int64_t off) {
+    if (ctx->scheme == HG_SCHEME_AB || mode == 2) return 2;
     return (int)((mode + off + 1) & 1);  // 1 when the executed step is odd
 }
 
 cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
     CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
     for (int64_t off = 0; off < k; ++off) {
+        const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
+                            (const int64_t *)ctx->steps.p};
         cudaError_t e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p,
                                               (const TileDev *)p->tiles.p, p->n_tiles, (int)off,
-                                              step_parity(ctx, mode, off), ctx->stream);
+                                              step_parity(ctx, mode, off), one, ctx->stream);
         if (e != cudaSuccess) return e;
         e = launch_guo_force(ctx->storage, ctx->scheme, (const DomDev *)ctx->dom_table.p,
                              (const int2 *)p->fslots.p, p->n_fslots, (int)off, ctx->stream);
@@ -1302,8 +1310,10 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float
     cudaError_t e = cudaSuccess;
     for (int64_t j = 0; j < n && e == cudaSuccess; ++j) {
         cudaEventRecord(ev[3 * j], ctx->stream);
+        const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
+                            (const int64_t *)ctx->steps.p};
         e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
-                                  p->n_tiles, (int)j, step_parity(ctx, mode, j), ctx->stream);
+                                  p->n_tiles, (int)j, step_parity(ctx, mode, j), one, ctx->stream);
         cudaEventRecord(ev[3 * j + 1], ctx->stream);
         if (e == cudaSuccess)  // the body-force pass (if any) is timed with the iolet update
             e = launch_guo_force(ctx->storage, ctx->scheme, (const DomDev *)ctx->dom_table.p,

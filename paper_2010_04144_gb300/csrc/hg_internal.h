@@ -26,18 +26,28 @@ struct DomDev {
     const uint32_t *iomask;   // bit s: site s has an iolet link
     const int32_t *ioprefix;  // per 32-site word: flagged sites before it (slot = rank of the flag)
     const int32_t *io_codes;  // per slot x 18: canonical codes (-1 wall, -(2+k) iolet, >= 0 fluid)
-    const int32_t *slot_site; // per slot: the site's device index
     float4 *bnd;              // per adjacent slot: (drho, ux, uy, uz) of the step's G_t
     const float *coef;        // per adjacent slot x 18: velocity-link coefficient 6 w_i c_i.(-a) phi
     const float *bcv;         // per iolet: boundary value of the step being run
     const int8_t *io_kind;    // per iolet: 0 pressure, 1 velocity
-    const float4 *io_force;   // per iolet: body-force density on its adjacent sites (null = none)
     const int64_t *step;      // completed steps before the current launch group
     int32_t *err;             // context error word: set when a bounded device wait gives up
     int64_t n;                // sites
     int64_t np;               // row stride (n padded)
     float omega;              // 1 / tau
     int32_t n_io;
+    // read by the body-force pass only (kept after the fields stream-collide reads)
+    const int32_t *slot_site; // per slot: the site's device index
+    const float4 *io_force;   // per iolet: body-force density on its adjacent sites (null = none)
+};
+
+// A launch over one domain only: its descriptor (host copy, passed by value as a
+// kernel parameter) and site count; d == nullptr means "use the tile table".
+// steps: the context's per-domain step counters (indexed by TileDev::dom).
+struct OneDomain {
+    const DomDev *d;
+    int64_t n;
+    const int64_t *steps;
 };
 
 // One block of the stream-collide grid: `count` sites of domain `dom` from `start`.
@@ -90,10 +100,11 @@ struct CollideCfg {
                   // stores staged in shared memory (spt 1)
 };
 
-// parity: 0 = every domain runs an even step, 1 = odd, 2 = per-domain
+// parity (AA only): 0 = every domain runs an even step, 1 = odd, 2 = per-domain
 // parity read from the step counters.
 cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                                  int64_t n_tiles, int off, int parity, cudaStream_t st);
+                                  int64_t n_tiles, int off, int parity, const OneDomain &one,
+                                  cudaStream_t st);
 // One CTA per (iolet, chunk) in `chunks`; partials: 2 doubles per chunk;
 // counters: n_ios + 1 zeroed unsigned ints (left zeroed on return).
 cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, const int2 *chunks, int n_chunks,

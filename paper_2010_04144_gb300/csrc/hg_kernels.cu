@@ -367,11 +367,12 @@ inline unsigned rb_grid(int64_t n) {
 }  // namespace
 
 cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                                  int64_t n_tiles, int off, int parity, cudaStream_t st) {
+                                  int64_t n_tiles, int off, int parity, const OneDomain &one,
+                                  cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    if (cfg.storage == kF32) return launch_sc_f32(cfg, doms, tiles, n_tiles, off, parity, st);
-    if (cfg.storage == kF16) return launch_sc_f16(cfg, doms, tiles, n_tiles, off, parity, st);
-    if (cfg.storage == kBF16) return launch_sc_bf16(cfg, doms, tiles, n_tiles, off, parity, st);
+    if (cfg.storage == kF32) return launch_sc_f32(cfg, doms, tiles, n_tiles, off, parity, one, st);
+    if (cfg.storage == kF16) return launch_sc_f16(cfg, doms, tiles, n_tiles, off, parity, one, st);
+    if (cfg.storage == kBF16) return launch_sc_bf16(cfg, doms, tiles, n_tiles, off, parity, one, st);
     return cudaErrorInvalidValue;
 }
 

@@ -4,8 +4,8 @@
 namespace hg {
 
 cudaError_t launch_sc_f16(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
-                          int off, int parity, cudaStream_t st) {
-    return launch_sc_storage<kF16>(cfg, doms, tiles, n_tiles, off, parity, st);
+                          int off, int parity, const OneDomain &one, cudaStream_t st) {
+    return launch_sc_storage<kF16>(cfg, doms, tiles, n_tiles, off, parity, one, st);
 }
 
 }  // namespace hg
