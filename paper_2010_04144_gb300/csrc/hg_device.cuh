@@ -263,10 +263,21 @@ __device__ __forceinline__ void apply_iolet_links(const DomDev &D, int slot, flo
         if (c < -1) g[I] = iolet_rule<I, St<S>::kScaled>(D, -c - 2, slot, g[I]);
     });
 }
+// A stream-collide launch may start while the previous step's iolet update is
+// still running (programmatic dependent launch): everything it reads except the
+// boundary values was complete before that update began.  Only the sites with
+// an iolet link use those values (and overwrite the moments slot the update
+// reads), so only they wait here for the update to finish.  Without an
+// overlapping launch the wait returns at once.
+__device__ __forceinline__ void wait_for_iolet_update() {
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+
 template <int S>
 __device__ __forceinline__ int iolet_fixup(const DomDev &D, int64_t s, float g[19]) {
     uint32_t word;
     if (!site_flag(D, s, word)) return -1;
+    wait_for_iolet_update();
     const int slot = site_slot(D, s, word);
     apply_iolet_links<S>(D, slot, g);
     return slot;
@@ -810,22 +821,30 @@ cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileD
     // V2 also holds the even step's 19 rows + mbarrier
     size_t smem = (V == 1 || V == 2 || V == 4) ? (size_t)SPT * 19 * cfg.block * 4 : 0;
     if (V == 2) smem += 16;
+    cudaLaunchConfig_t lc = {};
+    lc.gridDim = dim3((unsigned)n_tiles);
+    lc.blockDim = dim3((unsigned)cfg.block);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = 1;
+    lc.attrs = at;
+    lc.numAttrs = one.overlap_previous ? 1 : 0;  // start while the previous iolet update runs
     if (one.d) {
         auto k = k_stream_collide_one<S, SCHEME, SPT, PAR, V>;
         if (smem > 48 * 1024) {
             cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
             if (e != cudaSuccess) return e;
         }
-        k<<<(unsigned)n_tiles, cfg.block, smem, st>>>(*one.d, one.n, off);
-        return cudaGetLastError();
+        return cudaLaunchKernelEx(&lc, k, *one.d, one.n, off);
     }
     auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
     if (smem > 48 * 1024) {
         cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
     }
-    k<<<(unsigned)n_tiles, cfg.block, smem, st>>>(doms, tiles, one.steps, off);
-    return cudaGetLastError();
+    return cudaLaunchKernelEx(&lc, k, doms, tiles, one.steps, off);
 }
 
 template <int S, int SCHEME, int PAR>

@@ -1197,8 +1197,10 @@ inline int step_parity(hg_ctx *ctx, int mode, int64_t off) {
 cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
     CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
     for (int64_t off = 0; off < k; ++off) {
+        // after the first step of a group the previous kernel is this group's iolet update
+        // (the first follows the step-counter advance, which the parity read needs)
         const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
-                            (const int64_t *)ctx->steps.p};
+                            (const int64_t *)ctx->steps.p, off > 0 && p->n_ios > 0};
         cudaError_t e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p,
                                               (const TileDev *)p->tiles.p, p->n_tiles, (int)off,
                                               step_parity(ctx, mode, off), one, ctx->stream);
@@ -1311,7 +1313,7 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float
     for (int64_t j = 0; j < n && e == cudaSuccess; ++j) {
         cudaEventRecord(ev[3 * j], ctx->stream);
         const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
-                            (const int64_t *)ctx->steps.p};
+                            (const int64_t *)ctx->steps.p, false};  // timed launches stay serial
         e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
                                   p->n_tiles, (int)j, step_parity(ctx, mode, j), one, ctx->stream);
         cudaEventRecord(ev[3 * j + 1], ctx->stream);

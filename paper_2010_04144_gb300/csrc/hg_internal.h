@@ -44,10 +44,14 @@ struct DomDev {
 // A launch over one domain only: its descriptor (host copy, passed by value as a
 // kernel parameter) and site count; d == nullptr means "use the tile table".
 // steps: the context's per-domain step counters (indexed by TileDev::dom).
+// overlap_previous: the launch directly follows the previous step's iolet update
+// on the stream and may start before it ends (programmatic dependent launch);
+// only sites with iolet links wait for it.
 struct OneDomain {
     const DomDev *d;
     int64_t n;
     const int64_t *steps;
+    bool overlap_previous;
 };
 
 // One block of the stream-collide grid: `count` sites of domain `dom` from `start`.

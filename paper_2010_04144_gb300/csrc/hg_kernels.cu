@@ -69,6 +69,9 @@ __global__ void __launch_bounds__(kIoChunk) k_iolet_update(const IoDev *__restri
                                                            const int2 *__restrict__ chunks,
                                                            double2 *partials, unsigned *counters,
                                                            int off) {
+    // the next step's stream-collide may launch now: it waits for this grid
+    // only where it needs the boundary values this grid produces
+    asm volatile("griddepcontrol.launch_dependents;");
     __shared__ int s_last;
     const int2 ck = chunks[blockIdx.x];
     const IoDev &I = ios[ck.x];
