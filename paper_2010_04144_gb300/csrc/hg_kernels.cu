@@ -6,21 +6,26 @@
 // values drive the paired inlets of a coupled domain.
 //
 // Kernels
-//   k_stream_collide   fused streaming + boundary rules + LBGK collision for
-//                      every site of one or many domains (tile table), A/B pull
-//                      or AA in-place, FP32 / FP16 / BF16 storage.  HBM-bound.
+//   k_stream_collide_one / k_stream_collide (hg_device.cuh, instantiated per
+//                      storage type in hg_sc_f32.cu / hg_sc_f16.cu / hg_sc_bf16.cu):
+//                      fused streaming + boundary rules + LBGK collision for
+//                      every site of one domain, or of many through a tile
+//                      table; A/B pull or AA in place; FP32 / FP16 / BF16
+//                      storage.  HBM-bound.
+//   k_guo_force        body force on the sites next to forced arterial outlets
+//                      (alternating coupling exchanges only).
 //   k_iolet_update     per iolet: FP64 mean of u.n and drho over its adjacent
-//                      sites (fixed order), then the boundary value of the next
-//                      step (pulse, or coupled factor x source mean).
-//   k_advance          bumps the per-domain completed-step counters.
+//                      sites (fixed order), then the boundary values of the
+//                      next step (pulse, coupled factor x source mean, or the
+//                      reverse exchange's outlet force).  It lets the next
+//                      step's stream-collide start early (programmatic
+//                      dependent launch).
+//   k_advance_list     bumps the per-domain completed-step counters.
 //   k_macroscopic / k_export_state / k_import_state / k_mass*: read-back.
 //
-// Each launch carries the parity of the step it executes when all its domains
-// share it (graphs hold an even number of steps, so replays keep it); mixed
-// batches read it from the per-domain step counters.
-//
-// The stream-collide kernel lives in hg_device.cuh and is instantiated per
-// storage type in hg_sc_f32.cu / hg_sc_f16.cu / hg_sc_bf16.cu.
+// AA launches whose domains all share the parity of the step they execute get
+// it as a template argument (graphs hold an even number of steps, so replays
+// keep it); A/B launches and mixed AA batches read it from the step counters.
 //
 // Neighbour table on the device: entry i-1 of site s is the index of the pull
 // source x_s - c_i when it is fluid, else a virtual index s + d*np (d = +-1)
