@@ -290,7 +290,7 @@ struct hg_ctx {
     DevBuf steps;                   // int64[capacity]
     int capacity = 0;
     std::map<std::pair<int32_t, int32_t>, CoupleSrc> coupled;  // (dst dom, dst k) -> source
-    int couple_mode = HG_COUPLE_FORWARD;
+    std::atomic<int> couple_mode{HG_COUPLE_FORWARD};  // read by builds on another thread
     std::map<PlanKey, std::unique_ptr<Plan>> plans;
     DevBuf scratch;                 // mass partials, read-back staging
     std::atomic<int64_t> device_bytes{0};
@@ -490,18 +490,26 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
         c->own_stream = true;
     }
     c->capacity = 4096;
+    // on any failure below, release what was set up so far
+    auto undo = [&](int code) {
+        if (c->stream) cudaStreamSynchronize(c->stream);
+        dev_free(c.get(), c->dom_table);
+        dev_free(c.get(), c->steps);
+        dev_free(c.get(), c->errw);
+        if (c->own_stream) cudaStreamDestroy(c->stream);
+        cudaGetLastError();
+        return code;
+    };
     int rc = dev_alloc(c.get(), c->dom_table, sizeof(DomDev) * c->capacity);
     if (rc == HG_OK) rc = dev_alloc(c.get(), c->steps, sizeof(int64_t) * c->capacity);
     if (rc == HG_OK) rc = dev_alloc(c.get(), c->errw, 256);
-    if (rc != HG_OK) {
-        if (c->own_stream) cudaStreamDestroy(c->stream);
-        return rc;
-    }
-    if (cudaMemsetAsync(c->steps.p, 0, c->steps.bytes, c->stream) != cudaSuccess) return HG_ERR_CUDA;
-    if (cudaMemsetAsync(c->errw.p, 0, c->errw.bytes, c->stream) != cudaSuccess) return HG_ERR_CUDA;
+    if (rc != HG_OK) return undo(rc);
+    if (cudaMemsetAsync(c->steps.p, 0, c->steps.bytes, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(c->errw.p, 0, c->errw.bytes, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+        return undo(HG_ERR_CUDA);
     c->doms.assign(c->capacity, nullptr);
     c->reserved.assign(c->capacity, 0);
-    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return HG_ERR_CUDA;
     *out = c.release();
     return HG_OK;
 }
