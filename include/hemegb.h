@@ -103,7 +103,10 @@ typedef struct {
                                      sites_per_thread 1 or 2);
                                  3 = 0, with L2 256-byte prefetch hints on every load;
                                  4 = 1, with the AA odd step's stores staged in shared memory
-                                     and written coalesced (AA only, sites_per_thread 1) */
+                                     and written coalesced (AA only, sites_per_thread 1);
+                                 5 = 0 on pairs of adjacent sites sharing table loads and
+                                     packed stores (A/B with FP16/BF16 storage,
+                                     sites_per_thread 2) */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */

@@ -24,10 +24,12 @@ DEFAULT_CANDIDATES = (
     (128, 1, 1), (256, 1, 1), (128, 2, 1), (256, 2, 1), (64, 2, 1),
     (128, 2, 2), (256, 2, 2), (256, 1, 2),  # variant 2: AA scheme only
     (256, 1, 3), (128, 1, 3), (256, 2, 3), (128, 2, 3), (512, 2, 3), (128, 4, 3), (256, 4, 3),
+    (128, 2, 5), (256, 2, 5), (512, 2, 5),  # variant 5: A/B with 16-bit storage only
 )
 # Variant 4 (staged AA odd-step stores) is measured slower than variant 1 on
 # every workload tried; it stays available through Context.set_launch.
 AA_ONLY = (2, 4)
+AB_16BIT_ONLY = (5,)
 
 
 def _cache_path():
@@ -75,6 +77,8 @@ def autotune(ctx, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2, use_cache=T
         raise ValueError("autotune needs at least one domain in the context")
     if ctx.scheme != 1:
         candidates = [c for c in candidates if c[2] not in AA_ONLY]
+    if ctx.scheme != 0 or ctx.storage == 0:
+        candidates = [c for c in candidates if c[2] not in AB_16BIT_ONLY]
     key = _key(ctx, candidates)
     if use_cache:
         hit = _load().get(key)

@@ -602,6 +602,36 @@ template <int S16> struct Pair16 {
 template <> struct Pair<kF16> : Pair16<kF16> {};
 template <> struct Pair<kBF16> : Pair16<kBF16> {};
 
+// ---- A/B pull on a pair of adjacent sites (variant 5, 16-bit storage) ----
+// Sites s and s+1 (s even) share one 8-byte load per neighbour-table row, one
+// 4-byte load of the rest values and one 4-byte store per direction: fewer
+// memory instructions per site for a kernel that runs near its issue limit.
+template <int S>
+__device__ __forceinline__ void site_ab_pair(const DomDev &D, const typename St<S>::T *__restrict__ src,
+                                             typename St<S>::T *__restrict__ dst, int64_t s) {
+    using Tr = St<S>;
+    const int64_t np = D.np;
+    float ga[19], gb[19];
+    Pair<S>::template ld<0>(src + s, ga[0], gb[0]);
+    unroll<1, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        const int2 nb = __ldg(reinterpret_cast<const int2 *>(D.nbr + (int64_t)(I - 1) * np + s));
+        ga[I] = Tr::template ld<I>(ldg_nc(src + ((int64_t)I * np + nb.x)));
+        gb[I] = Tr::template ld<I>(ldg_nc(src + ((int64_t)I * np + nb.y)));
+    });
+    const int slot_a = iolet_fixup<S>(D, s, ga);
+    const int slot_b = iolet_fixup<S>(D, s + 1, gb);
+    const float4 ma = collide_s<S>(ga, D.omega);
+    const float4 mb = collide_s<S>(gb, D.omega);
+    typename St<S>::T *wb = opaque(dst + s);
+    unroll<0, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        Pair<S>::template st<I>(wb + (int64_t)I * np, ga[I], gb[I]);
+    });
+    if (slot_a >= 0) D.bnd[slot_a] = ma;
+    if (slot_b >= 0) D.bnd[slot_b] = mb;
+}
+
 template <int S>
 __device__ __forceinline__ void tile_aa_even_pairs(const DomDev &D, const TileDev &tl) {
     using T = typename St<S>::T;
@@ -746,6 +776,15 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
                 tile_aa_even_pairs<S>(D, tl);
             }
         }
+    } else if constexpr (V == 5) {
+        // A/B on adjacent pairs: each thread takes sites 2t and 2t+1 of the tile (SPT = 2)
+        static_assert(SCHEME == kAB && SPT == 2, "variant 5 is the A/B pair form");
+        const int r = 2 * threadIdx.x;
+        const int64_t s = tl.start + r;  // even: tiles start at multiples of 2 * blockDim
+        const T *src = (const T *)D.f[odd ? 0 : 1];
+        T *dst = (T *)D.f[odd ? 1 : 0];
+        if (r + 1 < tl.count) site_ab_pair<S>(D, src, dst, s);
+        else if (r < tl.count) site_ab<S, false>(D, src, dst, s);  // ragged tail: one site
     } else {
         constexpr bool HINT = V == 3;
 #pragma unroll
@@ -869,6 +908,11 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
         if constexpr (SCHEME == kAB) return cudaErrorInvalidValue;
         else if (cfg.spt != 1) return cudaErrorInvalidValue;
         else return launch_sc_one<S, SCHEME, PAR, 4, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+    }
+    if (cfg.variant == 5) {
+        if constexpr (SCHEME != kAB || S == kF32) return cudaErrorInvalidValue;
+        else if (cfg.spt != 2) return cudaErrorInvalidValue;
+        else return launch_sc_one<S, SCHEME, PAR, 5, 2>(cfg, doms, tiles, n_tiles, off, one, st);
     }
     if (cfg.variant == 2) {
         if (SCHEME == kAB) return cudaErrorInvalidValue;

@@ -434,12 +434,13 @@ const DomDev *domdev_ptr(hg_domain *d) {
 size_t elem_bytes(int storage) { return storage == HG_STORE_F32 ? 4 : 2; }
 
 // Kernel variants and the launch shapes each supports (see hg_ctx_params).
-bool variant_ok(int scheme, int spt, int variant) {
+bool variant_ok(int storage, int scheme, int spt, int variant) {
     switch (variant) {
         case 0: case 3: return true;
         case 1: return spt != 4;
         case 2: return spt != 4 && scheme == HG_SCHEME_AA;
         case 4: return spt == 1 && scheme == HG_SCHEME_AA;
+        case 5: return spt == 2 && scheme == HG_SCHEME_AB && storage != HG_STORE_F32;
         default: return false;
     }
 }
@@ -465,7 +466,7 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
     int spt = p->sites_per_thread ? p->sites_per_thread : 1;
     if (block < 32 || block > 512 || block % 32) return HG_ERR_ARG;
     if (spt != 1 && spt != 2 && spt != 4) return HG_ERR_ARG;
-    if (!variant_ok(p->scheme, spt, p->kernel_variant)) return HG_ERR_ARG;
+    if (!variant_ok(p->storage, p->scheme, spt, p->kernel_variant)) return HG_ERR_ARG;
     if ((p->alloc == nullptr) != (p->free == nullptr)) return HG_ERR_ARG;
     std::unique_ptr<hg_ctx> c(new hg_ctx);
     c->device = p->device;
@@ -1362,9 +1363,10 @@ int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) 
     if (!ctx) return HG_ERR_ARG;
     if (block < 32 || block > 512 || block % 32) return fail(ctx, HG_ERR_ARG, "block size must be a multiple of 32 in [32, 512]");
     if (spt != 1 && spt != 2 && spt != 4) return fail(ctx, HG_ERR_ARG, "sites per thread must be 1, 2 or 4");
-    if (!variant_ok(ctx->scheme, spt, variant))
+    if (!variant_ok(ctx->storage, ctx->scheme, spt, variant))
         return fail(ctx, HG_ERR_ARG, "kernel variant must be 0 or 3, 1 or 2 with 1 or 2 sites per thread "
-                                     "(2: AA only), or 4 with 1 site per thread (AA only)");
+                                     "(2: AA only), 4 with 1 site per thread (AA only), or 5 with 2 sites "
+                                     "per thread (A/B, 16-bit storage only)");
     if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));

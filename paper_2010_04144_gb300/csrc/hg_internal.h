@@ -101,7 +101,8 @@ struct CollideCfg {
     int variant;  // 0 = gathers into registers, 1 = gathers staged by cp.async (spt 1 or 2),
                   // 2 = as 1, and the AA even step moves whole rows with TMA bulk copies,
                   // 3 = as 0 with L2 prefetch hints, 4 = as 1 with the AA odd step's
-                  // stores staged in shared memory (spt 1)
+                  // stores staged in shared memory (spt 1), 5 = A/B on adjacent site
+                  // pairs (16-bit storage, spt 2)
 };
 
 // parity (AA only): 0 = every domain runs an even step, 1 = odd, 2 = per-domain

@@ -258,7 +258,8 @@ LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128,
             ("aa", 256, 1, 0), ("aa", 128, 4, 0), ("aa", 256, 1, 1), ("aa", 256, 2, 1),
             ("aa", 64, 2, 1), ("aa", 128, 2, 2), ("aa", 256, 1, 2), ("aa", 64, 2, 2),
             ("ab", 256, 1, 3), ("ab", 128, 4, 3), ("aa", 256, 1, 3), ("aa", 128, 2, 3),
-            ("aa", 256, 1, 4), ("aa", 64, 1, 4), ("aa", 512, 1, 4)]
+            ("aa", 256, 1, 4), ("aa", 64, 1, 4), ("aa", 512, 1, 4),
+            ("ab", 256, 2, 5), ("ab", 64, 2, 5)]   # variant 5: A/B, 16-bit storage only
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
@@ -267,6 +268,8 @@ def test_kernel_variants_bit_identical(gpu, storage):
     geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
     ref = {}
     for (scheme, block, spt, var) in LAUNCHES:
+        if var == 5 and storage == "f32":
+            continue
         ctx = gpu.Context(storage=storage, scheme=scheme, block_size=block, sites_per_thread=spt,
                           kernel_variant=var)
         try:
@@ -303,6 +306,14 @@ def test_variant4_against_oracle_and_launch_rules(gpu, oracle_mod):
         try:
             with pytest.raises(gpu.HgError):
                 ctx.set_launch(256, spt, 4)
+        finally:
+            ctx.close()
+    # variant 5 (adjacent pairs) is A/B with 16-bit storage and 2 sites per thread only
+    for storage, scheme, spt in (("f32", "ab", 2), ("f16", "aa", 2), ("f16", "ab", 1)):
+        ctx = gpu.Context(storage=storage, scheme=scheme)
+        try:
+            with pytest.raises(gpu.HgError):
+                ctx.set_launch(256, spt, 5)
         finally:
             ctx.close()
 
