@@ -30,17 +30,19 @@ import numpy as np
 
 from . import hemegb as H
 
-# device bytes per site (distributions + neighbour table + iolet mask)
+# bytes per stored distribution value
 _STATE_BYTES = {0: 4, 1: 2, 2: 2}
 
 
 def footprint_bytes(n_sites, storage, scheme, n_iolets=2):
-    """Estimated HBM bytes of one domain before it is built."""
+    """Estimated HBM bytes of one domain before it is built: distributions, neighbour
+    table, iolet mask and prefix per site; moments, link codes, link coefficients and
+    site index per boundary slot; per-iolet values."""
     np_ = max(128, (n_sites + 127) // 128 * 128)
     copies = 2 if scheme == H.SCHEME["ab"] else 1
-    per_site = 19 * _STATE_BYTES[storage] * copies + 72 + 0.125
-    adjacent = 0.05 * n_sites  # generous bound on sites next to iolets (88 B each)
-    return int(per_site * np_ + 88 * adjacent + 64 * n_iolets + 4 * 4096)
+    per_site = 19 * _STATE_BYTES[storage] * copies + 72 + 0.25
+    adjacent = 0.05 * n_sites  # generous bound on sites next to iolets (164 B each)
+    return int(per_site * np_ + 164 * adjacent + 64 * n_iolets + 4 * 4096)
 
 
 @dataclass
