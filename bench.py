@@ -649,7 +649,7 @@ def main():
         "roofline": {"bound": "hbm", "achieved": h["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": h["achieved_gbs"] / peak, "traffic": traffic,
                      "traffic_note": scaled_from,
-                     "kernel": "k_stream_collide",
+                     "kernel": "k_stream_collide_one (single-domain stream-collide)",
                      "bytes_per_update": h["bytes_per_update"],
                      "launch_ms": h["ms_sc"] / args.steps,
                      "peak_source": f"{peak_kind} HBM copy bandwidth (MEASURED_PEAKS.json hbm_gbs)"},
