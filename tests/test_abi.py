@@ -1,4 +1,5 @@
-"""The C-ABI library loads and exports every symbol include/hemegb.h declares (CPU only).
+"""The C-ABI library loads and exports every symbol include/hemegb.h declares (CPU only);
+the header is plain C99.
 
 Also checks the one host-only entry point, hg_coupling_factors (Section 3's
 coupling map and scale factors), against the oracle's implementation.
@@ -8,6 +9,7 @@ import re
 import subprocess
 
 import numpy as np
+import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
@@ -86,3 +88,17 @@ def test_paper_example_through_abi(hemegb_lib):
     assign, dist, dp, fac = hemegb_lib.hg_coupling_factors(art, [1.0], ven, [1.0] * 3, un)
     assert list(assign) == [0, 0, 0]
     assert [round(f, 2) for f in fac] == [float(r[2]) for r in rows]
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/hemegb.h compiles as strict C99 (a C ABI with no C++ or CUDA types)."""
+    import shutil
+
+    if shutil.which("gcc") is None:
+        pytest.skip("no C compiler")
+    hdr = os.path.join(ROOT, "include", "hemegb.h")
+    src = tmp_path / "use.c"
+    src.write_text(f'#include "{hdr}"\nint main(void) {{ hg_ctx_params p = {{0}}; (void)p; return 0; }}\n')
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-c", str(src),
+                        "-o", str(tmp_path / "use.o")], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
