@@ -192,6 +192,14 @@ int hg_domain_sites(hg_domain *d, int32_t *xyz_out);
  * (host), decoded to the conventions above. */
 int hg_domain_neighbours(hg_domain *d, int32_t *nbr_out);
 
+/* Host only (no context, no device): the canonical site order and neighbour
+ * table hg_domain_create builds for the same input, with the same checks.
+ * xyz_out: n_fluid x 3 in canonical order (may be NULL); nbr_out:
+ * nbr[18][n_fluid] in the conventions above.  Errors: HG_ERR_ARG (bad sizes,
+ * coordinates, duplicates or iolets). */
+int hg_build_neighbours(const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets, int32_t n_iolets,
+                        int32_t *xyz_out, int32_t *nbr_out);
+
 /* ---- coupling (Section 2.3, Section 3) ---- */
 
 /* Add forward coupling pairs from src to dst (both in ctx, src != dst).  Each

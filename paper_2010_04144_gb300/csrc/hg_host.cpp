@@ -452,6 +452,70 @@ int ensure_scratch(hg_ctx *ctx, size_t bytes) {
     return dev_alloc(ctx, ctx->scratch, bytes);
 }
 
+// Canonical site order (ascending 3-D Morton key) and neighbour table in
+// canonical codes (Section 2.2: sparse geometry, fluid sites only): entry i-1 of
+// site s is the canonical index of the fluid site at x_s - c_i, else -(2+k) if
+// that lattice point lies in the opening of iolet k (lowest k wins), else -1.
+// nbr has 18 rows of `stride` entries (>= n; the padding is -1).  Returns HG_OK
+// or HG_ERR_ARG with the reason in `why`.
+int build_canonical(const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32_t nio, int64_t stride,
+                    std::vector<int32_t> &xyz_sorted, std::vector<int32_t> &nbr, std::string &why) {
+    std::vector<uint64_t> key(n);
+    std::vector<int64_t> idx(n);
+    std::atomic<int> bad{0};
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s) {
+            const int32_t x = xyz[3 * s], y = xyz[3 * s + 1], z = xyz[3 * s + 2];
+            if (x < 0 || y < 0 || z < 0 || x >= (1 << 21) || y >= (1 << 21) || z >= (1 << 21)) bad = 1;
+            key[s] = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
+            idx[s] = s;
+        }
+    });
+    if (bad) {
+        why = "site coordinate outside [0, 2^21)";
+        return HG_ERR_ARG;
+    }
+    sort_keys(key, idx);
+    for (int64_t s = 1; s < n; ++s)
+        if (key[s] == key[s - 1]) {
+            char buf[96];
+            snprintf(buf, sizeof buf, "duplicate site at canonical index %lld", (long long)s);
+            why = buf;
+            return HG_ERR_ARG;
+        }
+    xyz_sorted.resize(3 * n);
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s)
+            for (int c = 0; c < 3; ++c) xyz_sorted[3 * s + c] = xyz[3 * idx[s] + c];
+    });
+    std::vector<int64_t>().swap(idx);
+    BlockIndex bi;
+    bi.build(key);
+    std::vector<IoletGeom> geo(nio);
+    for (int k = 0; k < nio; ++k) {
+        geo[k].d = iolets[k];
+        geo[k].cx = iolets[k].centre[0] / 1024.0;
+        geo[k].cy = iolets[k].centre[1] / 1024.0;
+        geo[k].cz = iolets[k].centre[2] / 1024.0;
+        const double r = iolets[k].radius / 1024.0 + 3.0;
+        geo[k].reach2 = r * r + 1.0;
+    }
+    nbr.assign((size_t)18 * stride, -1);
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s) {
+            const int64_t x = xyz_sorted[3 * s], y = xyz_sorted[3 * s + 1], z = xyz_sorted[3 * s + 2];
+            for (int i = 1; i < 19; ++i) {
+                const int64_t qx = x - kC[i][0], qy = y - kC[i][1], qz = z - kC[i][2];
+                int64_t v = -1;
+                if (qx >= 0 && qy >= 0 && qz >= 0 && qx < (1 << 21) && qy < (1 << 21) && qz < (1 << 21))
+                    v = bi.find(morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz));
+                nbr[(size_t)(i - 1) * stride + s] = v >= 0 ? (int32_t)v : classify(geo, qx, qy, qz);
+            }
+        }
+    });
+    return HG_OK;
+}
+
 }  // namespace
 
 // ================================================================ C ABI
@@ -597,56 +661,14 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     d->tau = tau;
     d->io.assign(iolets, iolets + nio);
 
-    // --- canonical order
-    std::vector<uint64_t> key(n);
-    std::vector<int64_t> idx(n);
-    std::atomic<int> bad{0};
-    parallel_for(n, [&](int64_t lo, int64_t hi) {
-        for (int64_t s = lo; s < hi; ++s) {
-            const int32_t x = xyz[3 * s], y = xyz[3 * s + 1], z = xyz[3 * s + 2];
-            if (x < 0 || y < 0 || z < 0 || x >= (1 << 21) || y >= (1 << 21) || z >= (1 << 21)) bad = 1;
-            key[s] = morton3((uint32_t)x, (uint32_t)y, (uint32_t)z);
-            idx[s] = s;
-        }
-    });
-    if (bad) return fail(ctx, HG_ERR_ARG, "site coordinate outside [0, 2^21)");
-    sort_keys(key, idx);
-    for (int64_t s = 1; s < n; ++s)
-        if (key[s] == key[s - 1]) return fail(ctx, HG_ERR_ARG, "duplicate site at canonical index %lld", (long long)s);
-    d->xyz.resize(3 * n);
-    parallel_for(n, [&](int64_t lo, int64_t hi) {
-        for (int64_t s = lo; s < hi; ++s)
-            for (int c = 0; c < 3; ++c) d->xyz[3 * s + c] = xyz[3 * idx[s] + c];
-    });
-    std::vector<int64_t>().swap(idx);
-
-    // --- neighbour table (canonical codes)
-    BlockIndex bi;
-    bi.build(key);
-    std::vector<IoletGeom> geo(nio);
-    for (int k = 0; k < nio; ++k) {
-        geo[k].d = iolets[k];
-        geo[k].cx = iolets[k].centre[0] / 1024.0;
-        geo[k].cy = iolets[k].centre[1] / 1024.0;
-        geo[k].cz = iolets[k].centre[2] / 1024.0;
-        const double r = iolets[k].radius / 1024.0 + 3.0;
-        geo[k].reach2 = r * r + 1.0;
-    }
+    // --- canonical order and neighbour table (canonical codes)
     const int64_t np = d->np;
-    std::vector<int32_t> nbr((size_t)18 * np, -1);
-    parallel_for(n, [&](int64_t lo, int64_t hi) {
-        for (int64_t s = lo; s < hi; ++s) {
-            const int64_t x = d->xyz[3 * s], y = d->xyz[3 * s + 1], z = d->xyz[3 * s + 2];
-            for (int i = 1; i < 19; ++i) {
-                const int64_t qx = x - kC[i][0], qy = y - kC[i][1], qz = z - kC[i][2];
-                int64_t v = -1;
-                if (qx >= 0 && qy >= 0 && qz >= 0 && qx < (1 << 21) && qy < (1 << 21) && qz < (1 << 21))
-                    v = bi.find(morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz));
-                nbr[(size_t)(i - 1) * np + s] = v >= 0 ? (int32_t)v : classify(geo, qx, qy, qz);
-            }
-        }
-    });
-    std::vector<uint64_t>().swap(key);
+    std::vector<int32_t> nbr;
+    {
+        std::string why;
+        const int brc = build_canonical(xyz, n, iolets, nio, np, d->xyz, nbr, why);
+        if (brc != HG_OK) return fail(ctx, brc, "%s", why.c_str());
+    }
 
     // --- iolet adjacency: slots in canonical order, per-iolet CSR lists
     std::vector<int32_t> slot_of(n, -1);
@@ -955,6 +977,23 @@ int hg_set_coupling_mode(hg_ctx *ctx, int32_t mode) {
     ctx->couple_mode = mode;
     drop_plans(ctx);
     CU(ctx, refresh_domdevs(ctx));
+    return HG_OK;
+}
+
+int hg_build_neighbours(const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32_t nio, int32_t *xyz_out,
+                        int32_t *nbr_out) {
+    if (n < 0 || (n > 0 && (!xyz || !nbr_out))) return HG_ERR_ARG;
+    if (nio < 0 || nio > kMaxIolets || (nio > 0 && !iolets)) return HG_ERR_ARG;
+    for (int k = 0; k < nio; ++k)
+        if (!iolet_ok(iolets[k])) return HG_ERR_ARG;
+    std::vector<int32_t> xs, nbr;
+    std::string why;
+    const int rc = build_canonical(xyz, n, iolets, nio, n, xs, nbr, why);
+    if (rc != HG_OK) return fail(nullptr, rc, "%s", why.c_str());
+    if (n > 0) {
+        memcpy(nbr_out, nbr.data(), (size_t)18 * n * sizeof(int32_t));
+        if (xyz_out) memcpy(xyz_out, xs.data(), (size_t)3 * n * sizeof(int32_t));
+    }
     return HG_OK;
 }
 

@@ -73,6 +73,7 @@ _SIGS = {
     "hg_domain_neighbours": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_couple": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
     "hg_set_coupling_mode": ([C.c_void_p, C.c_int32], C.c_int),
+    "hg_build_neighbours": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p], C.c_int),
     "hg_coupling_factors": ([C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                              C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hg_step": ([C.c_void_p, C.c_int64], C.c_int),
@@ -160,6 +161,18 @@ class _TorchAllocator:
 
     def _free(self, ptr, nbytes, user):
         self.live.pop(int(ptr), None)
+
+
+def build_neighbours(xyz, iolets):
+    """Host-only canonical order and neighbour table (what a domain build computes):
+    returns (xyz_canonical (n, 3) int32, nbr (18, n) int32)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    n = xyz.shape[0]
+    arr = iolet_struct_array(iolets)
+    xs = np.zeros((max(1, n), 3), np.int32)
+    nbr = np.zeros((18, max(1, n)), np.int32)
+    _check(lib().hg_build_neighbours(_p(xyz), n, arr, len(iolets), _p(xs), _p(nbr)))
+    return xs[:n], nbr[:, :n]
 
 
 def hg_coupling_factors(art_centres, art_areas, ven_centres, ven_areas, uniforms):
