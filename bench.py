@@ -446,10 +446,14 @@ def run_coupled(args, H, device):
             from paper_2010_04144_gb300 import analysis as AN
 
             for name, d, g in (("arterial", da, art), ("venous", dv, ven)):
-                rows = AN.velocity_vs_area(g, d.macroscopic(), d.sites(), arterial_negative=name == "arterial")
+                fields, sites = d.macroscopic(), d.sites()
+                rows = AN.velocity_vs_area(g, fields, sites, arterial_negative=name == "arterial")
                 lvl = np.floor(np.log2(rows[:, 0] + 1)).astype(int)
                 vva[name] = [[int(L), float(np.median(rows[lvl == L, 1])), float(np.median(rows[lvl == L, 2])),
                               int((lvl == L).sum())] for L in np.unique(lvl)]
+                # the paper's own cut: planes at 1/4, 1/2, 3/4 of the domain, one row per vessel
+                planes = AN.velocity_vs_area_planes(fields, sites, arterial_negative=name == "arterial")
+                vva[name + "_planes"] = [[float(r[0]), float(r[2]), float(r[3])] for r in planes]
         devs = [abs(abs(float(bv[vk])) / abs(f * Ma[ak, 0]) - 1.0) for ak, vk, f in pairs if Ma[ak, 0]]
         bc_dev = max(devs) if devs and args.coupled_mode == "forward" else None  # alternate: may hold
         ratio = [float(abs(Mv[vk, 0]) / abs(f * Ma[ak, 0])) for ak, vk, f in pairs if Ma[ak, 0]]

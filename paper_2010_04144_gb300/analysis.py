@@ -7,8 +7,12 @@ take the macroscopic fields a domain returns (``Domain.macroscopic()``:
 * ``lattice_parameters`` / ``physical_step``: the two relations Section 3.3
   states for single-relaxation-time LB, nu = (tau - 1/2) dx^2 / (3 dt) and
   Ma = sqrt(3) v_max dt / dx (< 0.1), solved for whichever quantity is asked.
-* ``velocity_vs_area``: mean speed against vessel cross-section area, the
-  quantity Section 3.3 plots for the coupled arterial and venous trees.  The
+* ``velocity_vs_area_planes``: mean speed against vessel cross-section area, the
+  quantity Section 3.3 plots for the coupled arterial and venous trees, measured
+  as the paper describes: lattice planes at 1/4, 1/2 and 3/4 of the domain's
+  length, separated into vessels, area from the convex hull of each vessel's
+  lattice points.
+* ``velocity_vs_area``: the same quantity per tree segment.  The
   paper cuts measurement planes through the whole domain and separates them
   into vessels; a synthetic tree knows its centrelines, so each segment is cut
   by the plane through its mid-point normal to its axis.  The cross-section is
@@ -99,3 +103,88 @@ def velocity_vs_area(geo, fields, xyz, arterial_negative=False):
         area = float(sel.size)
         rows.append((n, -area if arterial_negative else area, float(speed.mean()), int(sel.size)))
     return np.array(rows, dtype=np.float64).reshape(-1, 4)
+
+
+def _plane_components(P):
+    """Connected components of lattice points P (m, 2) under 8-neighbour adjacency."""
+    m = P.shape[0]
+    parent = np.arange(m)
+
+    def find(a):
+        while parent[a] != a:
+            parent[a] = parent[parent[a]]
+            a = parent[a]
+        return a
+
+    index = {(int(x), int(y)): i for i, (x, y) in enumerate(P)}
+    for i, (x, y) in enumerate(P):
+        for dx, dy in ((1, 0), (0, 1), (1, 1), (1, -1)):
+            j = index.get((int(x) + dx, int(y) + dy))
+            if j is not None:
+                a, b = find(i), find(j)
+                if a != b:
+                    parent[max(a, b)] = min(a, b)
+    roots = np.array([find(i) for i in range(m)])
+    _, labels = np.unique(roots, return_inverse=True)
+    return labels
+
+
+def _hull_area(P):
+    """Area of the convex hull of 2-D points (0 for fewer than 3 or collinear points)."""
+    if P.shape[0] < 3:
+        return 0.0
+    pts = np.unique(P.astype(np.float64), axis=0)
+    if pts.shape[0] < 3:
+        return 0.0
+    # Andrew's monotone chain, then the shoelace formula
+    pts = pts[np.lexsort((pts[:, 1], pts[:, 0]))]
+
+    def cross(o, a, b):
+        return (a[0] - o[0]) * (b[1] - o[1]) - (a[1] - o[1]) * (b[0] - o[0])
+
+    lower, upper = [], []
+    for p in pts:
+        while len(lower) >= 2 and cross(lower[-2], lower[-1], p) <= 0:
+            lower.pop()
+        lower.append(p)
+    for p in pts[::-1]:
+        while len(upper) >= 2 and cross(upper[-2], upper[-1], p) <= 0:
+            upper.pop()
+        upper.append(p)
+    hull = np.array(lower[:-1] + upper[:-1])
+    if hull.shape[0] < 3:
+        return 0.0
+    x, y = hull[:, 0], hull[:, 1]
+    return 0.5 * abs(float(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1))))
+
+
+def velocity_vs_area_planes(fields, xyz, fractions=(0.25, 0.5, 0.75), axis=None,
+                            arterial_negative=False):
+    """Section 3.3's measurement as the paper describes it: lattice planes normal to the
+    domain's longest extent (or ``axis``) at the given fractions of its length, each cut
+    separated into vessels (8-connected groups of sites in the plane), each vessel's area
+    the convex hull of its lattice points, its speed the mean |u| over them.
+
+    Returns rows (fraction, vessel, area, mean |u|, sites); areas negative when
+    ``arterial_negative`` is set, as the paper plots the arterial vessels."""
+    X = np.asarray(xyz, np.int64)
+    fields = np.asarray(fields)
+    if axis is None:
+        axis = int(np.argmax(X.max(axis=0) - X.min(axis=0)))
+    others = [a for a in range(3) if a != axis]
+    lo, hi = int(X[:, axis].min()), int(X[:, axis].max())
+    rows = []
+    for f in fractions:
+        level = int(round(lo + f * (hi - lo)))
+        sel = np.nonzero(X[:, axis] == level)[0]
+        if sel.size == 0:
+            continue
+        P = X[sel][:, others]
+        labels = _plane_components(P)
+        for c in range(labels.max() + 1):
+            mem = sel[labels == c]
+            Pc = X[mem][:, others]
+            area = _hull_area(Pc) if mem.size >= 3 else float(mem.size)
+            speed = float(np.linalg.norm(fields[mem, 1:4].astype(np.float64), axis=1).mean())
+            rows.append((f, c, -area if arterial_negative else area, speed, int(mem.size)))
+    return np.array(rows, dtype=np.float64).reshape(-1, 5)

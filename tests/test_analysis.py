@@ -60,3 +60,35 @@ def test_mean_speed_of_steady_tube_is_half_the_peak(oracle_mod):
     assert abs(speed - expect) / expect < 0.04
     neg = A.velocity_vs_area(geo, d.moments(), d.xyz, arterial_negative=True)
     assert neg[0, 1] == -area
+
+
+def test_hull_area_matches_a_library_hull():
+    from scipy.spatial import ConvexHull
+
+    rng = np.random.default_rng(5)
+    for _ in range(20):
+        P = rng.integers(-20, 20, size=(rng.integers(3, 60), 2))
+        if np.linalg.matrix_rank(P - P[0]) < 2:
+            continue
+        assert abs(A._hull_area(P) - ConvexHull(P.astype(float)).volume) < 1e-9
+    assert A._hull_area(np.array([[0, 0], [1, 1], [2, 2]])) == 0.0     # collinear
+
+
+def test_plane_cuts_separate_vessels():
+    g = S.parallel_tubes(3, radius=5, length=30)
+    fields = np.zeros((g.n, 4))
+    fields[:, 3] = 0.25
+    rows = A.velocity_vs_area_planes(fields, g.xyz, axis=2)
+    assert rows.shape[0] == 9                                  # 3 planes x 3 tubes
+    x, y = np.meshgrid(np.arange(-5, 6), np.arange(-5, 6))
+    disc = np.stack([x.ravel(), y.ravel()], 1)[(x ** 2 + y ** 2).ravel() <= 25]
+    assert np.allclose(rows[:, 2], A._hull_area(disc))         # each cut: one lattice disc
+    assert np.allclose(rows[:, 3], 0.25) and np.all(rows[:, 4] == disc.shape[0])
+    neg = A.velocity_vs_area_planes(fields, g.xyz, axis=2, arterial_negative=True)
+    assert np.allclose(neg[:, 2], -rows[:, 2])
+    t = S.tree(S.TreeSpec(depth=4, root_radius=5, seed=7))
+    rt = A.velocity_vs_area_planes(np.ones((t.n, 4)), t.xyz)
+    ax = int(np.argmax(t.xyz.max(0) - t.xyz.min(0)))
+    for f in (0.25, 0.5, 0.75):
+        level = int(round(t.xyz[:, ax].min() + f * (t.xyz[:, ax].max() - t.xyz[:, ax].min())))
+        assert rt[rt[:, 0] == f, 4].sum() == np.sum(t.xyz[:, ax] == level)   # every site in a vessel
