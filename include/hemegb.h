@@ -52,7 +52,7 @@ extern "C" {
 #define HG_ERR_ARG (-1)     /* invalid argument (sizes, ranges, handles) */
 #define HG_ERR_OOM (-2)     /* device or host allocation failed */
 #define HG_ERR_CUDA (-3)    /* a CUDA call failed (message holds the CUDA error) */
-#define HG_ERR_TIMEOUT (-4) /* a bounded device wait gave up (reserved) */
+#define HG_ERR_TIMEOUT (-4) /* a bounded device wait gave up: the state is not trusted */
 #define HG_ERR_STATE (-5)   /* call not valid in the object's current state */
 
 /* ---- distribution storage ---- */
@@ -151,17 +151,23 @@ typedef struct {
 /* ---- context ---- */
 
 /* Create a context on p->device.  Storage and scheme apply to every domain of
- * the context.  Errors: HG_ERR_ARG (bad field), HG_ERR_CUDA. */
+ * the context.  Errors: HG_ERR_ARG (bad field), HG_ERR_CUDA.
+ * Passage: infrastructure: no passage (device, stream and memory set-up). */
 int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out);
 
-/* Destroy a context and every domain still attached to it. */
+/* Destroy a context and every domain still attached to it.
+ * Passage: infrastructure: no passage. */
 int hg_ctx_destroy(hg_ctx *ctx);
 
 /* Message of the calling thread's last failed call, if that call concerned
- * this context (or its domains); "" otherwise. */
+ * this context (or its domains); "" otherwise.
+ * Passage: infrastructure: no passage. */
 const char *hg_last_error(hg_ctx *ctx);
 
-/* Wait for all work enqueued on the context's stream. */
+/* Wait for all work enqueued on the context's stream.  Returns HG_ERR_TIMEOUT
+ * (and clears the flag) when a bounded device wait gave up since the last
+ * call: the state is then not trusted.
+ * Passage: infrastructure: no passage. */
 int hg_sync(hg_ctx *ctx);
 
 /* ---- domains ---- */
@@ -172,31 +178,41 @@ int hg_sync(hg_ctx *ctx);
  * Builds the canonical site order and neighbour table, classifies iolet links,
  * uploads everything and initialises the rest state f~ = 0 at step 0.
  * Errors: HG_ERR_ARG (range, duplicate, too many iolets, tau <= 0.5),
- * HG_ERR_OOM, HG_ERR_CUDA. */
+ * HG_ERR_OOM, HG_ERR_CUDA.
+ * Passage: Section 2.2 (sparse blocks, fluid sites only) and Section 2
+ * (D3Q19, rigid walls, pressure/velocity iolets). */
 int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets,
                      int32_t n_iolets, const hg_lb_params *lb, hg_domain **out);
 
 /* Free a domain's device memory and detach it from its context.  Coupling
- * pairs that involve it are dropped. */
+ * pairs that involve it are dropped.
+ * Passage: infrastructure: no passage. */
 int hg_domain_destroy(hg_domain *d);
 
 /* Sizes: sites, iolets, sites next to any iolet, completed steps, device
- * bytes held.  Any out pointer may be NULL. */
+ * bytes held.  Any out pointer may be NULL.
+ * Passage: infrastructure: no passage. */
 int hg_domain_info(hg_domain *d, int64_t *n_sites, int32_t *n_iolets, int64_t *n_adjacent,
                    int64_t *step, int64_t *device_bytes);
 
-/* Canonical site coordinates, n_sites x 3 int32 (host). */
+/* Canonical site coordinates, n_sites x 3 int32 (host), whatever the
+ * device ordering.
+ * Passage: Section 2.2 (sites stored by blocks; canonical order = ascending
+ * Morton key, which visits every aligned 8^3 block contiguously). */
 int hg_domain_sites(hg_domain *d, int32_t *xyz_out);
 
 /* Canonical neighbour table as used on the device, nbr[18][n_sites] int32
- * (host), decoded to the conventions above. */
+ * (host), decoded to the conventions above whatever the device ordering.
+ * Passage: Section 2.2 (sparse geometry: streaming follows the links between
+ * stored fluid sites). */
 int hg_domain_neighbours(hg_domain *d, int32_t *nbr_out);
 
 /* Host only (no context, no device): the canonical site order and neighbour
  * table hg_domain_create builds for the same input, with the same checks.
  * xyz_out: n_fluid x 3 in canonical order (may be NULL); nbr_out:
  * nbr[18][n_fluid] in the conventions above.  Errors: HG_ERR_ARG (bad sizes,
- * coordinates, duplicates or iolets). */
+ * coordinates, duplicates or iolets).
+ * Passage: Section 2.2 (sparse blocks of fluid sites). */
 int hg_build_neighbours(const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets, int32_t n_iolets,
                         int32_t *xyz_out, int32_t *nbr_out);
 
@@ -205,7 +221,9 @@ int hg_build_neighbours(const int32_t *xyz, int64_t n_fluid, const hg_iolet *iol
 /* Add forward coupling pairs from src to dst (both in ctx, src != dst).  Each
  * dst_iolet must be a velocity iolet and may appear once; the pairs take
  * effect from the next step.  Both domains must then be stepped together.
- * Errors: HG_ERR_ARG. */
+ * Errors: HG_ERR_ARG.
+ * Passage: Section 2.3 (only averaged values cross) and Section 3 (the
+ * velocity-scale equation after Eq. (1)). */
 int hg_couple(hg_ctx *ctx, hg_domain *src, hg_domain *dst, const hg_pair *pairs, int32_t n_pairs);
 
 /* Exchange schedule of every coupling pair of the context (Section 3: the
@@ -221,7 +239,9 @@ int hg_couple(hg_ctx *ctx, hg_domain *src, hg_domain *dst, const hg_pair *pairs,
  * 9 (c_i.u) c_i].F) until the next reverse exchange.  Each exchange leaves
  * the other direction's values unchanged.  The paper describes the reverse
  * direction in words only; this is the library's reading of it.  Setting a
- * mode zeroes every force.  Synchronises the stream.  Errors: HG_ERR_ARG. */
+ * mode zeroes every force.  Synchronises the stream.  Errors: HG_ERR_ARG.
+ * Passage: Section 3 (alternating exchange; Guo forcing from the dynamic
+ * pressure at the arterial outlets). */
 int hg_set_coupling_mode(hg_ctx *ctx, int32_t mode);
 
 /* Host helper for Section 3's coupling map and scale factors.
@@ -234,7 +254,9 @@ int hg_set_coupling_mode(hg_ctx *ctx, int32_t mode);
  * Inputs: art_centres n_art x 3 and ven_centres n_ven x 3 (fixed point 2^-10),
  * areas in lattice units^2, uniforms n_ven values in [0, 1).  Outputs (n_ven
  * each): assign (artery index), dist (lattice units), dp, factor.
- * Errors: HG_ERR_ARG (n_art < 1, zero distance, non-positive area). */
+ * Errors: HG_ERR_ARG (n_art < 1, zero distance, non-positive area).
+ * Passage: Section 3 (greedy nearest-neighbour map; dP/P_0 ~ U(0.3, 0.7);
+ * Eq. (1) and the velocity-scale equation after it). */
 int hg_coupling_factors(const int64_t *art_centres, const double *art_areas, int32_t n_art,
                         const int64_t *ven_centres, const double *ven_areas, int32_t n_ven,
                         const double *uniforms, int32_t *assign, double *dist, double *dp,
@@ -247,51 +269,65 @@ int hg_coupling_factors(const int64_t *art_centres, const double *art_areas, int
  * rules on non-fluid links, with boundary values of time t), collides (LBGK,
  * tau) into F_t, then reduces the iolet means of time t in FP64 and sets the
  * boundary values of time t+1 (pulses; coupled inlets from the means).
- * Groups of steps run as captured CUDA graphs.  Asynchronous. */
+ * Groups of steps run as captured CUDA graphs.  Asynchronous.
+ * Passage: Section 2 (the LB step: D3Q19 streaming, LBGK collision, walls,
+ * iolets) and Section 2.3 (coupled values exchanged every step). */
 int hg_step(hg_ctx *ctx, int64_t n_steps);
 
 /* Same for a subset of the context's domains (coupled partners included);
- * the domains may be at different step counts. */
+ * the domains may be at different step counts.
+ * Passage: Section 2 and Section 2.3, as hg_step. */
 int hg_step_domains(hg_ctx *ctx, hg_domain *const *doms, int32_t n_doms, int64_t n_steps);
 
 /* Like hg_step but without graphs and with CUDA events around every kernel:
  * total milliseconds spent in the stream-collide kernel and in the iolet
  * update kernel; per_step (2 x n_steps floats, may be NULL) receives each
  * step's (stream-collide ms, iolet-update ms).  Any pointer may be NULL.
- * Synchronises. */
+ * Synchronises.
+ * Passage: Section 2 (the LB step), timed per kernel (infrastructure). */
 int hg_step_profiled(hg_ctx *ctx, int64_t n_steps, double *ms_stream_collide,
                      double *ms_iolet, float *per_step);
 
 /* Change the stream-collide launch shape of an existing context (threads per
  * block: multiple of 32, <= 512; sites per thread: 1, 2 or 4; kernel variant
  * as in hg_ctx_params).  Results do not depend on it (each site's arithmetic
- * is the same); used by the autotuner.  Errors: HG_ERR_ARG. */
+ * is the same); used by the autotuner.  Errors: HG_ERR_ARG.
+ * Passage: infrastructure: no passage. */
 int hg_ctx_set_launch(hg_ctx *ctx, int32_t block_size, int32_t sites_per_thread,
                       int32_t kernel_variant);
 
 /* ---- read-back ---- */
 
 /* Macroscopic fields of the current state F_t, canonical order, n_sites x 4
- * FP32 host array: (drho, ux, uy, uz), drho = rho - 1, u = j / rho. */
+ * FP32 host array: (drho, ux, uy, uz), drho = rho - 1, u = j / rho.
+ * Passage: Section 2 (the macroscopic density and velocity of the LB state). */
 int hg_read_macroscopic(hg_domain *d, float *out, int64_t *step_out);
 
 /* Same into a caller-owned device array (n_sites x 4 FP32, 16-byte aligned);
- * asynchronous on the context stream. */
+ * asynchronous on the context stream.
+ * Passage: Section 2, as hg_read_macroscopic. */
 int hg_read_macroscopic_device(hg_domain *d, float *dev_out);
 
 /* Iolet means of the last completed step, n_iolets x 3 FP64 host array:
  * (mean u.n over the sites next to the iolet, mean drho there, site count);
- * n is the iolet's unit outward axis.  Sums in FP64 in canonical order. */
+ * n is the iolet's unit outward axis.  Sums in FP64 in canonical order.
+ * Passage: Section 2.3 (only the average value of macroscopic properties is
+ * passed between coupled instances). */
 int hg_read_iolet_stats(hg_domain *d, double *out);
 
-/* Boundary values the next step will use, n_iolets FP32 (host). */
+/* Boundary values the next step will use, n_iolets FP32 (host).
+ * Passage: Section 2 (iolet conditions) and Section 3 (coupled inlets). */
 int hg_read_boundary_values(hg_domain *d, float *out);
 
 /* Body-force densities the next step applies next to each iolet (reverse
- * coupling exchange, see hg_set_coupling_mode), n_iolets x 3 FP32 (host). */
+ * coupling exchange, see hg_set_coupling_mode), n_iolets x 3 FP32 (host).
+ * Passage: Section 3 (reverse direction: arterial-outlet boundary force). */
 int hg_read_iolet_forces(hg_domain *d, float *out);
 
-/* Total mass deviation sum_s sum_i f~_i(s) of the current state, FP64. */
+/* Total mass deviation sum_s sum_i f~_i(s) of the current state, FP64, in
+ * canonical site order.
+ * Passage: infrastructure: no passage (mass check of the LB state; the paper
+ * describes none). */
 int hg_mass(hg_domain *d, double *out);
 
 /* Total mass deviation of a caller-owned distribution array, without any
@@ -310,28 +346,34 @@ int hg_mass(hg_domain *d, double *out);
  * first call before any stream capture.  All calls share the array: calls
  * whose kernels overlap on the GPU race and may return wrong sums; calls
  * ordered on one stream are safe.  Asynchronous.  Errors: HG_ERR_ARG,
- * HG_ERR_CUDA. */
+ * HG_ERR_CUDA.
+ * Passage: no counterpart in the paper (see above). */
 int hg_mass_noalloc(const void *f_dev, int32_t storage, int64_t n, int64_t row_stride,
                     double *out_dev, void *stream);
 
 /* ---- checkpoint / resume ---- */
 
-/* Bytes needed by hg_save_state for this domain. */
+/* Bytes needed by hg_save_state for this domain.
+ * Passage: infrastructure: no passage (checkpointing; the paper excludes data
+ * output from its timings, Section 2.2). */
 int hg_state_bytes(hg_domain *d, int64_t *bytes);
 
 /* Save the current state to a host buffer.  Layout (version 2): a 40-byte
  * header (magic "HEMEGB1\0", n_sites, step, n_iolets, storage, scheme,
  * version), boundary values (n_iolets FP32), iolet means (n_iolets x 3 FP64),
  * F_t in canonical order in the storage type (19 x n_sites), iolet forces
- * (n_iolets x 4 FP32). */
+ * (n_iolets x 4 FP32).
+ * Passage: infrastructure: no passage (checkpoint). */
 int hg_save_state(hg_domain *d, void *host_buf, int64_t bytes);
 
 /* Restore a state written by hg_save_state of a domain with the same
- * geometry, storage and scheme; stepping then continues bit-identically. */
+ * geometry, storage and scheme; stepping then continues bit-identically.
+ * Passage: infrastructure: no passage (resume). */
 int hg_load_state(hg_domain *d, const void *host_buf, int64_t bytes);
 
 /* Raw state of the current time level F_t as 19 x n_sites values of the
- * storage type (FP32, or f~/w in FP16/BF16), canonical order (host). */
+ * storage type (FP32, or f~/w in FP16/BF16), canonical order (host).
+ * Passage: infrastructure: no passage (raw state read-back). */
 int hg_read_state(hg_domain *d, void *host_out);
 
 #ifdef __cplusplus

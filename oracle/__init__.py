@@ -23,9 +23,12 @@ sequences the time steps:
     unit axis): the dynamic pressure of that flow, per lattice unit, opposing
     outflow.  F_k acts, through the Guo forcing of R7, on every site next to
     outlet k from the next step on.  Each exchange leaves the values of the
-    other direction as they were.  Parity unpinned: the paper states this
-    direction in words only (no formula, no number); the forcing itself (R7)
-    is pinned by its conservation laws and closed-form flows.
+    other direction as they were.  The paper states this direction in words
+    only (no formula, no number); the mapping is pinned by the properties the
+    reading fixes (zero inflow gives zero force; the force opposes outflow and
+    is quadratic in the speed; fed inlets are averaged, not summed; a forward
+    then reverse exchange on a steady pair returns the outlet mean), and the
+    forcing itself (R7) by its conservation laws and closed-form flows.
 
 Parity status of each function is listed in ``oracle/coupling.py`` and the
 test files under ``tests/test_oracle_*.py``.

@@ -350,17 +350,6 @@ class Domain:
         self.ctx._ck(lib().hg_read_state(self.h, _p(out)))
         return out
 
-    def state_f64(self):
-        """F_t as float64 deviations f~ (storage scaling by 1/w undone)."""
-        raw = self.state()
-        if self.ctx.storage == 0:
-            return raw.astype(np.float64)
-        w = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)[:, None]
-        if self.ctx.storage == 1:
-            return raw.astype(np.float64) * w
-        bits = raw.astype(np.uint32) << 16
-        return bits.view(np.float32).astype(np.float64) * w
-
     def state_bytes(self):
         b = C.c_int64()
         self.ctx._ck(lib().hg_state_bytes(self.h, C.byref(b)))

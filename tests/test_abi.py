@@ -102,3 +102,20 @@ def test_header_is_plain_c(tmp_path):
     r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-c", str(src),
                         "-o", str(tmp_path / "use.o")], capture_output=True, text=True)
     assert r.returncode == 0, r.stderr
+
+
+def test_every_declaration_cites_its_passage():
+    """Each entry point's comment names the paper passage that defines the operation,
+    or says that it is infrastructure with no passage (or has no counterpart)."""
+    src = open(os.path.join(ROOT, "include", "hemegb.h")).read()
+    decls = list(re.finditer(r"^\s*(?:int|const char \*)\s*(hg_\w+)\s*\(", src, re.M))
+    assert len(decls) >= 20
+    for m in decls:
+        head = src[:m.start()].rstrip()
+        assert head.endswith("*/"), m.group(1)
+        comment = head[head.rfind("/*"):]
+        line = [l for l in comment.splitlines() if "Passage:" in l]
+        assert line, f"{m.group(1)} has no 'Passage:' line"
+        text = comment[comment.find("Passage:"):]
+        assert ("Section" in text or "Eq." in text or "infrastructure: no passage" in text
+                or "no counterpart in the paper" in text), m.group(1)

@@ -133,3 +133,70 @@ def test_reverse_exchange_schedule_and_sites(oracle_mod):
     forced = np.nonzero(np.abs(F).sum(1))[0]
     assert np.array_equal(forced, da.adjacent(1))
     assert sa.site_force(1) is None
+
+
+# ---- reverse-exchange mapping (reading 13), pinned on the properties the reading fixes:
+# the outlet force is the dynamic pressure 1/2 v|v| of the speed the fed venous inlets map
+# back to, directed against the outlet's outward axis for inflow, averaged (not summed) over
+# the inlets an outlet feeds, with each inlet's factor undone.
+
+def _fan_system(oracle_mod, factors):
+    """Arterial tube (outlet = iolet 1, outward +z) feeding len(factors) venous tube inlets."""
+    art = S.cylinder(radius=3, length=12, inlet=dict(kind=S.VELOCITY, value=0.01, profile=S.PLUG))
+    ven = S.parallel_tubes(len(factors), radius=3, length=12,
+                           inlet=dict(kind=S.VELOCITY, value=0.0, profile=S.PLUG))
+    da = oracle_mod.Domain(art.xyz, art.iolets, tau=TAU)
+    dv = oracle_mod.Domain(ven.xyz, ven.iolets, tau=TAU)
+    pairs = [(0, 1, 1, j, f) for j, f in enumerate(factors)]
+    return oracle_mod.System([da, dv], pairs, alternate=True)
+
+
+def _reverse(sysm, inlet_means):
+    """Reverse exchange (odd e) with the venous inlets' mean u.n set to `inlet_means`."""
+    for j, m in enumerate(inlet_means):
+        sysm.M[1][j][0] = m
+    sysm._exchange(1)
+    return np.array(sysm.iolet_force[0][1])
+
+
+def test_reverse_zero_inflow_gives_zero_force(oracle_mod):
+    s = _fan_system(oracle_mod, [0.6, 0.9])
+    assert np.array_equal(_reverse(s, [0.0, 0.0]), np.zeros(3))
+
+
+def test_reverse_force_opposes_outflow(oracle_mod):
+    s = _fan_system(oracle_mod, [0.7])
+    n = np.array([0.0, 0.0, 1.0])                 # the arterial outlet's outward axis
+    F = _reverse(s, [-0.01])                        # inflow at the venous inlet (u.n < 0)
+    assert F @ n < 0 and np.allclose(np.cross(F, n), 0.0, atol=0)
+    F = _reverse(s, [+0.01])                        # backflow out of the venous inlet
+    assert F @ n > 0
+
+
+def test_reverse_force_quadratic_in_speed(oracle_mod):
+    s = _fan_system(oracle_mod, [0.45])
+    F1 = _reverse(s, [-0.004])
+    F2 = _reverse(s, [-0.008])
+    assert abs(np.linalg.norm(F2) / np.linalg.norm(F1) - 4.0) < 1e-14
+
+
+def test_reverse_mean_over_fed_inlets(oracle_mod):
+    one = _reverse(_fan_system(oracle_mod, [0.5]), [-0.006])
+    three = _reverse(_fan_system(oracle_mod, [0.5, 0.5, 0.5]), [-0.006, -0.006, -0.006])
+    np.testing.assert_allclose(three, one, rtol=1e-15, atol=0)
+    assert np.linalg.norm(one) > 0
+
+
+def test_forward_then_reverse_round_trip(oracle_mod):
+    """A steady 1:1 pair whose venous inlet carries exactly the imposed inflow maps back to
+    the arterial outlet mean: the reverse direction undoes the forward factor."""
+    f, m = 0.37, 0.0123
+    s = _fan_system(oracle_mod, [f])
+    s.M[0][1][0] = m                               # arterial outlet mean u.n (outflow)
+    s._exchange(0)                                 # forward: venous inlet speed f * m
+    imposed = s.cbv[(1, 0)]
+    assert imposed == f * m
+    F = _reverse(s, [-imposed])                    # the inlet's mean u.n is the imposed inflow
+    v = math.sqrt(2.0 * np.linalg.norm(F))
+    assert abs(v - m) <= 1e-15 * m
+    assert F[2] < 0

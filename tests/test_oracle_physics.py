@@ -7,9 +7,15 @@ fixes, not against itself:
     conserves mass, bounce-back walls return every population);
   * Poiseuille: steady tube flow driven by a density difference matches the
     analytic parabola u = G (R^2 - r^2) / (4 nu), G = drho / (3 L),
-    nu = (tau - 1/2) / 3 (the viscosity relation quoted in Section 3.3);
+    nu = (tau - 1/2) / 3 (the viscosity relation quoted in Section 3.3), to 3%
+    on a tube of radius 12, and the error shrinks as the radius grows.  R is
+    the radius of the staircase cross-section's area: half-way bounce-back on a
+    voxelised circle is a first-order wall, and at radius 8 no parabola of any
+    radius fits the exact LBGK profile better than 3.3%, so 3% against the
+    nominal radius is out of reach of a correct solver at that size;
   * Womersley: oscillating pressure drop, complex velocity amplitude against
-    the Bessel-function solution;
+    the Bessel-function solution, to 5% at radius 12 with alpha = 2;
+  * pulse: the (1 - cos) and sine waveforms at the quarter periods;
   * velocity inlet: steady mass flux through every interior plane equals the
     mass the moving-wall rule injects, sum over inlet links of 6 w_i c_i.u_w;
   * axis symmetry: the same tube along x and along z gives the same fields.
@@ -48,7 +54,7 @@ def test_mass_conserved_closed_box(oracle_mod):
     assert not np.all(d.F == 0.0)
 
 
-def _poiseuille(oracle_mod, R=8, L=64, drho=0.001, steps=2000):
+def _poiseuille(oracle_mod, R=12, L=96, drho=0.001, steps=2000):
     geo = S.cylinder(radius=R, length=L, inlet=dict(kind=S.PRESSURE, value=drho))
     d = oracle_mod.Domain(geo.xyz, geo.iolets, tau=TAU)
     s = oracle_mod.System([d])
@@ -61,29 +67,46 @@ def poiseuille(oracle_mod):
     return _poiseuille(oracle_mod)
 
 
-def test_poiseuille_profile(poiseuille):
-    geo, d, m = poiseuille
+def _poiseuille_errors(geo, d, m):
+    """(relative L2 against the analytic profile with the staircase cross-section's area
+    radius, fitted R_eff, fitted gradient) over the middle half of the tube."""
     R, L, c, mg = geo.meta["radius"], geo.meta["length"], geo.meta["centre"], geo.meta["margin"]
     z = d.xyz[:, 2]
     mid = (z >= mg + L // 4) & (z < mg + 3 * L // 4)
     r2 = ((d.xyz[mid, 0] - c) ** 2 + (d.xyz[mid, 1] - c) ** 2).astype(np.float64)
     uz = m[mid, 3]
     G = 0.001 / (3.0 * L)
-    # fitted parabola u = a - b r^2: b = G / (4 nu), R_eff^2 = a / b
+    R_area = math.sqrt(int(np.sum(z == mg)) / math.pi)
+    ua = G * (R_area ** 2 - r2) / (4 * NU)
     A = np.stack([np.ones_like(r2), -r2], 1)
     a, b = np.linalg.lstsq(A, uz, rcond=None)[0]
-    G_fit = 4 * NU * b
-    R_eff = math.sqrt(a / b)
+    return np.linalg.norm(uz - ua) / np.linalg.norm(ua), math.sqrt(a / b), 4 * NU * b, mid
+
+
+def test_poiseuille_profile(poiseuille):
+    """Steady flow in the R = 12 tube: the analytic parabola u = G (R^2 - r^2) / (4 nu),
+    G = drho / (3 L), within 3% relative L2, R taken as the radius of the staircase
+    cross-section's area (the lattice disc of radius 12 holds 441 sites, R_area = 11.85);
+    the fitted radius within 1 of R and the fitted gradient within 3% of G."""
+    geo, d, m = poiseuille
+    R, L = geo.meta["radius"], geo.meta["length"]
+    err, R_eff, G_fit, mid = _poiseuille_errors(geo, d, m)
+    G = 0.001 / (3.0 * L)
+    assert err < 0.03, err
+    assert abs(R_eff - R) < 1.0
     assert abs(G_fit - G) / G < 0.03
-    assert abs(R_eff - R) < 0.5
-    # analytic profile with the radius of the staircase cross-section's area
-    n_cross = int(np.sum(z == mg))
-    R_area = math.sqrt(n_cross / math.pi)
-    ua = G * (R_area ** 2 - r2) / (4 * NU)
-    assert np.linalg.norm(uz - ua) / np.linalg.norm(ua) < 0.06
     # no transverse flow, positive axial flow everywhere
+    uz = m[mid, 3]
     assert np.max(np.abs(m[mid, 1:3])) < 1e-3 * np.max(uz)
     assert np.all(uz > 0)
+
+
+def test_poiseuille_converges_with_radius(oracle_mod, poiseuille):
+    """The staircase wall's error falls as the tube is resolved more finely: a dropped
+    term or a wrong viscosity would leave an error that does not shrink with R."""
+    e12 = _poiseuille_errors(*poiseuille)[0]
+    e8 = _poiseuille_errors(*_poiseuille(oracle_mod, R=8, L=64, steps=1500))[0]
+    assert e12 < 0.5 * e8, (e8, e12)
 
 
 def test_poiseuille_pressure_drop(poiseuille):
@@ -109,41 +132,44 @@ def _j0(zz, terms=60):
 
 
 def test_womersley(oracle_mod):
-    """Complex velocity amplitude over the last period vs the Womersley solution.
+    """Complex velocity amplitude over the last period vs the Womersley solution,
+    within 5% relative L2 (R = 12 tube, period 2250 steps: alpha = R sqrt(omega/nu) = 2.0;
+    the staircase radius as in the Poiseuille pin).
 
     The driving gradient amplitude is measured between two planes around the
     central cross-section, so the test does not depend on the acoustic
     response of the short tube.
     """
-    T = 1000.0
-    geo = S.cylinder(inlet=dict(kind=S.PRESSURE, value=0.001, pulse=S.PULSE_SINE, period=T))
+    T, R0, L0 = 2250.0, 12, 96
+    geo = S.cylinder(radius=R0, length=L0,
+                     inlet=dict(kind=S.PRESSURE, value=0.001, pulse=S.PULSE_SINE, period=T))
     d = oracle_mod.Domain(geo.xyz, geo.iolets, tau=TAU)
     s = oracle_mod.System([d])
     c, mg, R = geo.meta["centre"], geo.meta["margin"], geo.meta["radius"]
     z = d.xyz[:, 2]
-    zc = mg + 32
+    zc = mg + L0 // 2
     sec = z == zc
     r = np.sqrt((d.xyz[sec, 0] - c) ** 2 + (d.xyz[sec, 1] - c) ** 2)
-    p1, p2 = z == zc - 8, z == zc + 8
+    p1, p2 = z == zc - L0 // 8, z == zc + L0 // 8
     w = 2 * math.pi / T
     acc = {"U": np.zeros(int(sec.sum()), complex), "G": 0j}
 
     def cb(st):
-        if st.t > 3 * T:
+        if st.t > 2 * T:
             e = np.exp(-1j * w * st.t) * 2 / T
-            acc["G"] += (d.mom[p1, 0].mean() - d.mom[p2, 0].mean()) / 3.0 / 16.0 * e
+            acc["G"] += (d.mom[p1, 0].mean() - d.mom[p2, 0].mean()) / 3.0 / (2 * (L0 // 8)) * e
             acc["U"] += d.mom[sec, 3] * e
 
-    s.step(int(4 * T), cb)
+    s.step(int(3 * T), cb)
     Gh, U = acc["G"], acc["U"]
     # the measured gradient oscillates with the imposed amplitude drho / (3 L), to within 10%
-    assert abs(abs(Gh) - 0.001 / (3 * 64)) / (0.001 / (3 * 64)) < 0.1
+    assert abs(abs(Gh) - 0.001 / (3 * L0)) / (0.001 / (3 * L0)) < 0.1
     R_area = math.sqrt(sec.sum() / math.pi)
     alpha = R_area * math.sqrt(w / NU)
     assert 1.9 < alpha < 2.1
     k = (1j) ** 1.5 * alpha
     Ua = (Gh / (1j * w)) * (1 - np.array([_j0(k * ri / R_area) for ri in r]) / _j0(k))
-    assert np.linalg.norm(U - Ua) / np.linalg.norm(Ua) < 0.08
+    assert np.linalg.norm(U - Ua) / np.linalg.norm(Ua) < 0.05
     # the centreline lags the gradient by more than the quasi-steady (zero) phase
     lag = np.angle(Gh) - np.angle(U[np.argmin(r)])
     lag_a = np.angle(Gh) - np.angle(Ua[np.argmin(r)])
@@ -203,3 +229,21 @@ def test_axis_symmetry(oracle_mod):
     np.testing.assert_allclose(mx[:, 2], mz[idx, 2], rtol=1e-9, atol=1e-15)
     np.testing.assert_allclose(mx[:, 3], mz[idx, 1], rtol=1e-9, atol=1e-15)
     assert np.max(np.abs(mx[:, 1])) > 1e-5
+
+
+def test_pulse_waveforms(oracle_mod):
+    """Inlet time modulation: the (1 - cos)/2 pulse starts from rest, peaks at 1 at half
+    period and is symmetric about it; the sine pulse takes 0, 1, 0, -1 at quarter periods;
+    both are periodic."""
+    o, T = oracle_mod, 1000.0
+    cos = [o.pulse(o.PULSE_COSINE, t, T) for t in (0, 250, 500, 750, 1000)]
+    np.testing.assert_allclose(cos, [0.0, 0.5, 1.0, 0.5, 0.0], atol=1e-15)
+    sin = [o.pulse(o.PULSE_SINE, t, T) for t in (0, 250, 500, 750)]
+    np.testing.assert_allclose(sin, [0.0, 1.0, 0.0, -1.0], atol=1e-15)
+    for t in (1, 37, 333, 601):
+        assert abs(o.pulse(o.PULSE_COSINE, t, T) - o.pulse(o.PULSE_COSINE, T - t, T)) < 1e-15
+        assert abs(o.pulse(o.PULSE_COSINE, t, T) - o.pulse(o.PULSE_COSINE, t + 3 * T, T)) < 1e-12
+        assert 0.0 <= o.pulse(o.PULSE_COSINE, t, T) <= 1.0
+    # the mean over a period is half the peak
+    assert abs(np.mean([o.pulse(o.PULSE_COSINE, t, T) for t in range(1000)]) - 0.5) < 1e-12
+    assert o.pulse(o.PULSE_CONST, 123, T) == 1.0
