@@ -14,6 +14,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -28,6 +29,11 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 PEAKS_PATH = os.path.join(ROOT, "MEASURED_PEAKS.json")
+# one metric string for both arms, so the two lines are directly comparable
+METRIC = "MFLUPS (D3Q19 LBGK site updates per second / 1e6), whole hot path per step"
+# each variant's K-step measurement is repeated until this much device time has passed
+# (nvidia-smi samples every 100 ms), and the median repetition is reported
+MIN_TIMED_S = 1.0
 FALLBACK_HBM_GBS = 6800.0
 
 # algorithmic bytes per site update of the stream-collide kernel
@@ -213,19 +219,29 @@ def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, 
             ctx.set_launch(*launch)
             best, timing = tuple(launch), {}
         nvtx.range_pop()
-        # warm-up, then the timed region: exactly `steps` steps, barrier + sync on both sides
+        # warm-up, then the timed regions: exactly `steps` steps each, barrier + sync on both
+        # sides, repeated until MIN_TIMED_S of device time has passed; the median is reported
         ctx.step(warmup)
-        barrier(dist)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        sampler.mark(True)
+        reps, total, n_rep = [], 0.0, 1
         nvtx.range_push(f"{tag}-timed")
-        e0.record(st)
-        ctx.step(steps)
-        e1.record(st)
-        barrier(dist)
+        while len(reps) < n_rep:
+            barrier(dist)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            sampler.mark(True)
+            e0.record(st)
+            ctx.step(steps)
+            e1.record(st)
+            barrier(dist)
+            sampler.mark(False)
+            x = e0.elapsed_time(e1)
+            reps.append(x)
+            total += x
+            if len(reps) == 1:  # the repetition count follows from the first measurement,
+                # the same on every rank (slowest rank's count)
+                n_rep = int(max_over_ranks(float(max(3, min(20000, math.ceil(MIN_TIMED_S * 1e3 / x)))),
+                                           dist, device))
         nvtx.range_pop()
-        sampler.mark(False)
-        ms = max_over_ranks(e0.elapsed_time(e1), dist, device)
+        ms = max_over_ranks(statistics.median(reps), dist, device)
         # per-kernel durations (CUDA events on the context stream around every launch)
         nvtx.range_push(f"{tag}-profiled")
         ms_sc, ms_io = ctx.step_profiled(steps)
@@ -248,7 +264,8 @@ def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, 
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device)
         gs = 16
         launches = steps * (1 + (1 if geo.iolets else 0)) + (steps + gs - 1) // gs
-        return dict(n=n, ms=ms, ms_sc=ms_sc, ms_io=ms_io, e2e_s=e2e_s, h2d=int(state.size),
+        return dict(n=n, ms=ms, reps=len(reps), timed_s=total / 1e3, ms_sc=ms_sc, ms_io=ms_io,
+                    e2e_s=e2e_s, h2d=int(state.size),
                     d2h=int(n * 16), launches=launches, device_bytes=d.info()["device_bytes"],
                     launch={"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]},
                     tuning_ms={f"{b}x{t}v{v}": round(x, 4) for (b, t, v), x in timing.items()})
@@ -305,7 +322,7 @@ def run_reference(args):
     dt = time.perf_counter() - t0
     v = od.n * args.steps / dt / 1e6
     cfg["steps_per_job"] = args.steps
-    line = {"impl": "reference", "metric": "MFLUPS (D3Q19 LBGK site updates per second / 1e6)",
+    line = {"impl": "reference", "metric": METRIC,
             "value": v, "unit": "MFLUPS", "n_gpus": 0, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dt / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic (seeded tree)", "config": cfg,
@@ -643,12 +660,14 @@ def main():
     e2e_value = total_sites * args.steps / h["e2e_s"] / 1e6
     traffic, scaled_from = profiled_traffic(f"{head[0]}:{head[1]}", h["launch"])
     line = {
-        "metric": "MFLUPS (D3Q19 LBGK site updates per second / 1e6), whole hot path per step",
+        "metric": METRIC,
         "value": value, "unit": "MFLUPS", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": h["ms"] / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[head[0]],
         "data": "synthetic (seeded tree geometry, rest initial state)",
         "config": {**cfg, "storage": head[0], "scheme": head[1], "launch": h["launch"],
+                   "timing": f"median of {h['reps']} back-to-back {args.steps}-step measurements "
+                             f"({h['timed_s']:.2f} s of device time)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": h["achieved_gbs"], "peak": peak, "unit": "GB/s",
                      "frac": h["achieved_gbs"] / peak, "traffic": traffic,
@@ -661,7 +680,8 @@ def main():
                 "h2d_bytes_per_step": h["h2d"] / args.steps,
                 "d2h_bytes_per_step": h["d2h"] / args.steps,
                 "job": "hg_load_state(pinned host) + steps + hg_read_macroscopic(host)"},
-        "gpu_launches": h["launches"],
+        "gpu_launches": h["launches"] * h["reps"],
+        "gpu_launches_per_measurement": h["launches"],
         "clocks": sampler.summary(),
         "variants": {f"{s}:{c}": {"mflups": r["mflups"], "achieved_gbs": r["achieved_gbs"],
                                    "roofline_frac": r["achieved_gbs"] / peak,

@@ -73,8 +73,17 @@ extern "C" {
 #define HG_PULSE_COSINE 1 /* value(t) = value * (1 - cos(2 pi t / period)) / 2 */
 #define HG_PULSE_SINE 2   /* value(t) = value * sin(2 pi t / period) */
 
-/* ---- site orderings (device layout; exported data is always canonical) ---- */
+/* ---- site orderings (device layout; exported data is always canonical) ----
+ * Every ordering gives bit-identical fields, iolet means and mass: the per-site
+ * arithmetic does not depend on it, each iolet's FP64 sums and the mass sum
+ * run in canonical order.  Only the memory access pattern changes. */
 #define HG_ORDER_MORTON 0 /* canonical order */
+#define HG_ORDER_ROWS 1   /* lexicographic: x fastest, then y, then z */
+#define HG_ORDER_BRICKS 2 /* x-fastest rows inside 32 x 8 x 8 bricks, bricks in Morton order */
+
+/* ---- host-side fault injection (hg_ctx_inject_fault) ---- */
+#define HG_FAULT_ALLOC 1       /* the arg-th device allocation from now on fails (0 cancels) */
+#define HG_FAULT_DEVICE_WAIT 2 /* set the device error word as a bounded wait that gave up does */
 
 /* Coupling exchange direction (Section 3 alternates forward and reverse). */
 #define HG_COUPLE_FORWARD 0   /* forward after every step (default) */
@@ -324,8 +333,9 @@ int hg_read_boundary_values(hg_domain *d, float *out);
  * Passage: Section 3 (reverse direction: arterial-outlet boundary force). */
 int hg_read_iolet_forces(hg_domain *d, float *out);
 
-/* Total mass deviation sum_s sum_i f~_i(s) of the current state, FP64, in
- * canonical site order.
+/* Total mass deviation sum_s sum_i f~_i(s) of the current state, FP64: fixed
+ * chunks of 8192 sites in canonical order, each summed by a fixed tree, the
+ * chunk sums added in order (the same bits for every device ordering).
  * Passage: infrastructure: no passage (mass check of the LB state; the paper
  * describes none). */
 int hg_mass(hg_domain *d, double *out);
@@ -343,13 +353,42 @@ int hg_mass(hg_domain *d, double *out);
  * that loads it until the process exits, so n is limited to 134,217,728 sites
  * (HG_ERR_ARG beyond).  The first call on a device looks up that array's
  * device address (cudaGetSymbolAddress) with the device current; make that
- * first call before any stream capture.  All calls share the array: calls
+ * first call before any stream capture.  The address is kept for the rest of
+ * the process: it belongs to the device's primary context as it was at that
+ * first call, so after cudaDeviceReset (or any teardown of that context) this
+ * entry point must not be called again in the same process.  All calls share the array: calls
  * whose kernels overlap on the GPU race and may return wrong sums; calls
  * ordered on one stream are safe.  Asynchronous.  Errors: HG_ERR_ARG,
  * HG_ERR_CUDA.
  * Passage: no counterpart in the paper (see above). */
 int hg_mass_noalloc(const void *f_dev, int32_t storage, int64_t n, int64_t row_stride,
                     double *out_dev, void *stream);
+
+/* Mass check with a NaN/Inf watchdog: the FP64 mass of the current state
+ * (as hg_mass) and the number of stored values that are not finite.  Returns
+ * HG_ERR_STATE when that number is non-zero (both outputs are still filled).
+ * Either pointer may be NULL.  Synchronises.
+ * Passage: infrastructure: no passage (state watchdog). */
+int hg_state_check(hg_domain *d, double *mass, int64_t *nonfinite);
+
+/* The per-site moments the last step's iolet reductions took as input: for
+ * every site next to any iolet, in canonical order, its canonical index
+ * (sites_out, n_adjacent int64) and (drho, ux, uy, uz) FP32 (mom_out,
+ * n_adjacent x 4) of that step's collision.  hg_read_iolet_stats holds the FP64
+ * means of exactly these values.  Synchronises.
+ * Passage: Section 2.3 (the averaged macroscopic values passed between coupled
+ * instances are averages of these per-site values). */
+int hg_read_adjacent_moments(hg_domain *d, int64_t *sites_out, float *mom_out);
+
+/* Host-side fault injection for tests of the error paths (no GPU fault is
+ * made).  HG_FAULT_ALLOC: the arg-th device allocation the context makes from
+ * now on (1 = the next) fails as if the allocator returned NULL; the call that
+ * makes it returns HG_ERR_OOM and releases what it had set up; arg = 0 cancels.
+ * HG_FAULT_DEVICE_WAIT: writes code arg (0 -> 1) to the context's device error
+ * word, stream-ordered, exactly as a bounded device wait that gave up would;
+ * the next hg_sync returns HG_ERR_TIMEOUT.  Errors: HG_ERR_ARG, HG_ERR_CUDA.
+ * Passage: infrastructure: no passage (failure detection). */
+int hg_ctx_inject_fault(hg_ctx *ctx, int32_t kind, int64_t arg);
 
 /* ---- checkpoint / resume ---- */
 

@@ -10,8 +10,8 @@ take the macroscopic fields a domain returns (``Domain.macroscopic()``:
 * ``velocity_vs_area_planes``: mean speed against vessel cross-section area, the
   quantity Section 3.3 plots for the coupled arterial and venous trees, measured
   as the paper describes: lattice planes at 1/4, 1/2 and 3/4 of the domain's
-  length, separated into vessels, area from the convex hull of each vessel's
-  lattice points.
+  length, separated into vessels, area from the convex hull around each
+  vessel's lattice points (each point as its unit cell).
 * ``velocity_vs_area``: the same quantity per tree segment.  The
   paper cuts measurement planes through the whole domain and separates them
   into vessels; a synthetic tree knows its centrelines, so each segment is cut
@@ -158,12 +158,23 @@ def _hull_area(P):
     return 0.5 * abs(float(np.dot(x, np.roll(y, -1)) - np.dot(y, np.roll(x, -1))))
 
 
+def _cell_hull_area(P):
+    """Area of the convex hull around lattice points P (m, 2), each point taken as the unit
+    square it stands for: one rule for every vessel size (one site: 1; a one-site-wide line
+    of k sites: k; never 0), and within half a lattice unit of the hull through the points'
+    centres along the rim of a large vessel."""
+    P = np.asarray(P, np.float64)
+    corners = np.concatenate([P + d for d in ((-0.5, -0.5), (-0.5, 0.5), (0.5, -0.5), (0.5, 0.5))])
+    return _hull_area(corners)
+
+
 def velocity_vs_area_planes(fields, xyz, fractions=(0.25, 0.5, 0.75), axis=None,
                             arterial_negative=False):
     """Section 3.3's measurement as the paper describes it: lattice planes normal to the
     domain's longest extent (or ``axis``) at the given fractions of its length, each cut
     separated into vessels (8-connected groups of sites in the plane), each vessel's area
-    the convex hull of its lattice points, its speed the mean |u| over them.
+    the convex hull around its lattice points (each point as its unit cell, so vessels one
+    site wide keep a non-zero area), its speed the mean |u| over them.
 
     Returns rows (fraction, vessel, area, mean |u|, sites); areas negative when
     ``arterial_negative`` is set, as the paper plots the arterial vessels."""
@@ -184,7 +195,7 @@ def velocity_vs_area_planes(fields, xyz, fractions=(0.25, 0.5, 0.75), axis=None,
         for c in range(labels.max() + 1):
             mem = sel[labels == c]
             Pc = X[mem][:, others]
-            area = _hull_area(Pc) if mem.size >= 3 else float(mem.size)
+            area = _cell_hull_area(Pc)
             speed = float(np.linalg.norm(fields[mem, 1:4].astype(np.float64), axis=1).mean())
             rows.append((f, c, -area if arterial_negative else area, speed, int(mem.size)))
     return np.array(rows, dtype=np.float64).reshape(-1, 5)

@@ -8,8 +8,8 @@ hg_load_state), so tuning never changes the simulation.  Every candidate
 computes bit-identical results; only the time differs.
 
 Results are kept in a JSON cache (``$HEMEGB_TUNE_CACHE``, default
-``~/.cache/hemegb/tune.json``) keyed by device, storage, scheme and domain
-sizes, so a later process on the same machine reuses the choice instead of
+``~/.cache/hemegb/tune.json``) keyed by device, storage, scheme, domain sizes
+and device orderings, so a later process on the same machine reuses the choice instead of
 re-timing (and a run under a profiler, whose timings are distorted, picks the
 same shape as the plain run before it).
 """
@@ -44,7 +44,7 @@ def _key(ctx, candidates):
         dev = torch.cuda.get_device_name(ctx.device)
     except Exception:
         dev = "cuda"
-    sizes = ",".join(str(d.n) for d in ctx.domains)
+    sizes = ",".join(f"{d.n}/{getattr(d, 'ordering', 0)}" for d in ctx.domains)
     cands = hashlib.sha1(repr(sorted(tuple(c) for c in candidates)).encode()).hexdigest()[:8]
     return f"{dev}|storage={ctx.storage}|scheme={ctx.scheme}|sites={sizes}|candidates={cands}"
 
@@ -103,3 +103,22 @@ def autotune(ctx, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2, use_cache=T
     if use_cache:
         _store(key, best, timing)
     return best, timing
+
+
+def tune_ordering(make_ctx, orderings=("morton", "rows", "bricks"), candidates=DEFAULT_CANDIDATES,
+                  use_cache=True):
+    """Site ordering as a tuning dimension: the device layout is fixed when a domain is
+    built, so ``make_ctx(ordering)`` builds a fresh context with its domains in that
+    ordering; each is launch-tuned and closed again.  Returns (best ordering, its launch
+    shape, {ordering: (shape, ms per stream-collide launch)}).  Every ordering computes
+    bit-identical results."""
+    table = {}
+    for o in orderings:
+        ctx = make_ctx(o)
+        try:
+            best, timing = autotune(ctx, candidates, use_cache=use_cache)
+            table[o] = (best, timing[best])
+        finally:
+            ctx.close()
+    o = min(table, key=lambda k: table[k][1])
+    return o, table[o][0], table

@@ -58,7 +58,7 @@ template <> struct St<kF16> {
     template <int I> static __device__ __forceinline__ float ld(T v) { return __half2float(v); }
     template <int I> static __device__ __forceinline__ T st(float v) { return __float2half_rn(v); }
     template <int I> static __device__ __forceinline__ float phys(T v) { return __half2float(v) * W(I); }
-    static __device__ __forceinline__ double ldd(T v, int i) { return (double)__half2float(v) * WD(i); }
+    static __device__ __forceinline__ double ldd(T v, int i) { return __dmul_rn((double)__half2float(v), WD(i)); }
 };
 template <> struct St<kBF16> {
     using T = __nv_bfloat16;
@@ -66,7 +66,7 @@ template <> struct St<kBF16> {
     template <int I> static __device__ __forceinline__ float ld(T v) { return __bfloat162float(v); }
     template <int I> static __device__ __forceinline__ T st(float v) { return __float2bfloat16_rn(v); }
     template <int I> static __device__ __forceinline__ float phys(T v) { return __bfloat162float(v) * W(I); }
-    static __device__ __forceinline__ double ldd(T v, int i) { return (double)__bfloat162float(v) * WD(i); }
+    static __device__ __forceinline__ double ldd(T v, int i) { return __dmul_rn((double)__bfloat162float(v), WD(i)); }
 };
 
 template <int N> struct IC { static constexpr int v = N; };

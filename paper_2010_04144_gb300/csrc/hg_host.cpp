@@ -236,6 +236,64 @@ void sort_keys(std::vector<uint64_t> &key, std::vector<int64_t> &idx) {
     }
 }
 
+// Device layout of a domain's sites (the canonical order is always Morton):
+//   HG_ORDER_ROWS   lexicographic, x fastest, then y, then z: a warp's 32
+//                   consecutive sites mostly form one x-row, and the same row
+//                   shifted by one lattice unit is again a run of consecutive
+//                   sites, so gathers and the AA scatter touch few sectors;
+//   HG_ORDER_BRICKS rows inside 32 x 8 x 8 bricks, the bricks in Morton order
+//                   (row locality with block locality for very large domains).
+// canon_of[q] = canonical index of the site at device position q.
+int device_order(const std::vector<int32_t> &xyz, int64_t n, int ordering, std::vector<int32_t> &canon_of,
+                 std::string &why) {
+    int32_t lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int e = 0; e < 3; ++e) {
+        lo[e] = n ? xyz[e] : 0;
+        hi[e] = lo[e];
+    }
+    for (int64_t s = 0; s < n; ++s)
+        for (int e = 0; e < 3; ++e) {
+            lo[e] = std::min(lo[e], xyz[3 * s + e]);
+            hi[e] = std::max(hi[e], xyz[3 * s + e]);
+        }
+    std::vector<uint64_t> key(n);
+    std::vector<int64_t> idx(n);
+    if (ordering == HG_ORDER_ROWS) {
+        parallel_for(n, [&](int64_t a, int64_t b) {
+            for (int64_t s = a; s < b; ++s) {
+                const uint64_t x = (uint64_t)(xyz[3 * s] - lo[0]), y = (uint64_t)(xyz[3 * s + 1] - lo[1]),
+                               z = (uint64_t)(xyz[3 * s + 2] - lo[2]);
+                key[s] = (z << 42) | (y << 21) | x;
+                idx[s] = s;
+            }
+        });
+    } else {  // HG_ORDER_BRICKS: 32 x 8 x 8
+        uint32_t mx = 0;
+        for (int e = 0; e < 3; ++e)
+            mx = std::max<uint32_t>(mx, (uint32_t)(hi[e] - lo[e]) >> (e == 0 ? 5 : 3));
+        int w = 0;
+        while (w < 21 && (mx >> w)) ++w;
+        if (3 * w + 11 > 64) {
+            why = "domain extent too large for the brick ordering";
+            return HG_ERR_ARG;
+        }
+        parallel_for(n, [&](int64_t a, int64_t b) {
+            for (int64_t s = a; s < b; ++s) {
+                const uint32_t x = (uint32_t)(xyz[3 * s] - lo[0]), y = (uint32_t)(xyz[3 * s + 1] - lo[1]),
+                               z = (uint32_t)(xyz[3 * s + 2] - lo[2]);
+                const uint64_t brick = morton3(x >> 5, y >> 3, z >> 3);
+                const uint64_t inner = ((uint64_t)(z & 7) << 8) | ((uint64_t)(y & 7) << 5) | (x & 31);
+                key[s] = (brick << 11) | inner;
+                idx[s] = s;
+            }
+        });
+    }
+    sort_keys(key, idx);
+    canon_of.resize(n);
+    for (int64_t q = 0; q < n; ++q) canon_of[q] = (int32_t)idx[q];
+    return HG_OK;
+}
+
 double pulse(int kind, double t, double period) {
     const double ph = kind == HG_PULSE_CONST ? 0.0 : std::fmod(t, period) / period;
     if (kind == HG_PULSE_COSINE) return 0.5 * (1.0 - std::cos(2.0 * 3.141592653589793 * ph));
@@ -294,6 +352,7 @@ struct hg_ctx {
     std::map<PlanKey, std::unique_ptr<Plan>> plans;
     DevBuf scratch;                 // mass partials, read-back staging
     std::atomic<int64_t> device_bytes{0};
+    std::atomic<int64_t> fail_alloc_in{0};  // injected fault: the k-th next allocation fails (0 = none)
 };
 
 struct hg_domain {
@@ -312,11 +371,20 @@ struct hg_domain {
     DevBuf slot_site;                    // per slot: device site index
     std::vector<int32_t> slots_host;     // per-iolet CSR of slots (io_ptr), host copy
     std::vector<int32_t> io_codes_host;  // per slot x 18, canonical codes
-    std::vector<int32_t> slot_of_site;   // canonical site -> slot or -1
+    std::vector<int32_t> slot_of_dev;    // device site -> slot or -1
+    int32_t ordering = HG_ORDER_MORTON;  // device layout of the sites
+    std::vector<int32_t> canon_of_host;  // device -> canonical index (empty: identity)
+    std::vector<int32_t> dev_of_host;    // canonical -> device index (empty: identity)
+    DevBuf canon_of, dev_of;             // device copies of the two permutations
     int64_t bytes = 0;
 };
 
 namespace {
+
+std::vector<DevBuf *> domain_buffers(hg_domain *d) {
+    return {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd, &d->coef,
+            &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force, &d->slot_site, &d->canon_of, &d->dev_of};
+}
 
 // last failure of the calling thread and the context it concerned
 thread_local const hg_ctx *t_err_ctx = nullptr;
@@ -343,6 +411,10 @@ int fail(hg_ctx *ctx, int code, const char *fmt, ...) {
 int dev_alloc(hg_ctx *ctx, DevBuf &b, size_t bytes) {
     if (bytes == 0) bytes = 256;
     bytes = (bytes + 255) & ~(size_t)255;
+    int64_t k = ctx->fail_alloc_in.load();
+    while (k > 0 && !ctx->fail_alloc_in.compare_exchange_weak(k, k - 1)) {
+    }
+    if (k == 1) return fail(ctx, HG_ERR_OOM, "injected allocation failure (%zu bytes)", bytes);
     void *p = nullptr;
     if (ctx->alloc) {
         p = ctx->alloc(bytes, ctx->alloc_user);
@@ -628,7 +700,9 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         return fail(ctx, HG_ERR_ARG, "n_iolets must be in [0, %d]", kMaxIolets);
     const double tau = lb ? lb->tau : 0.8;
     if (!(tau > 0.5)) return fail(ctx, HG_ERR_ARG, "tau must exceed 1/2");
-    if (lb && lb->ordering != HG_ORDER_MORTON) return fail(ctx, HG_ERR_ARG, "unknown ordering");
+    const int32_t ordering = lb ? lb->ordering : HG_ORDER_MORTON;
+    if (ordering < HG_ORDER_MORTON || ordering > HG_ORDER_BRICKS)
+        return fail(ctx, HG_ERR_ARG, "unknown ordering %d", ordering);
     for (int k = 0; k < nio; ++k)
         if (!iolet_ok(iolets[k])) return fail(ctx, HG_ERR_ARG, "iolet %d out of range", k);
     CU(ctx, cudaSetDevice(ctx->device));
@@ -659,6 +733,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     d->np = std::max<int64_t>(128, (n + 127) / 128 * 128);
     d->nio = nio;
     d->tau = tau;
+    d->ordering = ordering;
     d->io.assign(iolets, iolets + nio);
 
     // --- canonical order and neighbour table (canonical codes)
@@ -670,79 +745,113 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         if (brc != HG_OK) return fail(ctx, brc, "%s", why.c_str());
     }
 
-    // --- iolet adjacency: slots in canonical order, per-iolet CSR lists
+    // --- device ordering: a permutation of the canonical order (none for Morton).
+    // The table's columns move to their device positions and fluid entries are
+    // renumbered; every other table is built in device order below, except the
+    // per-iolet slot lists, which stay in canonical order of the sites so each
+    // iolet's FP64 sums run in the same order whatever the layout.
+    std::vector<int32_t> canon_of, dev_of;  // device -> canonical, canonical -> device
+    if (d->ordering != HG_ORDER_MORTON) {
+        std::string why;
+        if (device_order(d->xyz, n, d->ordering, canon_of, why) != HG_OK)
+            return fail(ctx, HG_ERR_ARG, "%s", why.c_str());
+        dev_of.assign(n, 0);
+        parallel_for(n, [&](int64_t lo, int64_t hi) {
+            for (int64_t q = lo; q < hi; ++q) dev_of[canon_of[q]] = (int32_t)q;
+        });
+        std::vector<int32_t> row(n);
+        for (int i = 0; i < 18; ++i) {
+            int32_t *r = nbr.data() + (size_t)i * np;
+            parallel_for(n, [&](int64_t lo, int64_t hi) {
+                for (int64_t q = lo; q < hi; ++q) {
+                    const int32_t v = r[canon_of[q]];
+                    row[q] = v >= 0 ? dev_of[v] : v;
+                }
+            });
+            std::copy(row.begin(), row.end(), r);
+        }
+    }
+    auto canon = [&](int64_t q) -> int64_t { return canon_of.empty() ? q : canon_of[q]; };
+    auto devix = [&](int64_t c) -> int64_t { return dev_of.empty() ? c : dev_of[c]; };
+
+    // --- iolet adjacency: slots numbered in device order (the kernels find a
+    // site's slot as the rank of its flag), per-iolet CSR lists in canonical order
     std::vector<int32_t> slot_of(n, -1);
     int64_t n_adj = 0;
     std::vector<int64_t> per_io(nio + 1, 0);
-    for (int64_t s = 0; s < n; ++s) {
-        bool adj = false;
-        int seen[18], n_seen = 0;  // distinct iolets touched by this site
+    auto distinct_iolets = [&](int64_t q, int seen[18]) {
+        int n_seen = 0;
         for (int i = 0; i < 18; ++i) {
-            const int32_t v = nbr[(size_t)i * np + s];
+            const int32_t v = nbr[(size_t)i * np + q];
             if (v < -1) {
-                adj = true;
                 const int k = -v - 2;
                 bool dup = false;
-                for (int q = 0; q < n_seen; ++q) dup = dup || seen[q] == k;
-                if (!dup) {
-                    seen[n_seen++] = k;
-                    per_io[k + 1]++;
-                }
+                for (int t = 0; t < n_seen; ++t) dup = dup || seen[t] == k;
+                if (!dup) seen[n_seen++] = k;
             }
         }
-        if (adj) slot_of[s] = (int32_t)n_adj++;
+        return n_seen;
+    };
+    for (int64_t q = 0; q < n; ++q) {
+        int seen[18];
+        const int ns = distinct_iolets(q, seen);
+        for (int t = 0; t < ns; ++t) per_io[seen[t] + 1]++;
+        if (ns) slot_of[q] = (int32_t)n_adj++;
     }
     d->n_adj = n_adj;
     for (int k = 0; k < nio; ++k) per_io[k + 1] += per_io[k];
     d->io_ptr.assign(per_io.begin(), per_io.end());
     std::vector<int32_t> slots(std::max<int64_t>(1, per_io[nio]));
+    {
+        std::vector<int64_t> fill(per_io.begin(), per_io.end() - 1);
+        for (int64_t c = 0; c < n; ++c) {
+            const int64_t q = devix(c);
+            if (slot_of[q] < 0) continue;
+            int seen[18];
+            const int ns = distinct_iolets(q, seen);
+            for (int t = 0; t < ns; ++t) slots[fill[seen[t]]++] = slot_of[q];
+        }
+    }
     std::vector<float> coef((size_t)std::max<int64_t>(1, n_adj) * 18, 0.0f);
     std::vector<uint32_t> mask((size_t)(np / 32), 0u);
     std::vector<int32_t> codes((size_t)std::max<int64_t>(1, n_adj) * 18, -1);
-    {
-        std::vector<int64_t> fill(per_io.begin(), per_io.end() - 1);
-        for (int64_t s = 0; s < n; ++s) {
-            const int32_t sl = slot_of[s];
-            if (sl < 0) continue;
-            mask[s >> 5] |= 1u << (s & 31);
-            int seen[18], n_seen = 0;
-            for (int i = 1; i < 19; ++i) codes[(size_t)sl * 18 + (i - 1)] = nbr[(size_t)(i - 1) * np + s];
-            for (int i = 1; i < 19; ++i) {
-                const int32_t v = nbr[(size_t)(i - 1) * np + s];
-                if (v >= -1) continue;
-                const int k = -v - 2;
-                bool dup = false;
-                for (int q = 0; q < n_seen; ++q) dup = dup || seen[q] == k;
-                if (!dup) {
-                    seen[n_seen++] = k;
-                    slots[fill[k]++] = sl;
-                }
-                const hg_iolet &io = iolets[k];
-                if (io.kind == HG_VELOCITY) {
-                    const double an = std::sqrt((double)io.axis[0] * io.axis[0] +
-                                                (double)io.axis[1] * io.axis[1] +
-                                                (double)io.axis[2] * io.axis[2]);
-                    const double ah[3] = {io.axis[0] / an, io.axis[1] / an, io.axis[2] / an};
-                    double phi = 1.0;
-                    if (io.profile == HG_PARABOLIC) {
-                        double rel[3], along = 0.0;
-                        for (int c = 0; c < 3; ++c) {
-                            rel[c] = (d->xyz[3 * s + c] - 0.5 * kC[i][c]) - io.centre[c] / 1024.0;
-                            along += rel[c] * ah[c];
-                        }
-                        double p2 = 0.0;
-                        for (int c = 0; c < 3; ++c) {
-                            const double q = rel[c] - along * ah[c];
-                            p2 += q * q;
-                        }
-                        const double r = io.radius / 1024.0;
-                        phi = r > 0 ? std::max(0.0, 1.0 - p2 / (r * r)) : 0.0;
+    for (int64_t q = 0; q < n; ++q) {
+        const int32_t sl = slot_of[q];
+        if (sl < 0) continue;
+        mask[q >> 5] |= 1u << (q & 31);
+        const int64_t c = canon(q);
+        for (int i = 1; i < 19; ++i) {  // canonical codes: fluid links hold the canonical source
+            const int32_t v = nbr[(size_t)(i - 1) * np + q];
+            codes[(size_t)sl * 18 + (i - 1)] = v >= 0 ? (int32_t)canon(v) : v;
+        }
+        for (int i = 1; i < 19; ++i) {
+            const int32_t v = nbr[(size_t)(i - 1) * np + q];
+            if (v >= -1) continue;
+            const hg_iolet &io = iolets[-v - 2];
+            if (io.kind == HG_VELOCITY) {
+                const double an = std::sqrt((double)io.axis[0] * io.axis[0] +
+                                            (double)io.axis[1] * io.axis[1] +
+                                            (double)io.axis[2] * io.axis[2]);
+                const double ah[3] = {io.axis[0] / an, io.axis[1] / an, io.axis[2] / an};
+                double phi = 1.0;
+                if (io.profile == HG_PARABOLIC) {
+                    double rel[3], along = 0.0;
+                    for (int e = 0; e < 3; ++e) {
+                        rel[e] = (d->xyz[3 * c + e] - 0.5 * kC[i][e]) - io.centre[e] / 1024.0;
+                        along += rel[e] * ah[e];
                     }
-                    const double cdot = -(kC[i][0] * ah[0] + kC[i][1] * ah[1] + kC[i][2] * ah[2]);
-                    // 16-bit storage holds f~/w and collides on it: the coefficient drops w_i
-                    const double wi = ctx->storage == HG_STORE_F32 ? wgt(i) : 1.0;
-                    coef[(size_t)sl * 18 + (i - 1)] = (float)(6.0 * wi * cdot * phi);
+                    double p2 = 0.0;
+                    for (int e = 0; e < 3; ++e) {
+                        const double t = rel[e] - along * ah[e];
+                        p2 += t * t;
+                    }
+                    const double r = io.radius / 1024.0;
+                    phi = r > 0 ? std::max(0.0, 1.0 - p2 / (r * r)) : 0.0;
                 }
+                const double cdot = -(kC[i][0] * ah[0] + kC[i][1] * ah[1] + kC[i][2] * ah[2]);
+                // 16-bit storage holds f~/w and collides on it: the coefficient drops w_i
+                const double wi = ctx->storage == HG_STORE_F32 ? wgt(i) : 1.0;
+                coef[(size_t)sl * 18 + (i - 1)] = (float)(6.0 * wi * cdot * phi);
             }
         }
     }
@@ -758,21 +867,23 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     // virtual indices for every non-fluid link (walls and iolet links alike)
     const bool aa = ctx->scheme == HG_SCHEME_AA;
     parallel_for(n, [&](int64_t lo, int64_t hi) {
-        for (int64_t s = lo; s < hi; ++s)
+        for (int64_t q = lo; q < hi; ++q)
             for (int i = 1; i < 19; ++i) {
-                int32_t &v = nbr[(size_t)(i - 1) * np + s];
+                int32_t &v = nbr[(size_t)(i - 1) * np + q];
                 if (v >= 0) continue;
                 const int opp = (i & 1) ? i + 1 : i - 1;
-                const int64_t d = aa ? (int64_t)(i - opp) : (int64_t)(opp - i);
-                v = (int32_t)(s + d * np);
+                const int64_t dd = aa ? (int64_t)(i - opp) : (int64_t)(opp - i);
+                v = (int32_t)(q + dd * np);
             }
     });
     std::vector<int32_t> slot_site((size_t)std::max<int64_t>(1, n_adj), 0);
-    for (int64_t s = 0; s < n; ++s)
-        if (slot_of[s] >= 0) slot_site[slot_of[s]] = (int32_t)s;
+    for (int64_t q = 0; q < n; ++q)
+        if (slot_of[q] >= 0) slot_site[slot_of[q]] = (int32_t)q;
     d->io_codes_host = codes;
-    d->slot_of_site = slot_of;
+    d->slot_of_dev = slot_of;
     d->slots_host = slots;
+    d->canon_of_host = canon_of;
+    d->dev_of_host = dev_of;
 
     // --- device buffers
     hg_ctx *c = ctx;
@@ -796,20 +907,18 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     A(d->slots, slots.size() * 4);
     A(d->force, (size_t)std::max(1, nio) * 16);
     A(d->slot_site, slot_site.size() * 4);
+    if (!canon_of.empty()) {
+        A(d->canon_of, (size_t)n * 4);
+        A(d->dev_of, (size_t)n * 4);
+    }
     auto cleanup = [&] {
-        DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
-                        &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force,
-                        &d->slot_site};
-        for (DevBuf *b : bs) dev_free(c, *b);
+        for (DevBuf *b : domain_buffers(d.get())) dev_free(c, *b);
     };
     if (rc != HG_OK) {
         cleanup();
         return rc;
     }
-    for (DevBuf *b : {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
-                      &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force,
-                        &d->slot_site})
-        d->bytes += (int64_t)b->bytes;
+    for (DevBuf *b : domain_buffers(d.get())) d->bytes += (int64_t)b->bytes;
     std::vector<float> bcv(std::max(1, nio), 0.0f);
     std::vector<int8_t> kinds(std::max(1, nio), 0);
     for (int k = 0; k < nio; ++k) {
@@ -832,6 +941,10 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     H2D(d->io_kind, kinds.data(), kinds.size());
     H2D(d->slots, slots.data(), slots.size() * 4);
     H2D(d->slot_site, slot_site.data(), slot_site.size() * 4);
+    if (!canon_of.empty()) {
+        H2D(d->canon_of, canon_of.data(), (size_t)n * 4);
+        H2D(d->dev_of, dev_of.data(), (size_t)n * 4);
+    }
     if (e == cudaSuccess) e = cudaMemsetAsync(d->f[0].p, 0, d->f[0].bytes, up);
     if (e == cudaSuccess && d->f[1].p) e = cudaMemsetAsync(d->f[1].p, 0, d->f[1].bytes, up);
     if (e == cudaSuccess) e = cudaMemsetAsync(d->bnd.p, 0, d->bnd.bytes, up);
@@ -872,10 +985,7 @@ int hg_domain_destroy(hg_domain *d) {
         }
         ctx->doms[d->idx] = nullptr;
     }
-    DevBuf *bs[] = {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd,
-                    &d->coef, &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force,
-                        &d->slot_site};
-    for (DevBuf *b : bs) dev_free(ctx, *b);
+    for (DevBuf *b : domain_buffers(d)) dev_free(ctx, *b);
     if (ctx->couple_mode == HG_COUPLE_ALTERNATE) refresh_domdevs(ctx);  // a source may have lost its pairs
     delete d;
     return HG_OK;
@@ -903,17 +1013,25 @@ int hg_domain_neighbours(hg_domain *d, int32_t *nbr_out) {
     hg_ctx *ctx = d->ctx;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
-    for (int i = 0; i < 18; ++i)
-        CU(ctx, cudaMemcpy(nbr_out + (size_t)i * d->n, (const int32_t *)d->nbr.p + (size_t)i * d->np,
+    std::vector<int32_t> row(std::max<int64_t>(1, d->n));
+    const std::vector<int32_t> &co = d->canon_of_host, &dv = d->dev_of_host;
+    for (int i = 0; i < 18; ++i) {
+        CU(ctx, cudaMemcpy(row.data(), (const int32_t *)d->nbr.p + (size_t)i * d->np,
                            sizeof(int32_t) * d->n, cudaMemcpyDeviceToHost));
-    // virtual indices (outside [0, n)) mark non-fluid links: wall, or the iolet code of the slot
-    for (int i = 0; i < 18; ++i)
-        for (int64_t s = 0; s < d->n; ++s) {
-            int32_t &v = nbr_out[(size_t)i * d->n + s];
-            if (v >= 0 && v < d->n) continue;
-            const int32_t sl = d->slot_of_site[s];
-            v = sl >= 0 ? d->io_codes_host[(size_t)sl * 18 + i] : -1;
+        // back to canonical positions and indices; virtual indices (outside [0, n)) mark
+        // non-fluid links: wall, or the iolet code of the site's slot
+        for (int64_t c = 0; c < d->n; ++c) {
+            const int64_t q = dv.empty() ? c : dv[c];
+            const int32_t v = row[q];
+            int32_t &o = nbr_out[(size_t)i * d->n + c];
+            if (v >= 0 && v < d->n) {
+                o = co.empty() ? v : co[v];
+            } else {
+                const int32_t sl = d->slot_of_dev[q];
+                o = sl >= 0 ? d->io_codes_host[(size_t)sl * 18 + i] : -1;
+            }
         }
+    }
     return HG_OK;
 }
 
@@ -1421,7 +1539,7 @@ int hg_read_macroscopic_device(hg_domain *d, float *dev_out) {
     hg_ctx *ctx = d->ctx;
     if (((uintptr_t)dev_out) & 15) return fail(ctx, HG_ERR_ARG, "output must be 16-byte aligned");
     CU(ctx, cudaSetDevice(ctx->device));
-    CU(ctx, launch_macroscopic(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, nullptr,
+    CU(ctx, launch_macroscopic(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, (const int32_t *)d->canon_of.p,
                                (float4 *)dev_out, ctx->stream));
     return HG_OK;
 }
@@ -1473,18 +1591,79 @@ int hg_read_boundary_values(hg_domain *d, float *out) {
     return HG_OK;
 }
 
-int hg_mass(hg_domain *d, double *out) {
-    if (!d || !out) return HG_ERR_ARG;
+// FP64 mass of the current state in canonical order, and its count of non-finite values.
+static int mass_pass(hg_domain *d, double *mass, int64_t *nonfinite) {
     hg_ctx *ctx = d->ctx;
     CU(ctx, cudaSetDevice(ctx->device));
     const int64_t P = mass_partials_needed(d->n);
-    int rc = ensure_scratch(ctx, (size_t)(P + 1) * 8);
+    int rc = ensure_scratch(ctx, (size_t)(P + 1) * sizeof(double2));
     if (rc != HG_OK) return rc;
-    double *part = (double *)ctx->scratch.p;
-    CU(ctx, launch_mass(ctx->storage, domdev_ptr(d), d->n, d->np, part, part + P, ctx->stream));
-    CU(ctx, cudaMemcpyAsync(out, part + P, 8, cudaMemcpyDeviceToHost, ctx->stream));
+    double2 *part = (double2 *)ctx->scratch.p;
+    CU(ctx, launch_mass(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, (const int32_t *)d->dev_of.p, part,
+                        part + P, ctx->stream));
+    double2 r;
+    CU(ctx, cudaMemcpyAsync(&r, part + P, sizeof r, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
+    if (mass) *mass = r.x;
+    if (nonfinite) *nonfinite = (int64_t)r.y;
     return HG_OK;
+}
+
+int hg_mass(hg_domain *d, double *out) {
+    if (!d || !out) return HG_ERR_ARG;
+    return mass_pass(d, out, nullptr);
+}
+
+int hg_state_check(hg_domain *d, double *mass, int64_t *nonfinite) {
+    if (!d) return HG_ERR_ARG;
+    double m = 0.0;
+    int64_t bad = 0;
+    const int rc = mass_pass(d, &m, &bad);
+    if (rc != HG_OK) return rc;
+    if (mass) *mass = m;
+    if (nonfinite) *nonfinite = bad;
+    if (bad) return fail(d->ctx, HG_ERR_STATE, "the state holds %lld non-finite values", (long long)bad);
+    return HG_OK;
+}
+
+int hg_read_adjacent_moments(hg_domain *d, int64_t *sites_out, float *mom_out) {
+    if (!d || (d->n_adj && (!sites_out || !mom_out))) return HG_ERR_ARG;
+    hg_ctx *ctx = d->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    std::vector<float4> b((size_t)std::max<int64_t>(1, d->n_adj));
+    if (d->n_adj)
+        CU(ctx, cudaMemcpyAsync(b.data(), d->bnd.p, (size_t)d->n_adj * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    int64_t j = 0;
+    for (int64_t c = 0; c < d->n; ++c) {  // canonical order of the sites
+        const int64_t q = d->dev_of_host.empty() ? c : d->dev_of_host[c];
+        const int32_t sl = d->slot_of_dev[q];
+        if (sl < 0) continue;
+        sites_out[j] = c;
+        mom_out[4 * j] = b[sl].x;
+        mom_out[4 * j + 1] = b[sl].y;
+        mom_out[4 * j + 2] = b[sl].z;
+        mom_out[4 * j + 3] = b[sl].w;
+        ++j;
+    }
+    return HG_OK;
+}
+
+int hg_ctx_inject_fault(hg_ctx *ctx, int32_t kind, int64_t arg) {
+    if (!ctx) return HG_ERR_ARG;
+    if (kind == HG_FAULT_ALLOC) {
+        if (arg < 0) return fail(ctx, HG_ERR_ARG, "allocation index must be >= 0");
+        ctx->fail_alloc_in = arg;
+        return HG_OK;
+    }
+    if (kind == HG_FAULT_DEVICE_WAIT) {
+        const int32_t code = arg ? (int32_t)arg : 1;
+        CU(ctx, cudaSetDevice(ctx->device));
+        CU(ctx, cudaMemcpyAsync(ctx->errw.p, &code, sizeof code, cudaMemcpyHostToDevice, ctx->stream));
+        CU(ctx, cudaStreamSynchronize(ctx->stream));
+        return HG_OK;
+    }
+    return fail(ctx, HG_ERR_ARG, "unknown fault kind %d", kind);
 }
 
 // checkpoint layout: header | bcv[nio] f32 | M[nio*3] f64 | F[19][n] storage |
@@ -1509,8 +1688,8 @@ int hg_read_state(hg_domain *d, void *host_out) {
     const size_t fb = 19 * (size_t)d->n * elem_bytes(ctx->storage);
     int rc = ensure_scratch(ctx, std::max<size_t>(fb, 16));
     if (rc != HG_OK) return rc;
-    CU(ctx, launch_export_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, nullptr, ctx->scratch.p,
-                                ctx->stream));
+    CU(ctx, launch_export_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, (const int32_t *)d->canon_of.p,
+                                ctx->scratch.p, ctx->stream));
     if (fb) CU(ctx, cudaMemcpyAsync(host_out, ctx->scratch.p, fb, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     return HG_OK;
@@ -1576,8 +1755,8 @@ int hg_load_state(hg_domain *d, const void *buf, int64_t bytes) {
     CU(ctx, cudaMemcpyAsync((int64_t *)ctx->steps.p + d->idx, &step, 8, cudaMemcpyHostToDevice, ctx->stream));
     d->step = h.step;
     if (fb) CU(ctx, cudaMemcpyAsync(ctx->scratch.p, p, fb, cudaMemcpyHostToDevice, ctx->stream));
-    CU(ctx, launch_import_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, nullptr, ctx->scratch.p,
-                                ctx->stream));
+    CU(ctx, launch_import_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, (const int32_t *)d->canon_of.p,
+                                ctx->scratch.p, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     return HG_OK;
 }

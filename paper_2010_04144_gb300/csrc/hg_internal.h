@@ -121,18 +121,21 @@ cudaError_t launch_advance_list(int64_t *steps_base, const int32_t *idx, int n, 
 cudaError_t launch_guo_force(int storage, int scheme, const DomDev *doms, const int2 *fslots, int n,
                              int off, cudaStream_t st);
 // Reconstruct F_t of one domain (device order) and write macroscopic fields
-// (drho, ux, uy, uz) to out[perm ? perm[s] : s].
+// (drho, ux, uy, uz) to out[canon_of ? canon_of[s] : s] (device -> canonical index).
 cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                               const int64_t *canon_of, float4 *out, cudaStream_t st);
+                               const int32_t *canon_of, float4 *out, cudaStream_t st);
 // Raw state export/import of F_t in canonical order (storage type, [19][n]).
 cudaError_t launch_export_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int64_t *canon_of, void *out, cudaStream_t st);
+                                const int32_t *canon_of, void *out, cudaStream_t st);
 cudaError_t launch_import_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int64_t *canon_of, const void *in, cudaStream_t st);
-// Mass: FP64 partial sums over fixed chunks of the stored values, then a
-// fixed-order final sum.  partials needs mass_partials_needed(n) doubles.
+                                const int32_t *canon_of, const void *in, cudaStream_t st);
+// Mass check: FP64 partial sums of F_t over fixed chunks of 8192 sites in
+// canonical order, each site's values in direction order (dev_of: canonical ->
+// device index, null = identity), then a fixed-order final sum.  Each partial
+// also counts the non-finite values (NaN/Inf watchdog).  partials needs
+// mass_partials_needed(n) entries; out receives (mass, non-finite count).
 int64_t mass_partials_needed(int64_t n);
-cudaError_t launch_mass(int storage, const DomDev *dom_dev, int64_t n, int64_t np,
-                        double *partials, double *out, cudaStream_t st);
+cudaError_t launch_mass(int storage, int scheme, const DomDev *dom_dev, int64_t n, const int32_t *dev_of,
+                        double2 *partials, double2 *out, cudaStream_t st);
 
 }  // namespace hg

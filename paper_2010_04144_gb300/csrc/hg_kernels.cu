@@ -282,7 +282,7 @@ __device__ __forceinline__ typename St<S>::T *stored_F_ptr(const DomDev &D, int6
 }
 
 template <int S, int SCHEME>
-__global__ void k_macroscopic(const DomDev *__restrict__ dd, int64_t n, const int64_t *canon_of,
+__global__ void k_macroscopic(const DomDev *__restrict__ dd, int64_t n, const int32_t *canon_of,
                               float4 *out) {
     using Tr = St<S>;
     const DomDev D = *dd;
@@ -308,7 +308,7 @@ __global__ void k_macroscopic(const DomDev *__restrict__ dd, int64_t n, const in
 }
 
 template <int S, int SCHEME>
-__global__ void k_export_state(const DomDev *__restrict__ dd, int64_t n, const int64_t *canon_of,
+__global__ void k_export_state(const DomDev *__restrict__ dd, int64_t n, const int32_t *canon_of,
                                typename St<S>::T *out) {
     const DomDev D = *dd;
     const int64_t t = *D.step;
@@ -323,7 +323,7 @@ __global__ void k_export_state(const DomDev *__restrict__ dd, int64_t n, const i
 }
 
 template <int S, int SCHEME>
-__global__ void k_import_state(const DomDev *__restrict__ dd, int64_t n, const int64_t *canon_of,
+__global__ void k_import_state(const DomDev *__restrict__ dd, int64_t n, const int32_t *canon_of,
                                const typename St<S>::T *in) {
     const DomDev D = *dd;
     const int64_t t = *D.step;
@@ -340,30 +340,44 @@ __global__ void k_import_state(const DomDev *__restrict__ dd, int64_t n, const i
 constexpr int kMassChunk = 8192;
 constexpr int kMassThreads = 256;
 
-template <int S>
+// Block b sums F_t of canonical sites [8192 b, 8192 (b+1)) in FP64, each site's
+// 19 values in direction order 0..18 wherever the scheme keeps them (thread t
+// takes every 256th site, then a fixed shuffle tree), reading each site at its
+// device index, and counts the values that are not finite.  The sum is a
+// function of the state F_t alone: the same bits for A/B and AA and for every
+// device ordering.  Explicit rounding intrinsics keep every operation's order
+// fixed against compiler contraction.
+template <int S, int SCHEME>
 __global__ void __launch_bounds__(kMassThreads) k_mass_partials(const DomDev *__restrict__ dd,
-                                                                int64_t n, double *partials) {
-    using T = typename St<S>::T;
+                                                                int64_t n, const int32_t *dev_of,
+                                                                double2 *partials) {
     const DomDev D = *dd;
     const int64_t t = *D.step;
-    const T *buf = (const T *)D.f[(D.f[1] != nullptr) ? (t & 1) : 0];
     const int64_t lo = (int64_t)blockIdx.x * kMassChunk;
     const int64_t hi = lo + kMassChunk < n ? lo + kMassChunk : n;
     double a = 0.0, b = 0.0;
-    for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
-#pragma unroll
-        for (int i = 0; i < 19; ++i) a += St<S>::ldd(buf[(int64_t)i * D.np + s], i);
+    for (int64_t c = lo + threadIdx.x; c < hi; c += blockDim.x) {
+        const int64_t s = dev_of ? (int64_t)dev_of[c] : c;
+        unroll<0, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            const double v = St<S>::ldd(stored_F<S, SCHEME, I>(D, t, s), I);
+            a = __dadd_rn(a, v);
+            if (!isfinite(v)) b = __dadd_rn(b, 1.0);
+        });
     }
     block_sum2(a, b);
-    if (threadIdx.x == 0) partials[blockIdx.x] = a;
+    if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(a, b);
 }
 
-__global__ void __launch_bounds__(kMassThreads) k_mass_final(const double *partials, int64_t np_,
-                                                             double *out) {
+__global__ void __launch_bounds__(kMassThreads) k_mass_final(const double2 *partials, int64_t np_,
+                                                             double2 *out) {
     double a = 0.0, b = 0.0;
-    for (int64_t j = threadIdx.x; j < np_; j += blockDim.x) a += partials[j];
+    for (int64_t j = threadIdx.x; j < np_; j += blockDim.x) {
+        a = __dadd_rn(a, partials[j].x);
+        b = __dadd_rn(b, partials[j].y);
+    }
     block_sum2(a, b);
-    if (threadIdx.x == 0) *out = a;
+    if (threadIdx.x == 0) *out = make_double2(a, b);
 }
 
 inline unsigned rb_grid(int64_t n) {
@@ -420,7 +434,7 @@ cudaError_t launch_guo_force(int storage, int scheme, const DomDev *doms, const 
 }
 
 cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                               const int64_t *canon_of, float4 *out, cudaStream_t st) {
+                               const int32_t *canon_of, float4 *out, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     HG_DISPATCH_SS(storage, scheme,
                    (k_macroscopic<S_, C_><<<rb_grid(n), 256, 0, st>>>(dom_dev, n, canon_of, out)));
@@ -428,7 +442,7 @@ cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, i
 }
 
 cudaError_t launch_export_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int64_t *canon_of, void *out, cudaStream_t st) {
+                                const int32_t *canon_of, void *out, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     HG_DISPATCH_SS(storage, scheme,
                    (k_export_state<S_, C_><<<rb_grid(n), 256, 0, st>>>(
@@ -437,7 +451,7 @@ cudaError_t launch_export_state(int storage, int scheme, const DomDev *dom_dev, 
 }
 
 cudaError_t launch_import_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int64_t *canon_of, const void *in, cudaStream_t st) {
+                                const int32_t *canon_of, const void *in, cudaStream_t st) {
     if (n <= 0) return cudaSuccess;
     HG_DISPATCH_SS(storage, scheme,
                    (k_import_state<S_, C_><<<rb_grid(n), 256, 0, st>>>(
@@ -447,15 +461,14 @@ cudaError_t launch_import_state(int storage, int scheme, const DomDev *dom_dev, 
 
 int64_t mass_partials_needed(int64_t n) { return n > 0 ? (n + kMassChunk - 1) / kMassChunk : 1; }
 
-cudaError_t launch_mass(int storage, const DomDev *dom_dev, int64_t n, int64_t /*np*/,
-                        double *partials, double *out, cudaStream_t st) {
+cudaError_t launch_mass(int storage, int scheme, const DomDev *dom_dev, int64_t n, const int32_t *dev_of,
+                        double2 *partials, double2 *out, cudaStream_t st) {
     const int64_t P = mass_partials_needed(n);
     if (n <= 0) {
-        return cudaMemsetAsync(out, 0, sizeof(double), st);
+        return cudaMemsetAsync(out, 0, sizeof(double2), st);
     }
-    if (storage == kF32) k_mass_partials<kF32><<<(unsigned)P, kMassThreads, 0, st>>>(dom_dev, n, partials);
-    else if (storage == kF16) k_mass_partials<kF16><<<(unsigned)P, kMassThreads, 0, st>>>(dom_dev, n, partials);
-    else k_mass_partials<kBF16><<<(unsigned)P, kMassThreads, 0, st>>>(dom_dev, n, partials);
+    HG_DISPATCH_SS(storage, scheme,
+                   (k_mass_partials<S_, C_><<<(unsigned)P, kMassThreads, 0, st>>>(dom_dev, n, dev_of, partials)));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     k_mass_final<<<1, kMassThreads, 0, st>>>(partials, P, out);

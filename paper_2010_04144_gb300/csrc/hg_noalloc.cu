@@ -42,8 +42,8 @@ __device__ __forceinline__ double weight_d(int i) {
 
 template <int S> __device__ __forceinline__ double load_dev(const void *f, int64_t idx, int i) {
     if (S == HG_STORE_F32) return (double)((const float *)f)[idx];
-    if (S == HG_STORE_F16) return (double)__half2float(((const __half *)f)[idx]) * weight_d(i);
-    return (double)__bfloat162float(((const __nv_bfloat16 *)f)[idx]) * weight_d(i);
+    if (S == HG_STORE_F16) return __dmul_rn((double)__half2float(((const __half *)f)[idx]), weight_d(i));
+    return __dmul_rn((double)__bfloat162float(((const __nv_bfloat16 *)f)[idx]), weight_d(i));
 }
 
 __device__ __forceinline__ double block_sum(double a) {
@@ -61,8 +61,9 @@ __device__ __forceinline__ double block_sum(double a) {
     return a;
 }
 
-// Same partition and order as the context's mass reduction: block b sums the
-// 19 rows of sites [b*8192, (b+1)*8192) in FP64, thread t taking every 256th site.
+// Same partition, order and rounding as the context's mass reduction: block b
+// sums the 19 rows of sites [b*8192, (b+1)*8192) in FP64, thread t taking every
+// 256th site, with explicit rounding intrinsics (no contraction).
 template <int S>
 __global__ void __launch_bounds__(kThreads) k_mass_partials_static(const void *f, int64_t n,
                                                                    int64_t stride,
@@ -72,7 +73,7 @@ __global__ void __launch_bounds__(kThreads) k_mass_partials_static(const void *f
     double a = 0.0;
     for (int64_t s = lo + threadIdx.x; s < hi; s += blockDim.x) {
 #pragma unroll
-        for (int i = 0; i < 19; ++i) a += load_dev<S>(f, (int64_t)i * stride + s, i);
+        for (int i = 0; i < 19; ++i) a = __dadd_rn(a, load_dev<S>(f, (int64_t)i * stride + s, i));
     }
     a = block_sum(a);
     if (threadIdx.x == 0) partials[blockIdx.x] = a;
@@ -81,12 +82,14 @@ __global__ void __launch_bounds__(kThreads) k_mass_partials_static(const void *f
 __global__ void __launch_bounds__(kThreads) k_mass_final_static(const double *partials,
                                                                 int64_t count, double *out) {
     double a = 0.0;
-    for (int64_t j = threadIdx.x; j < count; j += blockDim.x) a += partials[j];
+    for (int64_t j = threadIdx.x; j < count; j += blockDim.x) a = __dadd_rn(a, partials[j]);
     a = block_sum(a);
     if (threadIdx.x == 0) *out = a;
 }
 
-// Device address of the scratch array for the current device, looked up once.
+// Device address of the scratch array for the current device, looked up once
+// and kept: it is valid for the primary context that existed at the lookup, so
+// a process that resets the device must not call this entry point afterwards.
 cudaError_t scratch_for_current_device(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);

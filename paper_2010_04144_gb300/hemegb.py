@@ -22,6 +22,8 @@ HG_OK, HG_ERR_ARG, HG_ERR_OOM, HG_ERR_CUDA, HG_ERR_TIMEOUT, HG_ERR_STATE = 0, -1
 STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 SCHEME = {"ab": 0, "aa": 1}
 COUPLE = {"forward": 0, "alternate": 1}
+ORDER = {"morton": 0, "rows": 1, "bricks": 2}
+FAULT_ALLOC, FAULT_DEVICE_WAIT = 1, 2
 STORE_DTYPE = {0: np.float32, 1: np.float16, 2: None}  # bf16 is returned as uint16 bits
 
 
@@ -92,6 +94,9 @@ _SIGS = {
     "hg_ctx_set_launch": ([C.c_void_p, C.c_int32, C.c_int32, C.c_int32], C.c_int),
     "hg_mass_noalloc": ([C.c_void_p, C.c_int32, C.c_int64, C.c_int64, C.c_void_p, C.c_void_p],
                         C.c_int),
+    "hg_state_check": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hg_read_adjacent_moments": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hg_ctx_inject_fault": ([C.c_void_p, C.c_int32, C.c_int64], C.c_int),
 }
 
 
@@ -220,8 +225,13 @@ class Context:
     def _ck(self, rc):
         _check(rc, self.h)
 
-    def domain(self, xyz, iolets, tau=0.8):
-        return Domain(self, xyz, iolets, tau)
+    def domain(self, xyz, iolets, tau=0.8, ordering="morton"):
+        return Domain(self, xyz, iolets, tau, ordering)
+
+    def inject_fault(self, kind, arg=0):
+        """Host-side fault injection (FAULT_ALLOC: the arg-th next allocation fails;
+        FAULT_DEVICE_WAIT: the device error word is set, hg_sync then reports a timeout)."""
+        self._ck(lib().hg_ctx_inject_fault(self.h, int(kind), int(arg)))
 
     def couple(self, src, dst, pairs):
         arr = (hg_pair * max(1, len(pairs)))()
@@ -275,12 +285,14 @@ class Context:
 
 
 class Domain:
-    def __init__(self, ctx: Context, xyz, iolets, tau=0.8):
+    def __init__(self, ctx: Context, xyz, iolets, tau=0.8, ordering="morton"):
         self.ctx = ctx
         xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
         self._io = iolet_struct_array(iolets)
         lb = hg_lb_params()
-        lb.tau, lb.ordering = float(tau), 0
+        lb.tau = float(tau)
+        lb.ordering = ORDER[ordering] if isinstance(ordering, str) else int(ordering)
+        self.ordering = lb.ordering
         h = C.c_void_p()
         ctx._ck(lib().hg_domain_create(ctx.h, _p(xyz), xyz.shape[0], self._io, len(iolets),
                                        C.byref(lb), C.byref(h)))
@@ -342,6 +354,24 @@ class Domain:
         out = C.c_double()
         self.ctx._ck(lib().hg_mass(self.h, C.byref(out)))
         return out.value
+
+    def state_check(self):
+        """(mass, number of non-finite stored values, return code) -- HG_ERR_STATE when
+        the state holds a NaN or an Inf."""
+        m, bad = C.c_double(), C.c_int64()
+        rc = lib().hg_state_check(self.h, C.byref(m), C.byref(bad))
+        if rc not in (HG_OK, HG_ERR_STATE):
+            self.ctx._ck(rc)
+        return m.value, bad.value, rc
+
+    def adjacent_moments(self):
+        """Sites next to any iolet (canonical order) and the FP32 moments (drho, ux, uy, uz)
+        the last step's iolet means were taken over: (sites (m,) int64, moments (m, 4))."""
+        m = self.info()["n_adjacent"]
+        sites = np.zeros(max(1, m), np.int64)
+        mom = np.zeros((max(1, m), 4), np.float32)
+        self.ctx._ck(lib().hg_read_adjacent_moments(self.h, _p(sites), _p(mom)))
+        return sites[:m], mom[:m]
 
     def state(self):
         """Raw F_t, shape (19, n): float32, float16, or bf16 as uint16 bit patterns."""

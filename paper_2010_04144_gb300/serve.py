@@ -34,15 +34,38 @@ from . import hemegb as H
 _STATE_BYTES = {0: 4, 1: 2, 2: 2}
 
 
-def footprint_bytes(n_sites, storage, scheme, n_iolets=2):
-    """Estimated HBM bytes of one domain before it is built: distributions, neighbour
-    table, iolet mask and prefix per site; moments, link codes, link coefficients and
-    site index per boundary slot; per-iolet values."""
+def adjacent_bound(radius):
+    """Upper bound on the fluid sites with a link into one iolet opening of the given radius
+    (lattice units).  Such a site lies within sqrt(2) of a point of the opening, which is a
+    disc of that radius extended at most 2 units beyond the cut plane: the sites lie in a
+    cylinder of radius r + sqrt(2) and length 2 + 2 sqrt(2), and a convex body holds at most
+    as many lattice points as the volume of its dilation by sqrt(3)/2."""
+    return math.pi * (radius + 3.0) ** 2 * 7.0
+
+
+def footprint_bytes(n_sites, storage, scheme, n_iolets=2, iolet_radii=None, reordered=False):
+    """Upper bound on the HBM bytes of one domain before it is built: distributions,
+    neighbour table, iolet mask and prefix per site; moments, link codes, link coefficients
+    and site index per boundary slot (164 B) plus one list entry per (site, iolet) pair;
+    per-iolet values; the two site permutations of a reordered layout; and the 256-byte
+    rounding of each buffer.  With the iolet radii the boundary slots are bounded per iolet
+    (adjacent_bound); without them 5% of the sites is assumed."""
     np_ = max(128, (n_sites + 127) // 128 * 128)
     copies = 2 if scheme == H.SCHEME["ab"] else 1
-    per_site = 19 * _STATE_BYTES[storage] * copies + 72 + 0.25
-    adjacent = 0.05 * n_sites  # generous bound on sites next to iolets (164 B each)
-    return int(per_site * np_ + 164 * adjacent + 64 * n_iolets + 4 * 4096)
+    per_site = 19 * _STATE_BYTES[storage] * copies + 72 + 0.25 + (8 if reordered else 0)
+    if iolet_radii is not None:
+        pairs = min(18 * n_sites, sum(adjacent_bound(r) for r in iolet_radii))
+        adjacent = min(n_sites, pairs)
+        n_iolets = len(iolet_radii)
+    else:
+        adjacent = pairs = 0.05 * n_sites
+    return int(per_site * np_ + 164 * adjacent + 4 * pairs + 64 * n_iolets + 16 * 256 + 4 * 4096)
+
+
+def geometry_footprint(geo, storage, scheme, reordered=False):
+    """footprint_bytes of a seeded geometry, with its iolets' radii."""
+    return footprint_bytes(geo.n, storage, scheme, iolet_radii=[io.radius / 1024.0 for io in geo.iolets],
+                           reordered=reordered)
 
 
 @dataclass
@@ -96,6 +119,10 @@ class Server:
         self.building: list[tuple[Job, object]] = []   # (job, future) in admission order
         self.active: list[Job] = []
         self.finished: list[Job] = []
+        self.failed: list[Job] = []       # requests whose build failed (result holds the error)
+        self.estimate_exceeded = 0        # built domains larger than their footprint estimate
+        self.max_overshoot_bytes = 0
+        self._now = None
         self.in_use = 0
         self.peak_in_use = 0
         self.admit_order: list[int] = []
@@ -116,7 +143,7 @@ class Server:
     def submit(self, job: Job):
         if job.steps % self.chunk:
             raise ValueError("a request's step count must be a multiple of the tick size")
-        need = sum(footprint_bytes(g.n, self.storage, self.scheme, len(g.iolets)) for g in job.geoms)
+        need = self._estimate(job)
         if need > self.budget:
             raise ValueError(f"request {job.rid} needs {need / 1e9:.1f} GB, above the budget")
         self.queue.append(job)
@@ -139,7 +166,7 @@ class Server:
         return False
 
     def _estimate(self, job):
-        return sum(footprint_bytes(g.n, self.storage, self.scheme, len(g.iolets)) for g in job.geoms)
+        return sum(geometry_footprint(g, self.storage, self.scheme) for g in job.geoms)
 
     def _build(self, job):
         """Host build and upload of a job's domains (worker thread; touches no server state)."""
@@ -233,12 +260,17 @@ class Server:
                 for d in doms:
                     d.destroy()
                 self.in_use -= job.bytes
-                if err is not None:
-                    raise err
+                if err is not None:  # this request fails alone; the server keeps serving
+                    job.result = {"error": f"{type(err).__name__}: {err}"}
+                    job.finished_s = self._now() if self._now else math.nan
+                    self.failed.append(job)
                 continue
             self.in_use -= job.bytes
             job.domains = doms
-            job.bytes = sum(d.info()["device_bytes"] for d in doms)
+            estimate, job.bytes = job.bytes, sum(d.info()["device_bytes"] for d in doms)
+            if job.bytes > estimate:  # counted; admissions wait until in_use is back in budget
+                self.estimate_exceeded += 1
+                self.max_overshoot_bytes = max(self.max_overshoot_bytes, job.bytes - estimate)
             self.in_use += job.bytes
             self.peak_in_use = max(self.peak_in_use, self.in_use)
             job.start_tick = self.ticks
@@ -268,6 +300,7 @@ class Server:
     def run(self, clock=time.perf_counter, sleep=time.sleep, max_ticks=None):
         """Serve every submitted job; returns the finished jobs."""
         t0 = clock()
+        self._now = lambda: clock() - t0
         self.queue.sort(key=lambda j: (j.arrival_s, j.rid))
         while self.queue or self.active or self.building:
             self._activate()
@@ -307,7 +340,8 @@ class Server:
                "elapsed_s": getattr(self, "elapsed_s", float("nan")),
                "aggregate_mflups": self.site_steps / max(getattr(self, "elapsed_s", 1e-9), 1e-9) / 1e6,
                "peak_hbm_gb": self.peak_in_use / 1e9, "build_s": self.build_s,
-               "policy": self.policy, "backfilled": self.backfilled,
+               "policy": self.policy, "backfilled": self.backfilled, "failed": len(self.failed),
+               "estimate_exceeded": self.estimate_exceeded,
                "gpu_wait_s": self.wait_s, "idle_s": self.idle_s}
         if ttr.size:
             out.update(p50_s=float(np.percentile(ttr, 50)), p99_s=float(np.percentile(ttr, 99)),

@@ -97,7 +97,12 @@ def test_plane_cuts_separate_vessels():
     assert rows.shape[0] == 9                                  # 3 planes x 3 tubes
     x, y = np.meshgrid(np.arange(-5, 6), np.arange(-5, 6))
     disc = np.stack([x.ravel(), y.ravel()], 1)[(x ** 2 + y ** 2).ravel() <= 25]
-    assert np.allclose(rows[:, 2], A._hull_area(disc))         # each cut: one lattice disc
+    assert np.allclose(rows[:, 2], A._cell_hull_area(disc))    # each cut: one lattice disc
+    from scipy.spatial import ConvexHull
+
+    corners = np.concatenate([disc + d for d in ((-.5, -.5), (-.5, .5), (.5, -.5), (.5, .5))])
+    assert abs(A._cell_hull_area(disc) - ConvexHull(corners).volume) < 1e-9
+    assert A._cell_hull_area(disc) >= disc.shape[0] > A._hull_area(disc)
     assert np.allclose(rows[:, 3], 0.25) and np.all(rows[:, 4] == disc.shape[0])
     neg = A.velocity_vs_area_planes(fields, g.xyz, axis=2, arterial_negative=True)
     assert np.allclose(neg[:, 2], -rows[:, 2])
@@ -107,3 +112,21 @@ def test_plane_cuts_separate_vessels():
     for f in (0.25, 0.5, 0.75):
         level = int(round(t.xyz[:, ax].min() + f * (t.xyz[:, ax].max() - t.xyz[:, ax].min())))
         assert rt[rt[:, 0] == f, 4].sum() == np.sum(t.xyz[:, ax] == level)   # every site in a vessel
+
+
+def test_thin_vessels_have_consistent_areas():
+    """A vessel one site wide has the area of its sites, whatever their number; a square
+    block of sites has its full area; no cut yields a zero area."""
+    for k in range(1, 8):
+        line = np.stack([np.arange(k), np.zeros(k, int)], 1)
+        assert A._cell_hull_area(line) == float(k)
+        assert A._cell_hull_area(line[:, ::-1]) == float(k)
+    block = np.stack(np.meshgrid(np.arange(3), np.arange(3)), -1).reshape(-1, 2)
+    assert A._cell_hull_area(block) == 9.0
+    # a plane cut through a one-voxel-wide straight vessel next to a wide one
+    thin = np.stack([np.full(6, 3), np.full(6, 3), np.arange(6)], 1)
+    wide = S.cylinder(radius=3, length=6, margin=10).xyz
+    xyz = np.concatenate([thin, wide]).astype(np.int32)
+    rows = A.velocity_vs_area_planes(np.ones((xyz.shape[0], 4)), xyz, axis=2)
+    assert np.all(rows[:, 2] > 0)
+    assert sorted(set(rows[:, 4].astype(int))) == [1, 29]

@@ -4,9 +4,11 @@ Some callers cannot call cudaMalloc: an application whose own memory pool
 already owns the whole device heap, or a monitoring thread that must not
 stall the solver with an allocation.  hg_mass_noalloc keeps its scratch in a
 fixed array inside the library; this test checks, through the C ABI, that it
-returns what the regular hg_mass returns for the same state, on two calls in
-a row (the second call must not be disturbed by what the first left in the
-shared scratch array).  The file name makes pytest collect it last.
+returns exactly what the regular hg_mass returns for the same state (same
+partition, same summation order), on two calls in a row (the second call must
+not be disturbed by what the first left in the shared scratch array), for a
+dense copy on the legacy stream and for a copy with padded rows (garbage in
+the padding) on a caller's stream.  The file name makes pytest collect it last.
 """
 import ctypes as C
 
@@ -29,22 +31,38 @@ def test_mass_noalloc_matches_mass(gpu, storage):
         ctx.step(40)
         raw = d.state()                     # (19, n) raw storage values, canonical order
         ref = d.mass()                      # regular entry point
-        dev = torch.from_numpy(raw.view(np.int32 if raw.itemsize == 4 else np.int16).copy()).cuda()
-        out = torch.zeros(2, dtype=torch.float64, device="cuda")
+        assert ref != 0.0
+        n = d.n
+        bits = raw.view(np.int32 if raw.itemsize == 4 else np.int16)
+        dense = torch.from_numpy(bits.copy()).cuda()
+        stride = (n + 127) // 128 * 128
+        padded_h = np.full((19, stride), -12345, bits.dtype)   # non-zero garbage in the padding
+        padded_h[:, :n] = bits
+        padded = torch.from_numpy(padded_h).cuda()
         code = gpu.STORAGE[storage]
         L = gpu.lib()
-        for k in range(2):
-            rc = L.hg_mass_noalloc(C.c_void_p(dev.data_ptr()), code, d.n, d.n,
+        out = torch.zeros(4, dtype=torch.float64, device="cuda")
+        for k in range(2):                  # legacy default stream, dense rows
+            rc = L.hg_mass_noalloc(C.c_void_p(dense.data_ptr()), code, n, n,
                                    C.c_void_p(out.data_ptr() + 8 * k), None)
             assert rc == gpu.HG_OK
         torch.cuda.synchronize()
+        side = torch.cuda.Stream()
+        side.wait_stream(torch.cuda.current_stream())
+        for k in range(2, 4):               # a caller's stream, padded rows
+            rc = L.hg_mass_noalloc(C.c_void_p(padded.data_ptr()), code, n, stride,
+                                   C.c_void_p(out.data_ptr() + 8 * k), C.c_void_p(side.cuda_stream))
+            assert rc == gpu.HG_OK
+        side.synchronize()
         got = out.cpu().numpy()
-        for k in range(2):
-            assert abs(got[k] - ref) <= 1e-12 * max(1.0, abs(ref)), (k, got[k], ref)
-        assert ref != 0.0
+        for k in range(4):
+            assert got[k] == ref, (k, got[k], ref)
         # sizes beyond the fixed scratch are refused with HG_ERR_ARG
-        rc = L.hg_mass_noalloc(C.c_void_p(dev.data_ptr()), code, 16384 * 8192 + 1,
+        rc = L.hg_mass_noalloc(C.c_void_p(dense.data_ptr()), code, 16384 * 8192 + 1,
                                16384 * 8192 + 1, C.c_void_p(out.data_ptr()), None)
         assert rc == gpu.HG_ERR_ARG
+        rc = L.hg_mass_noalloc(C.c_void_p(dense.data_ptr()), code, n, n - 1,
+                               C.c_void_p(out.data_ptr()), None)
+        assert rc == gpu.HG_ERR_ARG         # rows shorter than the site count
     finally:
         ctx.close()
