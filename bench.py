@@ -36,6 +36,9 @@ METRIC = "MFLUPS (D3Q19 LBGK site updates per second / 1e6), whole hot path per 
 MIN_TIMED_S = 1.0
 FALLBACK_HBM_GBS = 6800.0
 
+# device site orderings the autotuner tries (every one gives bit-identical results)
+ORDERINGS = ("morton", "rows", "bricks")
+
 # algorithmic bytes per site update of the stream-collide kernel
 BYTES_PER_UPDATE = {
     ("f32", "ab"): 19 * 4 * 2 + 18 * 4,        # 224
@@ -131,15 +134,17 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def profiled_traffic(variant_key, launch):
-    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel build."""
+def profiled_traffic(variant_key, launch, ordering="morton"):
+    """DRAM bytes per launch from the committed ncu summary, if it matches this kernel build,
+    launch shape and site ordering."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             t = json.load(f)
         entries = t.get(variant_key) or []
         for e in entries if isinstance(entries, list) else [entries]:  # one record per launch shape
-            if e.get("launch") == launch and e.get("kernel_source_sha") == kernel_source_sha():
+            if (e.get("launch") == launch and e.get("kernel_source_sha") == kernel_source_sha()
+                    and e.get("ordering", "morton") == ordering):
                 return e["bytes_per_launch"], e.get("scaled_from")
     except Exception:
         pass
@@ -199,19 +204,34 @@ def whole_job_mflups(sites_per_rank, world_size, steps, max_ms):
     return sites_per_rank * world_size * steps / (max_ms / 1e3) / 1e6
 
 
-def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, launch=None):
-    """Autotuned (or given) launch shape, device-timed steps (graphs), per-kernel times, e2e job."""
+def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, launch=None,
+                 orderings=ORDERINGS):
+    """Autotuned (or given) site ordering and launch shape, device-timed steps (graphs),
+    per-kernel times, e2e job."""
     import torch
 
-    from paper_2010_04144_gb300.autotune import autotune
+    from paper_2010_04144_gb300.autotune import autotune, tune_ordering
 
+    nvtx = torch.cuda.nvtx
+    tag = f"{storage}:{scheme}"
+    order_ms = {}
+    if launch is None and len(orderings) > 1:
+        def make(o):
+            c = H.Context(device=device, storage=storage, scheme=scheme)
+            c.domain(geo.xyz, geo.iolets, tau=0.8, ordering=o)
+            return c
+
+        nvtx.range_push(f"{tag}-ordering")
+        ordering, _, table = tune_ordering(make, orderings)
+        order_ms = {o: round(v[1], 4) for o, v in table.items()}
+        nvtx.range_pop()
+    else:
+        ordering = orderings[0]
     ctx = H.Context(device=device, storage=storage, scheme=scheme)
     try:
-        d = ctx.domain(geo.xyz, geo.iolets, tau=0.8)
+        d = ctx.domain(geo.xyz, geo.iolets, tau=0.8, ordering=ordering)
         n = d.n
         st = ctx.stream
-        nvtx = torch.cuda.nvtx
-        tag = f"{storage}:{scheme}"
         nvtx.range_push(f"{tag}-autotune")
         if launch is None:
             best, timing = autotune(ctx)
@@ -265,7 +285,7 @@ def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, 
         gs = 16
         launches = steps * (1 + (1 if geo.iolets else 0)) + (steps + gs - 1) // gs
         return dict(n=n, ms=ms, reps=len(reps), timed_s=total / 1e3, ms_sc=ms_sc, ms_io=ms_io,
-                    e2e_s=e2e_s, h2d=int(state.size),
+                    ordering=ordering, ordering_ms=order_ms, e2e_s=e2e_s, h2d=int(state.size),
                     d2h=int(n * 16), launches=launches, device_bytes=d.info()["device_bytes"],
                     launch={"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]},
                     tuning_ms={f"{b}x{t}v{v}": round(x, 4) for (b, t, v), x in timing.items()})
@@ -505,6 +525,54 @@ def run_coupled(args, H, device):
         ctx.close()
 
 
+def run_split(args, H, device):
+    """Split domain (Section 2.2 decomposition, halo exchange every step) on one device:
+    the whole hot path plus the pack / copy / unpack of the crossing populations, against
+    the same domain unsplit; results are bit-identical, so only the time differs."""
+    import torch
+
+    from paper_2010_04144_gb300.autotune import autotune
+
+    geo, cfg = workload(scale=args.scale)
+    rows = []
+    launch = None
+    for k in [0] + [int(x) for x in args.parts.split(",")]:
+        ctx = H.Context(device=device, storage="f32", scheme="ab")
+        try:
+            if k == 0:
+                obj = ctx.domain(geo.xyz, geo.iolets)
+                launch, _ = autotune(ctx)
+            else:
+                obj = ctx.split(geo.xyz, geo.iolets, k, boundary_weight=args.boundary_weight)
+                ctx.set_launch(*launch)
+            obj.step(args.warmup) if k else ctx.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(ctx.stream)
+            obj.step(args.steps) if k else ctx.step(args.steps)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / args.steps
+            halo = sum(obj.info(p)["halo_in"] for p in range(k)) if k else 0
+            ghosts = sum(obj.info(p)["ghosts"] for p in range(k)) if k else 0
+            rows.append({"parts": k, "ms_per_step": ms, "mflups": geo.n / (ms / 1e3) / 1e6,
+                         "halo_values_per_step": halo, "ghost_sites": ghosts})
+        finally:
+            ctx.close()
+    base = rows[0]["ms_per_step"]
+    for r in rows:
+        r["time_vs_unsplit"] = r["ms_per_step"] / base
+    line = {"metric": METRIC, "value": rows[-1]["mflups"], "unit": "MFLUPS", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic (seeded tree geometry, rest initial state)",
+            "config": {**cfg, "steps_per_job": args.steps, "storage": "f32", "scheme": "ab",
+                       "launch": list(launch), "split": "contiguous Morton ranges, halo pack/copy/unpack "
+                                                        "per step on one device",
+                       "boundary_weight": args.boundary_weight},
+            "split": rows}
+    print(json.dumps(line))
+
+
 def run_precision(args, H, device):
     """FP32 vs FP16 vs BF16 storage: throughput on the large tree, error vs the FP64 oracle."""
     import torch
@@ -578,7 +646,10 @@ def main():
                     help="storage:scheme list; append @BLOCKxSPTvVARIANT to fix a launch shape")
     ap.add_argument("--headline", default="f32:best")
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve"])
+    ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve", "split"])
+    ap.add_argument("--parts", default="2,4,8", help="split config: partition counts to time")
+    ap.add_argument("--boundary-weight", type=float, default=1.0,
+                    help="split config: load-balancing cost of a site next to an iolet")
     ap.add_argument("--coupled-scale", type=float, default=2.12)
     ap.add_argument("--coupled-scheme", default="ab")
     ap.add_argument("--coupled-settle", type=int, default=4000,
@@ -614,7 +685,8 @@ def main():
 
         H.lib()
         torch.cuda.set_device(0)
-        return {"coupled": run_coupled, "precision": run_precision, "serve": run_serve}[args.config](args, H, 0)
+        return {"coupled": run_coupled, "precision": run_precision, "serve": run_serve,
+                "split": run_split}[args.config](args, H, 0)
 
     import torch
 
@@ -629,19 +701,20 @@ def main():
     peak, peak_kind = hbm_peak()
     variants = []
     for v in args.variants.split(","):  # "storage:scheme", optionally "@BLOCKxSPTvVARIANT" (no tuning)
-        form, _, shape = v.partition("@")
+        form, _, shape = v.partition("@")  # and "/ORDERING" after the shape (no ordering tuning)
+        shape, _, order = shape.partition("/")
         launch = None
         if shape:
             b, rest = shape.split("x")
             spt, var = rest.split("v")
             launch = (int(b), int(spt), int(var))
-        variants.append((*form.split(":"), launch))
+        variants.append((*form.split(":"), launch, (order,) if order else ORDERINGS))
     results = {}
     sampler = ClockSampler(device).start()
     try:
-        for (storage, scheme, launch) in variants:
+        for (storage, scheme, launch, orders) in variants:
             r = time_variant(H, geo, storage, scheme, args.steps, args.warmup, dist, device, sampler,
-                             launch=launch)
+                             launch=launch, orderings=orders if launch is None else (orders[0],))
             B = BYTES_PER_UPDATE[(storage, scheme)]
             r["mflups"] = r["n"] * ws * args.steps / (r["ms"] / 1e3) / 1e6
             r["achieved_gbs"] = B * r["n"] / (r["ms_sc"] / args.steps / 1e3) / 1e9
@@ -658,7 +731,7 @@ def main():
     total_sites = h["n"] * ws
     value = whole_job_mflups(h["n"], ws, args.steps, h["ms"])
     e2e_value = total_sites * args.steps / h["e2e_s"] / 1e6
-    traffic, scaled_from = profiled_traffic(f"{head[0]}:{head[1]}", h["launch"])
+    traffic, scaled_from = profiled_traffic(f"{head[0]}:{head[1]}", h["launch"], h["ordering"])
     line = {
         "metric": METRIC,
         "value": value, "unit": "MFLUPS", "n_gpus": ws, "steps": args.steps,
@@ -666,6 +739,7 @@ def main():
         "scaling": "weak", "vs_baseline": None, "dtype": DTYPE_NAME[head[0]],
         "data": "synthetic (seeded tree geometry, rest initial state)",
         "config": {**cfg, "storage": head[0], "scheme": head[1], "launch": h["launch"],
+                   "ordering": h["ordering"],
                    "timing": f"median of {h['reps']} back-to-back {args.steps}-step measurements "
                              f"({h['timed_s']:.2f} s of device time)",
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
@@ -688,7 +762,8 @@ def main():
                                    "bytes_per_update": r["bytes_per_update"],
                                    "stream_collide_ms": r["ms_sc"] / args.steps,
                                    "iolet_update_ms": r["ms_io"] / args.steps,
-                                   "launch": r["launch"], "tuning_ms": r["tuning_ms"],
+                                   "launch": r["launch"], "ordering": r["ordering"],
+                                   "ordering_ms": r["ordering_ms"], "tuning_ms": r["tuning_ms"],
                                    "device_bytes": r["device_bytes"]}
                      for (s, c), r in results.items()},
     }

@@ -91,6 +91,7 @@ extern "C" {
 
 typedef struct hg_ctx hg_ctx;
 typedef struct hg_domain hg_domain;
+typedef struct hg_split hg_split;
 
 /* Device allocator hook: returns a device pointer of at least `bytes` bytes
  * (256-byte aligned) or NULL; `free` receives the pointer and size. */
@@ -273,7 +274,8 @@ int hg_coupling_factors(const int64_t *art_centres, const double *art_areas, int
 
 /* ---- stepping ---- */
 
-/* Advance every domain of the context by n_steps LB steps.  Step t streams the
+/* Advance every domain of the context by n_steps LB steps (split domains are
+ * advanced by hg_split_step).  Step t streams the
  * post-collision state F_{t-1} (pull from x - c_i; wall, pressure and velocity
  * rules on non-fluid links, with boundary values of time t), collides (LBGK,
  * tau) into F_t, then reduces the iolet means of time t in FP64 and sets the
@@ -389,6 +391,70 @@ int hg_read_adjacent_moments(hg_domain *d, int64_t *sites_out, float *mom_out);
  * the next hg_sync returns HG_ERR_TIMEOUT.  Errors: HG_ERR_ARG, HG_ERR_CUDA.
  * Passage: infrastructure: no passage (failure detection). */
 int hg_ctx_inject_fault(hg_ctx *ctx, int32_t kind, int64_t arg);
+
+/* ---- split (partitioned) domains ----
+ * Section 2.2 decomposes the sparse domain over ranks and ends every step with a
+ * non-blocking exchange of the populations that cross the cuts; Section 2.2.1
+ * balances the cut.  A split domain cuts the canonical site list into n_parts
+ * contiguous ranges of equal cost (a site costs 1, a site with a link into an
+ * iolet opening costs boundary_weight); each partition holds its own
+ * distributions and neighbour table plus ghost copies of the sites it pulls
+ * from, and after every stream-collide the crossing values are packed per
+ * (sender, receiver) pair, copied into the receiver's buffer and unpacked into
+ * its ghosts.  Iolet means are reduced over the whole domain in canonical
+ * order, so a split run is bit-identical to the same domain unsplit.  All
+ * partitions of a split live on the context's device; the A/B scheme only; a
+ * split takes no part in coupling, and hg_step does not advance it. */
+typedef struct {
+    int32_t n_parts;        /* 1 <= n_parts <= min(n_fluid, 1024) */
+    int32_t reserved;
+    double boundary_weight; /* cost of a site next to an iolet relative to a bulk site (<= 0: 1) */
+} hg_split_params;
+
+/* Host only: the cut (first_out, n_parts + 1 canonical indices), the ghost
+ * count of every partition (ghosts_out, n_parts) and the halo values each pair
+ * exchanges per step (halo_out[q * n_parts + p]: values partition p pulls from
+ * partition q), for the same input hg_split_create takes.  Any output may be
+ * NULL.  Errors: HG_ERR_ARG.
+ * Passage: Section 2.2 (domain decomposition, neighbour exchange) and Section
+ * 2.2.1 (load balancing). */
+int hg_split_layout(const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets, int32_t n_iolets,
+                    const hg_split_params *sp, int64_t *first_out, int64_t *ghosts_out, int64_t *halo_out);
+
+/* Build a split domain (same inputs and checks as hg_domain_create; the context
+ * must use the A/B scheme; lb->ordering must be HG_ORDER_MORTON).  Errors:
+ * HG_ERR_ARG, HG_ERR_STATE (context full), HG_ERR_OOM, HG_ERR_CUDA.
+ * Passage: Section 2.2 and Section 2.2.1. */
+int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets, int32_t n_iolets,
+                    const hg_lb_params *lb, const hg_split_params *sp, hg_split **out);
+
+/* Free a split domain.
+ * Passage: infrastructure: no passage. */
+int hg_split_destroy(hg_split *s);
+
+/* Partition `part`: first canonical site, owned sites, ghost sites, halo values
+ * it receives per step.  Any out pointer may be NULL.
+ * Passage: Section 2.2 (decomposition). */
+int hg_split_info(hg_split *s, int32_t part, int64_t *first, int64_t *owned, int64_t *ghosts, int64_t *halo_in);
+
+/* Advance a split domain by n_steps (as hg_step, with the halo exchange after
+ * every stream-collide).  Asynchronous.
+ * Passage: Section 2 (the LB step) and Section 2.2 (neighbour exchange). */
+int hg_split_step(hg_split *s, int64_t n_steps);
+
+/* Read-back of a split domain, whole domain in canonical order, as the
+ * hg_read_macroscopic / hg_read_state / hg_read_iolet_stats /
+ * hg_read_boundary_values / hg_mass of an unsplit domain.  Synchronise.
+ * Passage: Section 2 (macroscopic fields) and Section 2.3 (iolet averages). */
+int hg_split_read_macroscopic(hg_split *s, float *out);
+/* Passage: infrastructure: no passage (raw state read-back). */
+int hg_split_read_state(hg_split *s, void *out);
+/* Passage: Section 2.3 (averaged iolet values). */
+int hg_split_read_iolet_stats(hg_split *s, double *out);
+/* Passage: Section 2 (iolet conditions). */
+int hg_split_read_boundary_values(hg_split *s, float *out);
+/* Passage: infrastructure: no passage (mass check). */
+int hg_split_mass(hg_split *s, double *out);
 
 /* ---- checkpoint / resume ---- */
 

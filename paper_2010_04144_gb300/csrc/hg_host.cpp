@@ -294,6 +294,36 @@ int device_order(const std::vector<int32_t> &xyz, int64_t n, int ordering, std::
     return HG_OK;
 }
 
+// Velocity-iolet link coefficient of link i of the site at xyz (Section 2: velocity
+// condition at inlets): 6 w_i c_i.u_w / U, u_w the inward profile velocity per unit
+// peak speed at the link midpoint x - c_i/2 (parabolic: peak on the axis, zero at
+// the radius; plug: uniform).  16-bit storage holds f~/w and collides on it, so
+// its coefficient drops w_i.  Zero for pressure iolets.
+float link_coef(const hg_iolet &io, const int32_t *xyz, int i, int storage) {
+    if (io.kind != HG_VELOCITY) return 0.0f;
+    const double an = std::sqrt((double)io.axis[0] * io.axis[0] + (double)io.axis[1] * io.axis[1] +
+                                (double)io.axis[2] * io.axis[2]);
+    const double ah[3] = {io.axis[0] / an, io.axis[1] / an, io.axis[2] / an};
+    double phi = 1.0;
+    if (io.profile == HG_PARABOLIC) {
+        double rel[3], along = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            rel[e] = (xyz[e] - 0.5 * kC[i][e]) - io.centre[e] / 1024.0;
+            along += rel[e] * ah[e];
+        }
+        double p2 = 0.0;
+        for (int e = 0; e < 3; ++e) {
+            const double t = rel[e] - along * ah[e];
+            p2 += t * t;
+        }
+        const double r = io.radius / 1024.0;
+        phi = r > 0 ? std::max(0.0, 1.0 - p2 / (r * r)) : 0.0;
+    }
+    const double cdot = -(kC[i][0] * ah[0] + kC[i][1] * ah[1] + kC[i][2] * ah[2]);
+    const double wi = storage == HG_STORE_F32 ? wgt(i) : 1.0;
+    return (float)(6.0 * wi * cdot * phi);
+}
+
 double pulse(int kind, double t, double period) {
     const double ph = kind == HG_PULSE_CONST ? 0.0 : std::fmod(t, period) / period;
     if (kind == HG_PULSE_COSINE) return 0.5 * (1.0 - std::cos(2.0 * 3.141592653589793 * ph));
@@ -317,6 +347,12 @@ struct PlanKey {
 struct Plan {
     std::vector<int32_t> doms;
     DevBuf tiles, ios, adv, chunks, partials, counters, rev, fslots;
+    // halo exchange of a split domain (after stream-collide, before the iolet update):
+    // pack into `send`, copy each (sender, receiver) block to `recv`, unpack
+    DevBuf halo_pack, halo_unpack, send, recv;
+    int64_t n_halo = 0;
+    int halo_elem = 4;
+    std::vector<std::pair<size_t, size_t>> halo_blocks;  // (byte offset, bytes) per partition pair
     DomDev one{};       // single-domain plans: the descriptor passed by value to stream-collide
     bool single = false;
     int64_t n_tiles = 0;
@@ -353,6 +389,32 @@ struct hg_ctx {
     DevBuf scratch;                 // mass partials, read-back staging
     std::atomic<int64_t> device_bytes{0};
     std::atomic<int64_t> fail_alloc_in{0};  // injected fault: the k-th next allocation fails (0 = none)
+    std::vector<hg_split *> splits;         // split domains (destroyed with the context)
+};
+
+// One partition of a split domain: a contiguous range of the canonical site list
+// (owned, device positions [0, n_own)) followed by its ghosts (sites of other
+// partitions it pulls from, [n_own, n_loc)), with its own distributions, neighbour
+// table (local indices) and iolet mask; boundary slots are numbered globally.
+struct SplitPart {
+    int32_t idx = -1;                  // context domain-table slot (descriptor, step counter)
+    int64_t first = 0, n_own = 0, n_loc = 0, np = 0;
+    std::vector<int64_t> ghosts;       // global canonical indices of the ghost sites
+    DevBuf f[2], nbr, iomask, ioprefix, gidx;  // gidx: local -> global canonical index
+    DomDev dev{};
+};
+
+struct hg_split {
+    hg_ctx *ctx = nullptr;
+    int64_t n = 0, n_adj = 0, step = 0;
+    int32_t nio = 0;
+    double tau = 0.8;
+    std::vector<hg_iolet> io;
+    std::vector<int32_t> io_ptr;
+    std::vector<SplitPart> parts;
+    std::vector<HaloDev> pack, unpack;              // grouped by (sender, receiver) pair
+    std::vector<std::pair<size_t, size_t>> blocks;  // element (offset, count) per pair
+    DevBuf bnd, io_codes, coef, slot_site, bcv, io_kind, M, slots, force;  // shared by the parts
 };
 
 struct hg_domain {
@@ -446,7 +508,8 @@ void drop_plans(hg_ctx *ctx) {
         Plan &p = *kv.second;
         for (auto &g : p.graph)
             if (g) cudaGraphExecDestroy(g);
-        for (DevBuf *b : {&p.tiles, &p.ios, &p.adv, &p.chunks, &p.partials, &p.counters, &p.rev, &p.fslots})
+        for (DevBuf *b : {&p.tiles, &p.ios, &p.adv, &p.chunks, &p.partials, &p.counters, &p.rev, &p.fslots,
+                          &p.halo_pack, &p.halo_unpack, &p.send, &p.recv})
             dev_free(ctx, *b);
     }
     ctx->plans.clear();
@@ -652,11 +715,13 @@ int hg_ctx_create(const hg_ctx_params *p, hg_ctx **out) {
 }
 
 int hg_domain_destroy(hg_domain *d);
+int hg_split_destroy(hg_split *sp);
 
 int hg_ctx_destroy(hg_ctx *ctx) {
     if (!ctx) return HG_ERR_ARG;
     cudaSetDevice(ctx->device);
     cudaStreamSynchronize(ctx->stream);
+    while (!ctx->splits.empty()) hg_split_destroy(ctx->splits.back());
     for (auto *d : ctx->doms)
         if (d) hg_domain_destroy(d);
     drop_plans(ctx);
@@ -827,32 +892,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         for (int i = 1; i < 19; ++i) {
             const int32_t v = nbr[(size_t)(i - 1) * np + q];
             if (v >= -1) continue;
-            const hg_iolet &io = iolets[-v - 2];
-            if (io.kind == HG_VELOCITY) {
-                const double an = std::sqrt((double)io.axis[0] * io.axis[0] +
-                                            (double)io.axis[1] * io.axis[1] +
-                                            (double)io.axis[2] * io.axis[2]);
-                const double ah[3] = {io.axis[0] / an, io.axis[1] / an, io.axis[2] / an};
-                double phi = 1.0;
-                if (io.profile == HG_PARABOLIC) {
-                    double rel[3], along = 0.0;
-                    for (int e = 0; e < 3; ++e) {
-                        rel[e] = (d->xyz[3 * c + e] - 0.5 * kC[i][e]) - io.centre[e] / 1024.0;
-                        along += rel[e] * ah[e];
-                    }
-                    double p2 = 0.0;
-                    for (int e = 0; e < 3; ++e) {
-                        const double t = rel[e] - along * ah[e];
-                        p2 += t * t;
-                    }
-                    const double r = io.radius / 1024.0;
-                    phi = r > 0 ? std::max(0.0, 1.0 - p2 / (r * r)) : 0.0;
-                }
-                const double cdot = -(kC[i][0] * ah[0] + kC[i][1] * ah[1] + kC[i][2] * ah[2]);
-                // 16-bit storage holds f~/w and collides on it: the coefficient drops w_i
-                const double wi = ctx->storage == HG_STORE_F32 ? wgt(i) : 1.0;
-                coef[(size_t)sl * 18 + (i - 1)] = (float)(6.0 * wi * cdot * phi);
-            }
+            coef[(size_t)sl * 18 + (i - 1)] = link_coef(iolets[-v - 2], &d->xyz[3 * c], i, ctx->storage);
         }
     }
     // per-32-site prefix counts of flagged sites: slot = rank of the site's flag
@@ -1360,6 +1400,27 @@ inline int step_parity(hg_ctx *ctx, int mode, int64_t off) {
     return (int)((mode + off + 1) & 1);  // 1 when the executed step is odd
 }
 
+// Halo exchange of a split domain after step offset `off`: every partition's F_t
+// values that another partition pulls are packed per (sender, receiver) pair,
+// each pair's block is copied into the receiver's buffer (on one device a plain
+// device-to-device copy; between devices this is the one transfer that changes),
+// and unpacked into the receiver's ghost positions.
+cudaError_t enqueue_halo(hg_ctx *ctx, Plan *p, int off) {
+    if (p->n_halo == 0) return cudaSuccess;
+    const DomDev *doms = (const DomDev *)ctx->dom_table.p;
+    const int64_t *steps = (const int64_t *)ctx->steps.p;
+    cudaError_t e = launch_halo_pack(p->halo_elem, doms, steps, (const HaloDev *)p->halo_pack.p, p->n_halo,
+                                     p->send.p, off, ctx->stream);
+    for (const auto &b : p->halo_blocks) {
+        if (e != cudaSuccess) return e;
+        e = cudaMemcpyAsync((char *)p->recv.p + b.first, (const char *)p->send.p + b.first, b.second,
+                            cudaMemcpyDeviceToDevice, ctx->stream);
+    }
+    if (e != cudaSuccess) return e;
+    return launch_halo_unpack(p->halo_elem, doms, steps, (const HaloDev *)p->halo_unpack.p, p->n_halo,
+                              p->recv.p, off, ctx->stream);
+}
+
 cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
     CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
     for (int64_t off = 0; off < k; ++off) {
@@ -1373,6 +1434,8 @@ cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
         if (e != cudaSuccess) return e;
         e = launch_guo_force(ctx->storage, ctx->scheme, (const DomDev *)ctx->dom_table.p,
                              (const int2 *)p->fslots.p, p->n_fslots, (int)off, ctx->stream);
+        if (e != cudaSuccess) return e;
+        e = enqueue_halo(ctx, p, (int)off);
         if (e != cudaSuccess) return e;
         e = launch_iolet_update((const IoDev *)p->ios.p, p->n_ios, (const int2 *)p->chunks.p, p->n_chunks,
                                 (double2 *)p->partials.p, (unsigned *)p->counters.p, (int)off, ctx->stream);
@@ -1404,6 +1467,22 @@ int ensure_graph(hg_ctx *ctx, Plan *p, int mode) {
     return HG_OK;
 }
 
+// n steps of a plan: whole groups as graph replays, the rest launched directly.
+int run_plan(hg_ctx *ctx, Plan *p, int64_t n, int mode) {
+    int64_t left = n;
+    if (ctx->graph_steps > 0 && n >= ctx->graph_steps) {
+        while (left >= ctx->graph_steps) {
+            const int rc = ensure_graph(ctx, p, mode);
+            if (rc != HG_OK) return rc;
+            CU(ctx, cudaGraphLaunch(p->graph[mode], ctx->stream));
+            left -= ctx->graph_steps;
+            if (mode != 2) mode = (int)((mode + ctx->graph_steps) & 1);
+        }
+    }
+    if (left > 0) CU(ctx, enqueue_steps(ctx, p, left, mode));
+    return HG_OK;
+}
+
 int step_set(hg_ctx *ctx, std::vector<int32_t> doms, int64_t n) {
     if (n < 0) return fail(ctx, HG_ERR_ARG, "negative step count");
     std::sort(doms.begin(), doms.end());
@@ -1413,18 +1492,8 @@ int step_set(hg_ctx *ctx, std::vector<int32_t> doms, int64_t n) {
     Plan *p = nullptr;
     int rc = build_plan(ctx, doms, p);
     if (rc != HG_OK) return rc;
-    int64_t left = n;
-    int mode = parity_mode(ctx, doms);
-    if (ctx->graph_steps > 0 && n >= ctx->graph_steps) {
-        while (left >= ctx->graph_steps) {
-            rc = ensure_graph(ctx, p, mode);
-            if (rc != HG_OK) return rc;
-            CU(ctx, cudaGraphLaunch(p->graph[mode], ctx->stream));
-            left -= ctx->graph_steps;
-            if (mode != 2) mode = (int)((mode + ctx->graph_steps) & 1);
-        }
-    }
-    if (left > 0) CU(ctx, enqueue_steps(ctx, p, left, mode));
+    rc = run_plan(ctx, p, n, parity_mode(ctx, doms));
+    if (rc != HG_OK) return rc;
     for (int32_t di : doms) ctx->doms[di]->step += n;
     return HG_OK;
 }
@@ -1757,6 +1826,547 @@ int hg_load_state(hg_domain *d, const void *buf, int64_t bytes) {
     if (fb) CU(ctx, cudaMemcpyAsync(ctx->scratch.p, p, fb, cudaMemcpyHostToDevice, ctx->stream));
     CU(ctx, launch_import_state(ctx->storage, ctx->scheme, domdev_ptr(d), d->n, (const int32_t *)d->canon_of.p,
                                 ctx->scratch.p, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+}  // extern "C"
+
+// ================================================================ split domains
+// Section 2.2: the sparse domain is decomposed over ranks and every step ends with
+// a non-blocking exchange of the populations that cross the cuts; Section 2.2.1:
+// the cut balances the work.  Here the canonical (Morton) site list is cut into
+// contiguous ranges of equal cost; each partition keeps ghost copies of the sites
+// it pulls from, and after every stream-collide the crossing values are packed per
+// (sender, receiver) pair, copied into the receiver's buffer and unpacked into its
+// ghosts.  All partitions of one split live on the context's device (the copy of
+// each block is a device-to-device copy).  Boundary slots are numbered globally in
+// canonical order and the per-slot and per-iolet arrays are shared, so each
+// iolet's FP64 reduction sees the same values in the same order as for the whole
+// domain: a split run is bit-identical to the unsplit one.
+namespace {
+
+struct SplitLayout {
+    std::vector<int64_t> first;                              // k + 1 cuts (canonical indices)
+    std::vector<std::vector<int64_t>> ghosts;                // per partition, sorted
+    std::vector<std::vector<std::pair<int32_t, int64_t>>> need;  // [q * k + p]: (direction i, site) p pulls from q
+};
+
+inline bool has_iolet_link(const std::vector<int32_t> &nbr, int64_t stride, int64_t s) {
+    for (int i = 0; i < 18; ++i)
+        if (nbr[(size_t)i * stride + s] < -1) return true;
+    return false;
+}
+
+// Cuts with equal cost per partition (a site costs 1, a site with an iolet link
+// `bw`), every partition non-empty; ghosts and the halo each partition needs.
+void split_layout(const std::vector<int32_t> &nbr, int64_t stride, int64_t n, int k, double bw, SplitLayout &L) {
+    std::vector<double> pre(n + 1, 0.0);
+    for (int64_t s = 0; s < n; ++s) pre[s + 1] = pre[s] + (has_iolet_link(nbr, stride, s) ? bw : 1.0);
+    L.first.assign(k + 1, 0);
+    for (int p = 1; p < k; ++p) {
+        int64_t c = std::lower_bound(pre.begin(), pre.end(), pre[n] * p / k) - pre.begin();
+        c = std::max<int64_t>(c, L.first[p - 1] + 1);
+        L.first[p] = std::min<int64_t>(c, n - (k - p));
+    }
+    L.first[k] = n;
+    L.ghosts.assign(k, {});
+    L.need.assign((size_t)k * k, {});
+    for (int p = 0; p < k; ++p) {
+        const int64_t a = L.first[p], b = L.first[p + 1];
+        std::vector<std::pair<int32_t, int64_t>> pulls;
+        for (int i = 0; i < 18; ++i)
+            for (int64_t s = a; s < b; ++s) {
+                const int32_t v = nbr[(size_t)i * stride + s];
+                if (v >= 0 && (v < a || v >= b)) pulls.push_back({i, v});
+            }
+        std::vector<int64_t> &g = L.ghosts[p];
+        for (const auto &e : pulls) g.push_back(e.second);
+        std::sort(g.begin(), g.end());
+        g.erase(std::unique(g.begin(), g.end()), g.end());
+        // (direction, site) pairs are distinct: site v + c_i is the only puller of (i, v)
+        for (const auto &e : pulls) {
+            const int q = (int)(std::upper_bound(L.first.begin(), L.first.end(), e.second) - L.first.begin()) - 1;
+            L.need[(size_t)q * k + p].push_back(e);
+        }
+    }
+}
+
+void free_split(hg_ctx *ctx, hg_split *sp) {
+    for (SplitPart &P : sp->parts)
+        for (DevBuf *b : {&P.f[0], &P.f[1], &P.nbr, &P.iomask, &P.ioprefix, &P.gidx}) dev_free(ctx, *b);
+    for (DevBuf *b : {&sp->bnd, &sp->io_codes, &sp->coef, &sp->slot_site, &sp->bcv, &sp->io_kind, &sp->M,
+                      &sp->slots, &sp->force})
+        dev_free(ctx, *b);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    for (SplitPart &P : sp->parts)
+        if (P.idx >= 0) ctx->reserved[P.idx] = 0;
+}
+
+int split_plan(hg_split *sp, Plan *&out) {
+    hg_ctx *ctx = sp->ctx;
+    PlanKey key;
+    for (const SplitPart &P : sp->parts) key.doms.push_back(P.idx);
+    auto it = ctx->plans.find(key);
+    if (it != ctx->plans.end()) {
+        out = it->second.get();
+        return HG_OK;
+    }
+    std::unique_ptr<Plan> p(new Plan);
+    p->doms = key.doms;
+    const int64_t ts = (int64_t)ctx->block * ctx->spt;
+    std::vector<TileDev> tiles;
+    for (const SplitPart &P : sp->parts)
+        for (int64_t s = 0; s < P.n_own; s += ts) tiles.push_back(TileDev{P.idx, (int32_t)std::min(ts, P.n_own - s), s});
+    std::vector<IoDev> ios;
+    std::vector<int2> chunks;
+    for (int k = 0; k < sp->nio; ++k) {
+        IoDev I;
+        memset(&I, 0, sizeof I);
+        const hg_iolet &io = sp->io[k];
+        I.slots = (const int32_t *)sp->slots.p + sp->io_ptr[k];
+        I.n_slots = sp->io_ptr[k + 1] - sp->io_ptr[k];
+        I.bnd = (const float4 *)sp->bnd.p;
+        I.M = (double *)sp->M.p + 3 * k;
+        I.bcv = (float *)sp->bcv.p + k;
+        I.step = (const int64_t *)ctx->steps.p + sp->parts[0].idx;
+        const double an = std::sqrt((double)io.axis[0] * io.axis[0] + (double)io.axis[1] * io.axis[1] +
+                                    (double)io.axis[2] * io.axis[2]);
+        I.nx = io.axis[0] / an;
+        I.ny = io.axis[1] / an;
+        I.nz = io.axis[2] / an;
+        I.value = io.value;
+        I.period = io.period;
+        I.pulse = io.pulse;
+        I.n_chunks = std::max(1, (I.n_slots + kIoChunk - 1) / kIoChunk);
+        I.part0 = (int32_t)chunks.size();
+        for (int c = 0; c < I.n_chunks; ++c) chunks.push_back(make_int2((int)ios.size(), c));
+        I.force = (float4 *)sp->force.p + k;
+        ios.push_back(I);
+    }
+    p->n_tiles = (int64_t)tiles.size();
+    p->n_ios = (int)ios.size();
+    p->n_chunks = (int)chunks.size();
+    p->n_halo = (int64_t)sp->pack.size();
+    p->halo_elem = (int)elem_bytes(ctx->storage);
+    for (const auto &b : sp->blocks)
+        p->halo_blocks.push_back({b.first * p->halo_elem, b.second * p->halo_elem});
+    int rc = HG_OK;
+    auto A = [&](DevBuf &b, size_t bytes) {
+        if (rc == HG_OK) rc = dev_alloc(ctx, b, bytes);
+    };
+    A(p->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TileDev));
+    A(p->ios, std::max<size_t>(1, ios.size()) * sizeof(IoDev));
+    A(p->adv, std::max<size_t>(1, key.doms.size()) * 4);
+    A(p->chunks, std::max<size_t>(1, chunks.size()) * sizeof(int2));
+    A(p->partials, std::max<size_t>(1, chunks.size()) * sizeof(double2));
+    A(p->counters, (ios.size() + 1) * sizeof(unsigned));
+    A(p->rev, sizeof(RevSrc));
+    A(p->fslots, sizeof(int2));
+    A(p->halo_pack, std::max<size_t>(1, sp->pack.size()) * sizeof(HaloDev));
+    A(p->halo_unpack, std::max<size_t>(1, sp->unpack.size()) * sizeof(HaloDev));
+    A(p->send, std::max<size_t>(1, sp->pack.size()) * p->halo_elem);
+    A(p->recv, std::max<size_t>(1, sp->pack.size()) * p->halo_elem);
+    auto release = [&] {
+        for (DevBuf *b : {&p->tiles, &p->ios, &p->adv, &p->chunks, &p->partials, &p->counters, &p->rev,
+                          &p->fslots, &p->halo_pack, &p->halo_unpack, &p->send, &p->recv})
+            dev_free(ctx, *b);
+    };
+    if (rc != HG_OK) {
+        release();
+        return rc;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(p->counters.p, 0, p->counters.bytes, st);
+    auto H2D = [&](DevBuf &b, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    H2D(p->tiles, tiles.data(), tiles.size() * sizeof(TileDev));
+    H2D(p->ios, ios.data(), ios.size() * sizeof(IoDev));
+    H2D(p->adv, key.doms.data(), key.doms.size() * 4);
+    H2D(p->chunks, chunks.data(), chunks.size() * sizeof(int2));
+    H2D(p->halo_pack, sp->pack.data(), sp->pack.size() * sizeof(HaloDev));
+    H2D(p->halo_unpack, sp->unpack.data(), sp->unpack.size() * sizeof(HaloDev));
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables above are temporaries
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        release();
+        return fail(ctx, HG_ERR_CUDA, "split plan upload failed: %s", cudaGetErrorString(e));
+    }
+    out = p.get();
+    ctx->plans[key] = std::move(p);
+    return HG_OK;
+}
+
+const DomDev *part_dev(hg_split *sp, int p) { return (const DomDev *)sp->ctx->dom_table.p + sp->parts[p].idx; }
+
+}  // namespace
+
+extern "C" {
+
+int hg_split_layout(const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32_t nio, const hg_split_params *sp,
+                    int64_t *first_out, int64_t *ghosts_out, int64_t *halo_out) {
+    if (!sp || n < 1 || !xyz || (nio > 0 && !iolets) || nio < 0 || nio > kMaxIolets) return HG_ERR_ARG;
+    const int k = sp->n_parts;
+    if (k < 1 || k > 1024 || k > n) return HG_ERR_ARG;
+    for (int q = 0; q < nio; ++q)
+        if (!iolet_ok(iolets[q])) return HG_ERR_ARG;
+    std::vector<int32_t> xs, nbr;
+    std::string why;
+    if (build_canonical(xyz, n, iolets, nio, n, xs, nbr, why) != HG_OK) return fail(nullptr, HG_ERR_ARG, "%s", why.c_str());
+    SplitLayout L;
+    split_layout(nbr, n, n, k, sp->boundary_weight > 0 ? sp->boundary_weight : 1.0, L);
+    for (int p = 0; p <= k; ++p)
+        if (first_out) first_out[p] = L.first[p];
+    for (int p = 0; p < k; ++p) {
+        if (ghosts_out) ghosts_out[p] = (int64_t)L.ghosts[p].size();
+        for (int q = 0; q < k; ++q)
+            if (halo_out) halo_out[(size_t)q * k + p] = (int64_t)L.need[(size_t)q * k + p].size();
+    }
+    return HG_OK;
+}
+
+int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32_t nio,
+                    const hg_lb_params *lb, const hg_split_params *spar, hg_split **out) {
+    if (!ctx) return HG_ERR_ARG;
+    if (!out || !spar) return fail(ctx, HG_ERR_ARG, "out or params is NULL");
+    *out = nullptr;
+    if (ctx->scheme != HG_SCHEME_AB) return fail(ctx, HG_ERR_ARG, "split domains use the A/B scheme");
+    if (n < 1 || !xyz || n > ((int64_t)200 << 20)) return fail(ctx, HG_ERR_ARG, "bad site array");
+    const int k = spar->n_parts;
+    if (k < 1 || k > 1024 || k > n) return fail(ctx, HG_ERR_ARG, "n_parts must be in [1, min(n, 1024)]");
+    if (nio < 0 || nio > kMaxIolets || (nio > 0 && !iolets)) return fail(ctx, HG_ERR_ARG, "bad iolet array");
+    const double tau = lb ? lb->tau : 0.8;
+    if (!(tau > 0.5)) return fail(ctx, HG_ERR_ARG, "tau must exceed 1/2");
+    if (lb && lb->ordering != HG_ORDER_MORTON) return fail(ctx, HG_ERR_ARG, "split domains keep the canonical order");
+    for (int q = 0; q < nio; ++q)
+        if (!iolet_ok(iolets[q])) return fail(ctx, HG_ERR_ARG, "iolet %d out of range", q);
+    CU(ctx, cudaSetDevice(ctx->device));
+    std::unique_ptr<hg_split> sp(new hg_split);
+    sp->ctx = ctx;
+    sp->n = n;
+    sp->nio = nio;
+    sp->tau = tau;
+    sp->io.assign(iolets, iolets + nio);
+    std::vector<int32_t> xs, nbr;
+    {
+        std::string why;
+        if (build_canonical(xyz, n, iolets, nio, n, xs, nbr, why) != HG_OK)
+            return fail(ctx, HG_ERR_ARG, "%s", why.c_str());
+    }
+    SplitLayout L;
+    split_layout(nbr, n, n, k, spar->boundary_weight > 0 ? spar->boundary_weight : 1.0, L);
+    // reserve one context slot (descriptor + step counter) per partition
+    sp->parts.resize(k);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        int got = 0;
+        for (int i = 0; i < ctx->capacity && got < k; ++i)
+            if (!ctx->doms[i] && !ctx->reserved[i]) {
+                ctx->reserved[i] = 1;
+                sp->parts[got++].idx = i;
+            }
+        if (got < k) {
+            for (int j = 0; j < got; ++j) ctx->reserved[sp->parts[j].idx] = 0;
+            return fail(ctx, HG_ERR_STATE, "context holds too many domains");
+        }
+    }
+    // global boundary slots in canonical order (as the whole domain numbers them)
+    std::vector<int32_t> slot_of(n, -1);
+    std::vector<int64_t> per_io(nio + 1, 0);
+    int64_t n_adj = 0;
+    auto distinct = [&](int64_t c, int seen[18]) {
+        int ns = 0;
+        for (int i = 0; i < 18; ++i) {
+            const int32_t v = nbr[(size_t)i * n + c];
+            if (v >= -1) continue;
+            bool dup = false;
+            for (int t = 0; t < ns; ++t) dup = dup || seen[t] == -v - 2;
+            if (!dup) seen[ns++] = -v - 2;
+        }
+        return ns;
+    };
+    for (int64_t c = 0; c < n; ++c) {
+        int seen[18];
+        const int ns = distinct(c, seen);
+        for (int t = 0; t < ns; ++t) per_io[seen[t] + 1]++;
+        if (ns) slot_of[c] = (int32_t)n_adj++;
+    }
+    sp->n_adj = n_adj;
+    for (int q = 0; q < nio; ++q) per_io[q + 1] += per_io[q];
+    sp->io_ptr.assign(per_io.begin(), per_io.end());
+    std::vector<int32_t> slots(std::max<int64_t>(1, per_io[nio]));
+    std::vector<int32_t> codes((size_t)std::max<int64_t>(1, n_adj) * 18, -1);
+    std::vector<float> coef((size_t)std::max<int64_t>(1, n_adj) * 18, 0.0f);
+    std::vector<int32_t> slot_site((size_t)std::max<int64_t>(1, n_adj), 0);
+    {
+        std::vector<int64_t> fill(per_io.begin(), per_io.end() - 1);
+        for (int p = 0; p < k; ++p)
+            for (int64_t c = L.first[p]; c < L.first[p + 1]; ++c) {
+                const int32_t sl = slot_of[c];
+                if (sl < 0) continue;
+                int seen[18];
+                const int ns = distinct(c, seen);
+                for (int t = 0; t < ns; ++t) slots[fill[seen[t]]++] = sl;
+                slot_site[sl] = (int32_t)(c - L.first[p]);
+                for (int i = 1; i < 19; ++i) {
+                    const int32_t v = nbr[(size_t)(i - 1) * n + c];
+                    codes[(size_t)sl * 18 + (i - 1)] = v;
+                    if (v < -1) coef[(size_t)sl * 18 + (i - 1)] = link_coef(iolets[-v - 2], &xs[3 * c], i, ctx->storage);
+                }
+            }
+    }
+    const size_t eb = elem_bytes(ctx->storage);
+    int rc = HG_OK;
+    auto A = [&](DevBuf &b, size_t bytes) {
+        if (rc == HG_OK) rc = dev_alloc(ctx, b, bytes);
+    };
+    A(sp->bnd, (size_t)std::max<int64_t>(1, n_adj) * 16);
+    A(sp->io_codes, codes.size() * 4);
+    A(sp->coef, coef.size() * 4);
+    A(sp->slot_site, slot_site.size() * 4);
+    A(sp->bcv, (size_t)std::max(1, nio) * 4);
+    A(sp->io_kind, (size_t)std::max(1, nio));
+    A(sp->M, (size_t)std::max(1, nio) * 24);
+    A(sp->slots, slots.size() * 4);
+    A(sp->force, (size_t)std::max(1, nio) * 16);
+    // per partition: local tables (owned sites first, then ghosts)
+    std::vector<std::vector<int32_t>> tab(k), mask(k), pref(k), gidx(k);
+    for (int p = 0; p < k && rc == HG_OK; ++p) {
+        SplitPart &P = sp->parts[p];
+        P.first = L.first[p];
+        P.n_own = L.first[p + 1] - L.first[p];
+        P.ghosts = L.ghosts[p];
+        P.n_loc = P.n_own + (int64_t)P.ghosts.size();
+        P.np = std::max<int64_t>(128, (P.n_loc + 127) / 128 * 128);
+        const int64_t a = P.first, b = L.first[p + 1], np = P.np;
+        auto local = [&](int64_t v) -> int64_t {
+            if (v >= a && v < b) return v - a;
+            return P.n_own + (std::lower_bound(P.ghosts.begin(), P.ghosts.end(), v) - P.ghosts.begin());
+        };
+        std::vector<int32_t> &T = tab[p];
+        T.assign((size_t)18 * np, 0);
+        for (int i = 1; i < 19; ++i) {
+            const int opp = (i & 1) ? i + 1 : i - 1;
+            for (int64_t q = 0; q < np; ++q) {
+                const int32_t v = q < P.n_own ? nbr[(size_t)(i - 1) * n + a + q] : -1;
+                T[(size_t)(i - 1) * np + q] = v >= 0 ? (int32_t)local(v) : (int32_t)(q + (int64_t)(opp - i) * np);
+            }
+        }
+        mask[p].assign((size_t)np / 32, 0u);
+        pref[p].assign((size_t)np / 32, 0);
+        int32_t acc = 0;
+        for (int64_t q = 0; q < P.n_own; ++q)
+            if (slot_of[a + q] >= 0) mask[p][q >> 5] |= 1u << (q & 31);
+        const int32_t base = [&] {
+            for (int64_t c = a; c < b; ++c)
+                if (slot_of[c] >= 0) return slot_of[c];
+            return (int32_t)0;
+        }();
+        for (size_t w = 0; w < mask[p].size(); ++w) {
+            pref[p][w] = base + acc;
+            acc += __builtin_popcount(mask[p][w]);
+        }
+        gidx[p].resize(P.n_loc);
+        for (int64_t q = 0; q < P.n_own; ++q) gidx[p][q] = (int32_t)(a + q);
+        for (size_t g = 0; g < P.ghosts.size(); ++g) gidx[p][P.n_own + g] = (int32_t)P.ghosts[g];
+        A(P.f[0], 19 * (size_t)np * eb);
+        A(P.f[1], 19 * (size_t)np * eb);
+        A(P.nbr, T.size() * 4);
+        A(P.iomask, mask[p].size() * 4);
+        A(P.ioprefix, pref[p].size() * 4);
+        A(P.gidx, gidx[p].size() * 4);
+    }
+    if (rc != HG_OK) {
+        free_split(ctx, sp.get());
+        return rc;
+    }
+    // halo blocks, one per (sender, receiver) pair
+    for (int q = 0; q < k; ++q)
+        for (int p = 0; p < k; ++p) {
+            const auto &need = L.need[(size_t)q * k + p];
+            if (need.empty()) continue;
+            const size_t off = sp->pack.size();
+            const SplitPart &Q = sp->parts[q], &P = sp->parts[p];
+            for (const auto &e : need) {
+                const int64_t g = P.n_own + (std::lower_bound(P.ghosts.begin(), P.ghosts.end(), e.second) -
+                                             P.ghosts.begin());
+                sp->pack.push_back(HaloDev{Q.idx, 0, (int64_t)(e.first + 1) * Q.np + (e.second - Q.first)});
+                sp->unpack.push_back(HaloDev{P.idx, 0, (int64_t)(e.first + 1) * P.np + g});
+            }
+            sp->blocks.push_back({off, need.size()});
+        }
+    std::vector<float> bcv(std::max(1, nio), 0.0f);
+    std::vector<int8_t> kinds(std::max(1, nio), 0);
+    for (int q = 0; q < nio; ++q) {
+        bcv[q] = (float)(iolets[q].value * pulse(iolets[q].pulse, 1.0, iolets[q].period));
+        kinds[q] = (int8_t)iolets[q].kind;
+    }
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaSuccess;
+    auto H2D = [&](DevBuf &b, const void *src, size_t bytes) {
+        if (e == cudaSuccess && bytes) e = cudaMemcpyAsync(b.p, src, bytes, cudaMemcpyHostToDevice, st);
+    };
+    H2D(sp->io_codes, codes.data(), codes.size() * 4);
+    H2D(sp->coef, coef.data(), coef.size() * 4);
+    H2D(sp->slot_site, slot_site.data(), slot_site.size() * 4);
+    H2D(sp->bcv, bcv.data(), bcv.size() * 4);
+    H2D(sp->io_kind, kinds.data(), kinds.size());
+    H2D(sp->slots, slots.data(), slots.size() * 4);
+    for (DevBuf *b : {&sp->bnd, &sp->M, &sp->force})
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, b->bytes, st);
+    for (int p = 0; p < k; ++p) {
+        SplitPart &P = sp->parts[p];
+        H2D(P.nbr, tab[p].data(), tab[p].size() * 4);
+        H2D(P.iomask, mask[p].data(), mask[p].size() * 4);
+        H2D(P.ioprefix, pref[p].data(), pref[p].size() * 4);
+        H2D(P.gidx, gidx[p].data(), gidx[p].size() * 4);
+        for (DevBuf *b : {&P.f[0], &P.f[1]})
+            if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, b->bytes, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync((int64_t *)ctx->steps.p + P.idx, 0, sizeof(int64_t), st);
+        DomDev &D = P.dev;
+        memset(&D, 0, sizeof D);
+        D.f[0] = P.f[0].p;
+        D.f[1] = P.f[1].p;
+        D.nbr = (const int32_t *)P.nbr.p;
+        D.iomask = (const uint32_t *)P.iomask.p;
+        D.ioprefix = (const int32_t *)P.ioprefix.p;
+        D.io_codes = (const int32_t *)sp->io_codes.p;
+        D.bnd = (float4 *)sp->bnd.p;
+        D.coef = (const float *)sp->coef.p;
+        D.bcv = (const float *)sp->bcv.p;
+        D.io_kind = (const int8_t *)sp->io_kind.p;
+        D.step = (const int64_t *)ctx->steps.p + P.idx;
+        D.err = (int32_t *)ctx->errw.p;
+        D.n = P.n_loc;
+        D.np = P.np;
+        D.omega = (float)(1.0 / tau);
+        D.n_io = nio;
+        D.slot_site = (const int32_t *)sp->slot_site.p;
+        D.io_force = nullptr;
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync((DomDev *)ctx->dom_table.p + P.idx, &D, sizeof D, cudaMemcpyHostToDevice, st);
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host tables are released below
+    if (e != cudaSuccess) {
+        cudaStreamSynchronize(st);
+        free_split(ctx, sp.get());
+        return fail(ctx, HG_ERR_CUDA, "split upload failed: %s", cudaGetErrorString(e));
+    }
+    ctx->splits.push_back(sp.get());
+    *out = sp.release();
+    return HG_OK;
+}
+
+int hg_split_destroy(hg_split *sp) {
+    if (!sp) return HG_ERR_ARG;
+    hg_ctx *ctx = sp->ctx;
+    cudaSetDevice(ctx->device);
+    cudaStreamSynchronize(ctx->stream);
+    drop_plans(ctx);
+    free_split(ctx, sp);
+    ctx->splits.erase(std::remove(ctx->splits.begin(), ctx->splits.end(), sp), ctx->splits.end());
+    delete sp;
+    return HG_OK;
+}
+
+int hg_split_info(hg_split *sp, int32_t part, int64_t *first, int64_t *owned, int64_t *ghosts, int64_t *halo_in) {
+    if (!sp || part < 0 || part >= (int32_t)sp->parts.size()) return HG_ERR_ARG;
+    const SplitPart &P = sp->parts[part];
+    if (first) *first = P.first;
+    if (owned) *owned = P.n_own;
+    if (ghosts) *ghosts = (int64_t)P.ghosts.size();
+    if (halo_in) {
+        int64_t h = 0;
+        for (const HaloDev &u : sp->unpack) h += u.dom == P.idx;
+        *halo_in = h;
+    }
+    return HG_OK;
+}
+
+int hg_split_step(hg_split *sp, int64_t n) {
+    if (!sp) return HG_ERR_ARG;
+    hg_ctx *ctx = sp->ctx;
+    if (n < 0) return fail(ctx, HG_ERR_ARG, "negative step count");
+    if (n == 0) return HG_OK;
+    CU(ctx, cudaSetDevice(ctx->device));
+    Plan *p = nullptr;
+    int rc = split_plan(sp, p);
+    if (rc == HG_OK) rc = run_plan(ctx, p, n, 2);
+    if (rc != HG_OK) return rc;
+    sp->step += n;
+    return HG_OK;
+}
+
+int hg_split_read_macroscopic(hg_split *sp, float *out) {
+    if (!sp || !out) return HG_ERR_ARG;
+    hg_ctx *ctx = sp->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    int rc = ensure_scratch(ctx, (size_t)sp->n * 16);
+    if (rc != HG_OK) return rc;
+    for (size_t p = 0; p < sp->parts.size(); ++p)
+        CU(ctx, launch_macroscopic(ctx->storage, ctx->scheme, part_dev(sp, (int)p), sp->parts[p].n_own,
+                                   (const int32_t *)sp->parts[p].gidx.p, (float4 *)ctx->scratch.p, ctx->stream));
+    CU(ctx, cudaMemcpyAsync(out, ctx->scratch.p, (size_t)sp->n * 16, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+// F_t of every partition's owned sites, canonical order, into the context scratch.
+static int split_export(hg_split *sp, size_t extra) {
+    hg_ctx *ctx = sp->ctx;
+    const size_t fb = 19 * (size_t)sp->n * elem_bytes(ctx->storage);
+    int rc = ensure_scratch(ctx, ((fb + 255) & ~(size_t)255) + extra);
+    if (rc != HG_OK) return rc;
+    for (size_t p = 0; p < sp->parts.size(); ++p)
+        CU(ctx, launch_export_state(ctx->storage, ctx->scheme, part_dev(sp, (int)p), sp->parts[p].n_own,
+                                    (const int32_t *)sp->parts[p].gidx.p, ctx->scratch.p, ctx->stream, sp->n));
+    return HG_OK;
+}
+
+int hg_split_read_state(hg_split *sp, void *out) {
+    if (!sp || !out) return HG_ERR_ARG;
+    hg_ctx *ctx = sp->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    int rc = split_export(sp, 0);
+    if (rc != HG_OK) return rc;
+    CU(ctx, cudaMemcpyAsync(out, ctx->scratch.p, 19 * (size_t)sp->n * elem_bytes(ctx->storage),
+                            cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+int hg_split_mass(hg_split *sp, double *out) {
+    if (!sp || !out) return HG_ERR_ARG;
+    hg_ctx *ctx = sp->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    const int64_t P = mass_partials_needed(sp->n);
+    int rc = split_export(sp, (size_t)(P + 1) * sizeof(double2));
+    if (rc != HG_OK) return rc;
+    const size_t fb = (19 * (size_t)sp->n * elem_bytes(ctx->storage) + 255) & ~(size_t)255;
+    double2 *part = (double2 *)((char *)ctx->scratch.p + fb);
+    CU(ctx, launch_mass_flat(ctx->storage, ctx->scratch.p, sp->n, sp->n, part, part + P, ctx->stream));
+    double2 r;
+    CU(ctx, cudaMemcpyAsync(&r, part + P, sizeof r, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    *out = r.x;
+    return HG_OK;
+}
+
+int hg_split_read_iolet_stats(hg_split *sp, double *out) {
+    if (!sp || (!out && sp->nio)) return HG_ERR_ARG;
+    hg_ctx *ctx = sp->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (sp->nio) CU(ctx, cudaMemcpyAsync(out, sp->M.p, (size_t)sp->nio * 24, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(ctx, cudaStreamSynchronize(ctx->stream));
+    return HG_OK;
+}
+
+int hg_split_read_boundary_values(hg_split *sp, float *out) {
+    if (!sp || (!out && sp->nio)) return HG_ERR_ARG;
+    hg_ctx *ctx = sp->ctx;
+    CU(ctx, cudaSetDevice(ctx->device));
+    if (sp->nio) CU(ctx, cudaMemcpyAsync(out, sp->bcv.p, (size_t)sp->nio * 4, cudaMemcpyDeviceToHost, ctx->stream));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     return HG_OK;
 }

@@ -124,11 +124,33 @@ cudaError_t launch_guo_force(int storage, int scheme, const DomDev *doms, const 
 // (drho, ux, uy, uz) to out[canon_of ? canon_of[s] : s] (device -> canonical index).
 cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, int64_t n,
                                const int32_t *canon_of, float4 *out, cudaStream_t st);
-// Raw state export/import of F_t in canonical order (storage type, [19][n]).
+// Raw state export/import of F_t of device sites [0, n) in canonical order
+// (storage type, [19][row] with row = n, or `row` when non-zero: the sites of a
+// partition written into the whole domain's rows).
 cudaError_t launch_export_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int32_t *canon_of, void *out, cudaStream_t st);
+                                const int32_t *canon_of, void *out, cudaStream_t st, int64_t row = 0);
 cudaError_t launch_import_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int32_t *canon_of, const void *in, cudaStream_t st);
+                                const int32_t *canon_of, const void *in, cudaStream_t st, int64_t row = 0);
+
+// One value of the halo exchange between partitions of a split domain: direction
+// row and site of one partition's distributions (offset = row * np + site in the
+// buffer holding F_t).
+struct HaloDev {
+    int32_t dom;    // descriptor (context domain table index) of the partition
+    int32_t pad;
+    int64_t off;
+};
+// After the stream-collide launch of step offset `off`: copy F_t values of the
+// owning partitions into a send buffer (pack), or from a receive buffer into the
+// ghost positions of the reading partitions (unpack); elem = 4 or 2 bytes.
+cudaError_t launch_halo_pack(int elem, const DomDev *doms, const int64_t *steps, const HaloDev *ent,
+                             int64_t n, void *send, int off, cudaStream_t st);
+cudaError_t launch_halo_unpack(int elem, const DomDev *doms, const int64_t *steps, const HaloDev *ent,
+                               int64_t n, const void *recv, int off, cudaStream_t st);
+// Mass of a state held in canonical order ([19][stride], sites [0, n)): the same
+// chunks, order and rounding as launch_mass.
+cudaError_t launch_mass_flat(int storage, const void *f, int64_t n, int64_t stride, double2 *partials,
+                             double2 *out, cudaStream_t st);
 // Mass check: FP64 partial sums of F_t over fixed chunks of 8192 sites in
 // canonical order, each site's values in direction order (dev_of: canonical ->
 // device index, null = identity), then a fixed-order final sum.  Each partial

@@ -309,7 +309,7 @@ __global__ void k_macroscopic(const DomDev *__restrict__ dd, int64_t n, const in
 
 template <int S, int SCHEME>
 __global__ void k_export_state(const DomDev *__restrict__ dd, int64_t n, const int32_t *canon_of,
-                               typename St<S>::T *out) {
+                               typename St<S>::T *out, int64_t row) {
     const DomDev D = *dd;
     const int64_t t = *D.step;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
@@ -317,14 +317,14 @@ __global__ void k_export_state(const DomDev *__restrict__ dd, int64_t n, const i
         const int64_t c = canon_of ? canon_of[s] : s;
         unroll<0, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
-            out[(int64_t)I * n + c] = stored_F<S, SCHEME, I>(D, t, s);
+            out[(int64_t)I * row + c] = stored_F<S, SCHEME, I>(D, t, s);
         });
     }
 }
 
 template <int S, int SCHEME>
 __global__ void k_import_state(const DomDev *__restrict__ dd, int64_t n, const int32_t *canon_of,
-                               const typename St<S>::T *in) {
+                               const typename St<S>::T *in, int64_t row) {
     const DomDev D = *dd;
     const int64_t t = *D.step;
     for (int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; s < n;
@@ -332,8 +332,31 @@ __global__ void k_import_state(const DomDev *__restrict__ dd, int64_t n, const i
         const int64_t c = canon_of ? canon_of[s] : s;
         unroll<0, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
-            *stored_F_ptr<S, SCHEME, I>(D, t, s) = in[(int64_t)I * n + c];
+            *stored_F_ptr<S, SCHEME, I>(D, t, s) = in[(int64_t)I * row + c];
         });
+    }
+}
+
+// ---- halo exchange of a split domain (A/B scheme: F_t sits in f[t & 1]) ----
+template <typename W>
+__global__ void k_halo_pack(const DomDev *__restrict__ doms, const int64_t *__restrict__ steps,
+                            const HaloDev *__restrict__ ent, int64_t n, W *send, int off) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const HaloDev h = ent[e];
+        const int64_t t = steps[h.dom] + off + 1;
+        send[e] = ((const W *)doms[h.dom].f[t & 1])[h.off];
+    }
+}
+
+template <typename W>
+__global__ void k_halo_unpack(const DomDev *__restrict__ doms, const int64_t *__restrict__ steps,
+                              const HaloDev *__restrict__ ent, int64_t n, const W *recv, int off) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const HaloDev h = ent[e];
+        const int64_t t = steps[h.dom] + off + 1;
+        ((W *)doms[h.dom].f[t & 1])[h.off] = recv[e];
     }
 }
 
@@ -361,6 +384,25 @@ __global__ void __launch_bounds__(kMassThreads) k_mass_partials(const DomDev *__
         unroll<0, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
             const double v = St<S>::ldd(stored_F<S, SCHEME, I>(D, t, s), I);
+            a = __dadd_rn(a, v);
+            if (!isfinite(v)) b = __dadd_rn(b, 1.0);
+        });
+    }
+    block_sum2(a, b);
+    if (threadIdx.x == 0) partials[blockIdx.x] = make_double2(a, b);
+}
+
+// The same sum over a state already in canonical order ([19][stride]).
+template <int S>
+__global__ void __launch_bounds__(kMassThreads) k_mass_partials_flat(const typename St<S>::T *f, int64_t n,
+                                                                     int64_t stride, double2 *partials) {
+    const int64_t lo = (int64_t)blockIdx.x * kMassChunk;
+    const int64_t hi = lo + kMassChunk < n ? lo + kMassChunk : n;
+    double a = 0.0, b = 0.0;
+    for (int64_t c = lo + threadIdx.x; c < hi; c += blockDim.x) {
+        unroll<0, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            const double v = St<S>::ldd(f[(int64_t)I * stride + c], I);
             a = __dadd_rn(a, v);
             if (!isfinite(v)) b = __dadd_rn(b, 1.0);
         });
@@ -442,20 +484,57 @@ cudaError_t launch_macroscopic(int storage, int scheme, const DomDev *dom_dev, i
 }
 
 cudaError_t launch_export_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int32_t *canon_of, void *out, cudaStream_t st) {
+                                const int32_t *canon_of, void *out, cudaStream_t st, int64_t row) {
     if (n <= 0) return cudaSuccess;
+    if (row == 0) row = n;
     HG_DISPATCH_SS(storage, scheme,
                    (k_export_state<S_, C_><<<rb_grid(n), 256, 0, st>>>(
-                       dom_dev, n, canon_of, (typename St<S_>::T *)out)));
+                       dom_dev, n, canon_of, (typename St<S_>::T *)out, row)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_import_state(int storage, int scheme, const DomDev *dom_dev, int64_t n,
-                                const int32_t *canon_of, const void *in, cudaStream_t st) {
+                                const int32_t *canon_of, const void *in, cudaStream_t st, int64_t row) {
     if (n <= 0) return cudaSuccess;
+    if (row == 0) row = n;
     HG_DISPATCH_SS(storage, scheme,
                    (k_import_state<S_, C_><<<rb_grid(n), 256, 0, st>>>(
-                       dom_dev, n, canon_of, (const typename St<S_>::T *)in)));
+                       dom_dev, n, canon_of, (const typename St<S_>::T *)in, row)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_pack(int elem, const DomDev *doms, const int64_t *steps, const HaloDev *ent,
+                             int64_t n, void *send, int off, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (elem == 4) k_halo_pack<uint32_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, ent, n, (uint32_t *)send, off);
+    else k_halo_pack<uint16_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, ent, n, (uint16_t *)send, off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_unpack(int elem, const DomDev *doms, const int64_t *steps, const HaloDev *ent,
+                               int64_t n, const void *recv, int off, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (elem == 4)
+        k_halo_unpack<uint32_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, ent, n, (const uint32_t *)recv, off);
+    else
+        k_halo_unpack<uint16_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, ent, n, (const uint16_t *)recv, off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mass_flat(int storage, const void *f, int64_t n, int64_t stride, double2 *partials,
+                             double2 *out, cudaStream_t st) {
+    const int64_t P = mass_partials_needed(n);
+    if (n <= 0) return cudaMemsetAsync(out, 0, sizeof(double2), st);
+    if (storage == kF32)
+        k_mass_partials_flat<kF32><<<(unsigned)P, kMassThreads, 0, st>>>((const float *)f, n, stride, partials);
+    else if (storage == kF16)
+        k_mass_partials_flat<kF16><<<(unsigned)P, kMassThreads, 0, st>>>((const __half *)f, n, stride, partials);
+    else
+        k_mass_partials_flat<kBF16><<<(unsigned)P, kMassThreads, 0, st>>>((const __nv_bfloat16 *)f, n, stride,
+                                                                           partials);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_mass_final<<<1, kMassThreads, 0, st>>>(partials, P, out);
     return cudaGetLastError();
 }
 

@@ -55,6 +55,10 @@ class hg_lb_params(C.Structure):
     _fields_ = [("tau", C.c_double), ("ordering", C.c_int32), ("reserved", C.c_int32)]
 
 
+class hg_split_params(C.Structure):
+    _fields_ = [("n_parts", C.c_int32), ("reserved", C.c_int32), ("boundary_weight", C.c_double)]
+
+
 class hg_pair(C.Structure):
     _fields_ = [("src_iolet", C.c_int32), ("dst_iolet", C.c_int32), ("factor", C.c_double)]
 
@@ -97,6 +101,18 @@ _SIGS = {
     "hg_state_check": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hg_read_adjacent_moments": ([C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
     "hg_ctx_inject_fault": ([C.c_void_p, C.c_int32, C.c_int64], C.c_int),
+    "hg_split_layout": ([C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                         C.c_void_p], C.c_int),
+    "hg_split_create": ([C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_int32, C.POINTER(hg_lb_params),
+                         C.c_void_p, C.POINTER(C.c_void_p)], C.c_int),
+    "hg_split_destroy": ([C.c_void_p], C.c_int),
+    "hg_split_info": ([C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p], C.c_int),
+    "hg_split_step": ([C.c_void_p, C.c_int64], C.c_int),
+    "hg_split_read_macroscopic": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_split_read_state": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_split_read_iolet_stats": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_split_read_boundary_values": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_split_mass": ([C.c_void_p, C.c_void_p], C.c_int),
 }
 
 
@@ -180,6 +196,19 @@ def build_neighbours(xyz, iolets):
     return xs[:n], nbr[:, :n]
 
 
+def split_layout(xyz, iolets, n_parts, boundary_weight=1.0):
+    """Host-only partition of a domain (Section 2.2 / 2.2.1): (first (k+1,), ghosts (k,),
+    halo (k, k) with halo[q, p] = values partition p pulls from partition q per step)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+    sp = hg_split_params(int(n_parts), 0, float(boundary_weight))
+    first = np.zeros(n_parts + 1, np.int64)
+    ghosts = np.zeros(n_parts, np.int64)
+    halo = np.zeros((n_parts, n_parts), np.int64)
+    _check(lib().hg_split_layout(_p(xyz), xyz.shape[0], iolet_struct_array(iolets), len(iolets), C.byref(sp),
+                                 _p(first), _p(ghosts), _p(halo)))
+    return first, ghosts, halo
+
+
 def hg_coupling_factors(art_centres, art_areas, ven_centres, ven_areas, uniforms):
     """Section 3 coupling map + factors: returns (assign, dist, dp, factor) numpy arrays."""
     ac = np.ascontiguousarray(art_centres, dtype=np.int64).reshape(-1, 3)
@@ -227,6 +256,9 @@ class Context:
 
     def domain(self, xyz, iolets, tau=0.8, ordering="morton"):
         return Domain(self, xyz, iolets, tau, ordering)
+
+    def split(self, xyz, iolets, n_parts, tau=0.8, boundary_weight=1.0):
+        return Split(self, xyz, iolets, n_parts, tau, boundary_weight)
 
     def inject_fault(self, kind, arg=0):
         """Host-side fault injection (FAULT_ALLOC: the arg-th next allocation fails;
@@ -276,6 +308,9 @@ class Context:
             for d in self.domains:
                 d.h = None
             self.domains = []
+            for sp in getattr(self, "splits", []):
+                sp.h = None
+            self.splits = []
 
     def __del__(self):
         try:
@@ -399,3 +434,62 @@ class Domain:
             self.ctx._ck(lib().hg_domain_destroy(self.h))
             self.h = None
             self.ctx.domains.remove(self)
+
+
+class Split:
+    """A domain cut into partitions with a halo exchange every step (Section 2.2)."""
+
+    def __init__(self, ctx: Context, xyz, iolets, n_parts, tau=0.8, boundary_weight=1.0):
+        self.ctx = ctx
+        xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
+        lb = hg_lb_params()
+        lb.tau, lb.ordering = float(tau), 0
+        sp = hg_split_params(int(n_parts), 0, float(boundary_weight))
+        h = C.c_void_p()
+        ctx._ck(lib().hg_split_create(ctx.h, _p(xyz), xyz.shape[0], iolet_struct_array(iolets), len(iolets),
+                                      C.byref(lb), C.byref(sp), C.byref(h)))
+        self.h = h
+        self.n, self.n_iolets, self.n_parts = xyz.shape[0], len(iolets), int(n_parts)
+        if not hasattr(ctx, "splits"):
+            ctx.splits = []
+        ctx.splits.append(self)
+
+    def info(self, part):
+        v = [C.c_int64() for _ in range(4)]
+        self.ctx._ck(lib().hg_split_info(self.h, int(part), *[C.byref(x) for x in v]))
+        return dict(first=v[0].value, owned=v[1].value, ghosts=v[2].value, halo_in=v[3].value)
+
+    def step(self, n):
+        self.ctx._ck(lib().hg_split_step(self.h, int(n)))
+
+    def macroscopic(self):
+        out = np.zeros((self.n, 4), np.float32)
+        self.ctx._ck(lib().hg_split_read_macroscopic(self.h, _p(out)))
+        return out
+
+    def state(self):
+        dt = {0: np.float32, 1: np.float16, 2: np.uint16}[self.ctx.storage]
+        out = np.zeros((19, self.n), dt)
+        self.ctx._ck(lib().hg_split_read_state(self.h, _p(out)))
+        return out
+
+    def iolet_stats(self):
+        out = np.zeros((max(1, self.n_iolets), 3), np.float64)
+        self.ctx._ck(lib().hg_split_read_iolet_stats(self.h, _p(out)))
+        return out[: self.n_iolets]
+
+    def boundary_values(self):
+        out = np.zeros(max(1, self.n_iolets), np.float32)
+        self.ctx._ck(lib().hg_split_read_boundary_values(self.h, _p(out)))
+        return out[: self.n_iolets]
+
+    def mass(self):
+        out = C.c_double()
+        self.ctx._ck(lib().hg_split_mass(self.h, C.byref(out)))
+        return out.value
+
+    def destroy(self):
+        if self.h:
+            self.ctx._ck(lib().hg_split_destroy(self.h))
+            self.h = None
+            self.ctx.splits.remove(self)
