@@ -205,7 +205,7 @@ def whole_job_mflups(sites_per_rank, world_size, steps, max_ms):
 
 
 def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, launch=None,
-                 orderings=ORDERINGS):
+                 orderings=ORDERINGS, min_timed_s=MIN_TIMED_S):
     """Autotuned (or given) site ordering and launch shape, device-timed steps (graphs),
     per-kernel times, e2e job."""
     import torch
@@ -258,7 +258,7 @@ def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, 
             total += x
             if len(reps) == 1:  # the repetition count follows from the first measurement,
                 # the same on every rank (slowest rank's count)
-                n_rep = int(max_over_ranks(float(max(3, min(20000, math.ceil(MIN_TIMED_S * 1e3 / x)))),
+                n_rep = int(max_over_ranks(float(max(3, min(20000, math.ceil(min_timed_s * 1e3 / x)))),
                                            dist, device))
         nvtx.range_pop()
         ms = max_over_ranks(statistics.median(reps), dist, device)
@@ -365,30 +365,67 @@ def _geo_pool_gen(args):
     return (art, ven)
 
 
-def serve_requests(args):
-    """The seeded request stream and its voxelised geometries (spawned host processes)."""
+def _large_tree(scale):
+    """Worker (spawned process): the precision workload's tree, depth 8, root radius 40."""
+    from paper_2010_04144_gb300 import synth as S
+
+    return S.tree(S.TreeSpec(depth=8, root_radius=40.0, seed=2010041442, scale=scale),
+                  inlet_speed=0.05, period=1000.0)
+
+
+def serve_requests(args, pool=None):
+    """The seeded request stream and its voxelised geometries (spawned host processes).  With
+    a pool given, the voxelisation starts there and a callable returns the result later."""
     import multiprocessing as mp
 
     from paper_2010_04144_gb300 import synth as S
 
     reqs = S.request_stream(n_requests=args.requests, rate_per_s=args.rate,
                             sites_range=(args.min_sites, args.max_sites), steps=args.serve_steps)
-    pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+    own = pool is None
+    if own:
+        pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
     t0 = time.perf_counter()
-    geos = pool.map(_geo_pool_gen, [(r.spec, r.coupled) for r in reqs], chunksize=1)
-    pool.close()
-    return reqs, geos, time.perf_counter() - t0
+    pending = pool.map_async(_geo_pool_gen, [(r.spec, r.coupled) for r in reqs], chunksize=1)
+
+    def result():
+        geos = pending.get()
+        if own:
+            pool.close()
+        return reqs, geos, time.perf_counter() - t0
+
+    return result if not own else result()
 
 
-def run_serve(args, H, device, prepared=None):
+def serve_tuning(args, H, device, reqs, geos):
+    """Site ordering and launch shape of the packed (tile-table) launches serving runs: tuned
+    on a context that holds the stream's first requests, as a tick would pack them."""
+    from paper_2010_04144_gb300 import synth as S
+    from paper_2010_04144_gb300.autotune import tune_ordering
+
+    pack = [x for g in geos[:4] for x in g]
+
+    def make(o):
+        c = H.Context(device=device, storage=args.serve_storage, scheme=args.serve_scheme)
+        for g in pack:
+            c.domain(g.xyz, g.iolets, ordering=o)
+        return c
+
+    o, shape, table = tune_ordering(make, ORDERINGS if args.serve_ordering == "auto" else (args.serve_ordering,))
+    return o, shape, {k: round(v[1], 4) for k, v in table.items()}, int(sum(g.n for g in pack))
+
+
+def serve_stats(args, H, device, prepared=None):
     """Serving workload: seeded request stream, continuous batching, p50/p99 time-to-result."""
     from paper_2010_04144_gb300 import serve as SV
     from paper_2010_04144_gb300 import synth as S
 
     reqs, geos, gen_s = prepared if prepared is not None else serve_requests(args)
-    srv = SV.Server(device=device, storage=args.serve_storage, scheme="aa",
-                    budget_bytes=args.budget_gb * 1e9, chunk_steps=100,
-                    build_workers=args.serve_build_workers, policy=args.serve_policy)
+    ordering, shape, order_ms, tuned_sites = serve_tuning(args, H, device, reqs, geos)
+    srv = SV.Server(device=device, storage=args.serve_storage, scheme=args.serve_scheme,
+                    budget_bytes=args.budget_gb * 1e9, chunk_steps=100, block_size=shape[0],
+                    sites_per_thread=shape[1], kernel_variant=shape[2],
+                    build_workers=args.serve_build_workers, policy=args.serve_policy, ordering=ordering)
     try:
         for r, g in zip(reqs, geos):
             if r.coupled:
@@ -408,18 +445,24 @@ def run_serve(args, H, device, prepared=None):
     mean_work = sum(sites) * args.serve_steps / len(sites) / 1e6
     st["max_sustainable_rate_per_s"] = st["aggregate_mflups"] / mean_work
     st["saturated"] = offered > st["aggregate_mflups"]
+    cfg = {"workload": f"first {len(reqs)} of the seeded 256-request stream (Poisson {args.rate}/s, "
+                       f"sites log-uniform [{args.min_sites:.0e}, {args.max_sites:.0e}], half coupled "
+                       f"pairs, {args.serve_steps} steps each)",
+           "budget_gb": args.budget_gb, "tick_steps": 100, "scheme": args.serve_scheme,
+           "storage": args.serve_storage, "ordering": ordering, "ordering_ms": order_ms,
+           "launch": list(shape), "launch_tuned_on_sites": tuned_sites,
+           "build_workers": args.serve_build_workers, "policy": args.serve_policy,
+           "total_sites": int(sum(sites)), "offered_mflups": offered, "geometry_generation_s": gen_s}
+    return st, cfg
+
+
+def run_serve(args, H, device, prepared=None):
+    st, cfg = serve_stats(args, H, device, prepared)
     line = {"metric": "served time-to-result p50/p99 (s) and aggregate MFLUPS", "value": st["p50_s"],
             "unit": "s (p50 time-to-result)", "p99_s": st["p99_s"], "higher_is_better": False,
-            "aggregate_mflups": st["aggregate_mflups"], "n_gpus": 1, "dtype": args.serve_storage + "-stored/f32-compute",
-            "data": "synthetic (seeded request stream)",
-            "config": {"workload": f"{args.requests} seeded tree requests, Poisson {args.rate}/s, "
-                                   f"sites log-uniform [{args.min_sites:.0e}, {args.max_sites:.0e}], "
-                                   f"half coupled pairs, {args.serve_steps} steps each",
-                       "budget_gb": args.budget_gb, "tick_steps": 100, "scheme": "aa",
-                       "build_workers": args.serve_build_workers, "policy": args.serve_policy,
-                       "total_sites": int(sum(sites)), "offered_mflups": offered,
-                       "geometry_generation_s": gen_s},
-            "serving": st}
+            "aggregate_mflups": st["aggregate_mflups"], "n_gpus": 1,
+            "dtype": args.serve_storage + "-stored/f32-compute", "data": "synthetic (seeded request stream)",
+            "config": cfg, "serving": st}
     print(json.dumps(line))
 
 
@@ -541,7 +584,12 @@ def run_split(args, H, device):
         try:
             if k == 0:
                 obj = ctx.domain(geo.xyz, geo.iolets)
-                launch, _ = autotune(ctx)
+                if args.split_launch:
+                    b, rest = args.split_launch.split("x")
+                    launch = (int(b), *[int(x) for x in rest.split("v")])
+                    ctx.set_launch(*launch)
+                else:
+                    launch, _ = autotune(ctx)
             else:
                 obj = ctx.split(geo.xyz, geo.iolets, k, boundary_weight=args.boundary_weight)
                 ctx.set_launch(*launch)
@@ -571,6 +619,45 @@ def run_split(args, H, device):
                        "boundary_weight": args.boundary_weight},
             "split": rows}
     print(json.dumps(line))
+
+
+def time_large(args, H, device, geo, results):
+    """The precision workload's ~77M-site tree in the 32- and 16-bit forms, each with the
+    ordering and launch shape the ~10M-site tuning chose for it: MFLUPS of the whole step
+    and the stream-collide kernel's fraction of its HBM roofline."""
+    import torch
+
+    peak, _ = hbm_peak()
+    out = {}
+    for key in (("f32", "ab"), ("f32", "aa"), ("f16", "ab"), ("f16", "aa")):
+        if key not in results:
+            continue
+        r = results[key]
+        storage, scheme = key
+        ctx = H.Context(device=device, storage=storage, scheme=scheme)
+        try:
+            d = ctx.domain(geo.xyz, geo.iolets, ordering=r["ordering"])
+            L = r["launch"]
+            ctx.set_launch(L["block"], L["sites_per_thread"], L["kernel_variant"])
+            ctx.step(args.warmup)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            k = 64
+            e0.record(ctx.stream)
+            ctx.step(k)
+            e1.record(ctx.stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / k
+            ms_sc, _ = ctx.step_profiled(16)
+            B = BYTES_PER_UPDATE[key]
+            out[f"{storage}:{scheme}"] = {"mflups": d.n / (ms / 1e3) / 1e6, "ms_per_step": ms,
+                                          "roofline_frac": B * d.n / (ms_sc / 16 / 1e3) / 1e9 / peak,
+                                          "ordering": r["ordering"], "launch": L,
+                                          "device_gb": d.info()["device_bytes"] / 1e9}
+        finally:
+            ctx.close()
+    return {"workload": f"tree d=8 R=40x{args.large_scale} seed=2010041442", "fluid_sites": geo.n,
+            "steps": 64, "forms": out}
 
 
 def run_precision(args, H, device):
@@ -645,9 +732,12 @@ def main():
     ap.add_argument("--variants", default="f32:ab,f32:aa,f16:ab,f16:aa,bf16:aa",
                     help="storage:scheme list; append @BLOCKxSPTvVARIANT to fix a launch shape")
     ap.add_argument("--headline", default="f32:best")
+    ap.add_argument("--min-timed-s", type=float, default=MIN_TIMED_S,
+                    help="device time each variant's repeated K-step measurement covers (0: three)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve", "split"])
     ap.add_argument("--parts", default="2,4,8", help="split config: partition counts to time")
+    ap.add_argument("--split-launch", default="", help="split config: fixed launch BLOCKxSPTvVARIANT (no tuning)")
     ap.add_argument("--boundary-weight", type=float, default=1.0,
                     help="split config: load-balancing cost of a site next to an iolet")
     ap.add_argument("--coupled-scale", type=float, default=2.12)
@@ -670,10 +760,18 @@ def main():
     ap.add_argument("--max-sites", type=float, default=4e7)
     ap.add_argument("--serve-steps", type=int, default=2000)
     ap.add_argument("--serve-storage", default="f16")
+    ap.add_argument("--serve-scheme", default="aa")
+    ap.add_argument("--serve-ordering", default="auto", help="auto (tuned) or morton / rows / bricks")
     ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "backfill"])
     ap.add_argument("--serve-build-workers", type=int, default=1,
                     help="0: build admitted requests inline between ticks; 1: on a worker thread")
     ap.add_argument("--budget-gb", type=float, default=180.0)
+    ap.add_argument("--large-scale", type=float, default=1.84,
+                    help="tree config: scale of the ~77M-site precision tree timed beside the headline "
+                         "(0 skips it)")
+    ap.add_argument("--serve-requests", type=int, default=32,
+                    help="tree config: the first k requests of the serving stream, served beside the "
+                         "headline (0 skips them)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)
     if args.impl == "reference":
@@ -696,6 +794,18 @@ def main():
     rank, ws, local, dist = dist_setup()
     device = local
     torch.cuda.set_device(device)
+    extra_pool = large_pending = serve_pending = None
+    if rank == 0 and ws == 1 and (args.large_scale > 0 or args.serve_requests > 0):
+        # host-side geometry for the large-domain and serving legs, voxelised meanwhile
+        import multiprocessing as mp
+
+        extra_pool = mp.get_context("spawn").Pool(max(1, min(16, os.cpu_count() or 1)))
+        if args.large_scale > 0:
+            large_pending = extra_pool.apply_async(_large_tree, (args.large_scale,))
+        if args.serve_requests > 0:
+            sargs = argparse.Namespace(**vars(args))
+            sargs.requests = args.serve_requests
+            serve_pending = serve_requests(sargs, pool=extra_pool)
     geo, cfg = workload(scale=args.scale)
     cfg["steps_per_job"] = args.steps
     peak, peak_kind = hbm_peak()
@@ -714,7 +824,8 @@ def main():
     try:
         for (storage, scheme, launch, orders) in variants:
             r = time_variant(H, geo, storage, scheme, args.steps, args.warmup, dist, device, sampler,
-                             launch=launch, orderings=orders if launch is None else (orders[0],))
+                             launch=launch, orderings=orders if launch is None else (orders[0],),
+                             min_timed_s=args.min_timed_s)
             B = BYTES_PER_UPDATE[(storage, scheme)]
             r["mflups"] = r["n"] * ws * args.steps / (r["ms"] / 1e3) / 1e6
             r["achieved_gbs"] = B * r["n"] / (r["ms_sc"] / args.steps / 1e3) / 1e9
@@ -767,6 +878,17 @@ def main():
                                    "device_bytes": r["device_bytes"]}
                      for (s, c), r in results.items()},
     }
+    if large_pending is not None:
+        line["large_domain"] = time_large(args, H, device, large_pending.get(), results)
+    if serve_pending is not None:
+        st, scfg = serve_stats(sargs, H, device, prepared=serve_pending())
+        line["serving"] = {"p50_s": st.get("p50_s"), "p99_s": st.get("p99_s"),
+                           "aggregate_mflups": st["aggregate_mflups"], "requests": st["requests"],
+                           "elapsed_s": st["elapsed_s"], "peak_hbm_gb": st["peak_hbm_gb"],
+                           "max_sustainable_rate_per_s": st["max_sustainable_rate_per_s"],
+                           "saturated": st["saturated"], "config": scfg}
+    if extra_pool is not None:
+        extra_pool.close()
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(geo)
     if rank == 0:

@@ -116,7 +116,11 @@ typedef struct {
                                      and written coalesced (AA only, sites_per_thread 1);
                                  5 = 0 on pairs of adjacent sites sharing table loads and
                                      packed stores (A/B with FP16/BF16 storage,
-                                     sites_per_thread 2) */
+                                     sites_per_thread 2);
+                                 6 = AA on pairs of adjacent sites: shared table loads for
+                                     the gathers and the scatter, packed rest values, the
+                                     even step on vector pairs (sites_per_thread 2);
+                                 7 = 6 with L2 256-byte prefetch hints on the loads */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */

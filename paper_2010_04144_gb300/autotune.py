@@ -25,10 +25,11 @@ DEFAULT_CANDIDATES = (
     (128, 2, 2), (256, 2, 2), (256, 1, 2),  # variant 2: AA scheme only
     (256, 1, 3), (128, 1, 3), (256, 2, 3), (128, 2, 3), (512, 2, 3), (128, 4, 3), (256, 4, 3),
     (128, 2, 5), (256, 2, 5), (512, 2, 5),  # variant 5: A/B with 16-bit storage only
+    (128, 2, 6), (256, 2, 6), (256, 2, 7), (512, 2, 7),  # variants 6, 7: AA on site pairs
 )
 # Variant 4 (staged AA odd-step stores) is measured slower than variant 1 on
 # every workload tried; it stays available through Context.set_launch.
-AA_ONLY = (2, 4)
+AA_ONLY = (2, 4, 6, 7)
 AB_16BIT_ONLY = (5,)
 
 

@@ -632,6 +632,62 @@ __device__ __forceinline__ void site_ab_pair(const DomDev &D, const typename St<
     if (slot_b >= 0) D.bnd[slot_b] = mb;
 }
 
+// ---- AA on a pair of adjacent sites (variant 6 / 7: 7 adds L2 prefetch hints) ----
+// Sites s and s+1 (s even) share one 8-byte load per neighbour-table row, both for
+// the gathers and for the re-read that addresses the scatter, and one load and one
+// store of their two rest values; the 18 gathers and 18 scattered stores stay per
+// site.  The odd step reads slot OPP(I) at x - c_I and writes slot I at x + c_I.
+template <int S, bool HINT>
+__device__ __forceinline__ void site_aa_odd_pair(const DomDev &D, typename St<S>::T *buf, int64_t s) {
+    using Tr = St<S>;
+    const int64_t np = D.np;
+    float ga[19], gb[19];
+    Pair<S>::template ld<0>(buf + s, ga[0], gb[0]);
+    unroll<1, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        const int2 nb = __ldg(reinterpret_cast<const int2 *>(D.nbr + (int64_t)(I - 1) * np + s));
+        ga[I] = Tr::template ld<I>(load_rw<HINT>(buf + ((int64_t)OPP(I) * np + nb.x)));
+        gb[I] = Tr::template ld<I>(load_rw<HINT>(buf + ((int64_t)OPP(I) * np + nb.y)));
+    });
+    const int slot_a = iolet_fixup<S>(D, s, ga);
+    const int slot_b = iolet_fixup<S>(D, s + 1, gb);
+    const float4 ma = collide_s<S>(ga, D.omega);
+    const float4 mb = collide_s<S>(gb, D.omega);
+    typename St<S>::T *wb = opaque(buf);
+    const int32_t *nb2 = opaque(D.nbr);  // reread (L1 hits) instead of keeping 36 entries live
+    Pair<S>::template st<0>(wb + s, ga[0], gb[0]);
+    unroll<1, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        const int2 tg = __ldg(reinterpret_cast<const int2 *>(nb2 + (int64_t)(OPP(I) - 1) * np + s));
+        wb[(int64_t)I * np + tg.x] = Tr::template st<I>(ga[I]);
+        wb[(int64_t)I * np + tg.y] = Tr::template st<I>(gb[I]);
+    });
+    if (slot_a >= 0) D.bnd[slot_a] = ma;
+    if (slot_b >= 0) D.bnd[slot_b] = mb;
+}
+
+// AA even step on the same pairs: local, vector loads and stores of both sites.
+template <int S, bool HINT>
+__device__ __forceinline__ void site_aa_even_pair(const DomDev &D, typename St<S>::T *buf, int64_t s) {
+    const int64_t np = D.np;
+    float ga[19], gb[19];
+    unroll<0, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        Pair<S>::template ld<I>(buf + (int64_t)I * np + s, ga[I], gb[I]);
+    });
+    const int slot_a = iolet_fixup<S>(D, s, ga);
+    const int slot_b = iolet_fixup<S>(D, s + 1, gb);
+    const float4 ma = collide_s<S>(ga, D.omega);
+    const float4 mb = collide_s<S>(gb, D.omega);
+    typename St<S>::T *wb = opaque(buf + s);
+    unroll<0, 19>([&](auto ic) {
+        constexpr int I = decltype(ic)::v;
+        Pair<S>::template st<I>(wb + (int64_t)OPP(I) * np, ga[I], gb[I]);
+    });
+    if (slot_a >= 0) D.bnd[slot_a] = ma;
+    if (slot_b >= 0) D.bnd[slot_b] = mb;
+}
+
 template <int S>
 __device__ __forceinline__ void tile_aa_even_pairs(const DomDev &D, const TileDev &tl) {
     using T = typename St<S>::T;
@@ -776,6 +832,20 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
                 tile_aa_even_pairs<S>(D, tl);
             }
         }
+    } else if constexpr (V == 6 || V == 7) {
+        // AA on adjacent pairs: each thread takes sites 2t and 2t+1 of the tile (SPT = 2)
+        static_assert(SCHEME == kAA && SPT == 2, "variants 6 and 7 are the AA pair forms");
+        constexpr bool HINT = V == 7;
+        const int r = 2 * threadIdx.x;
+        const int64_t s = tl.start + r;  // even: tiles start at multiples of 2 * blockDim
+        T *buf = (T *)D.f[0];
+        if (r + 1 < tl.count) {
+            if (odd) site_aa_odd_pair<S, HINT>(D, buf, s);
+            else site_aa_even_pair<S, HINT>(D, buf, s);
+        } else if (r < tl.count) {  // ragged tail: one site
+            if (odd) site_aa_odd<S, HINT>(D, buf, s);
+            else site_aa_even<S, HINT>(D, buf, s);
+        }
     } else if constexpr (V == 5) {
         // A/B on adjacent pairs: each thread takes sites 2t and 2t+1 of the tile (SPT = 2)
         static_assert(SCHEME == kAB && SPT == 2, "variant 5 is the A/B pair form");
@@ -853,6 +923,31 @@ __global__ void __launch_bounds__(512) k_stream_collide_one(const __grid_constan
 }
 
 
+// Several domains per launch, every descriptor in the kernel parameter: each block
+// finds its domain by a uniform binary search over the tile prefix (constant-bank
+// reads), then runs exactly as the one-domain kernel.
+template <int S, int SCHEME, int SPT, int PAR, int V>
+__global__ void __launch_bounds__(512) k_stream_collide_multi(const __grid_constant__ MultiDom M, int off) {
+    extern __shared__ __align__(128) uint32_t stage[];
+    const int b = (int)blockIdx.x;
+    int lo = 0, hi = M.n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (M.first_tile[mid] <= b) lo = mid;
+        else hi = mid - 1;
+    }
+    const DomDev &D = M.d[lo];
+    const int64_t ts = (int64_t)SPT * blockDim.x;
+    TileDev tl;
+    tl.dom = lo;
+    tl.start = (int64_t)(b - M.first_tile[lo]) * ts;
+    tl.count = (int32_t)(M.n_step[lo] - tl.start < ts ? M.n_step[lo] - tl.start : ts);
+    bool odd;
+    if constexpr (PAR == 2) odd = ((__ldg(D.step) + off + 1) & 1) != 0;
+    else odd = PAR == 1;
+    stream_collide_tile<S, SCHEME, SPT, PAR, V>(D, tl, odd, stage);
+}
+
 template <int S, int SCHEME, int PAR, int V, int SPT>
 cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                           int64_t n_tiles, int off, const OneDomain &one, cudaStream_t st) {
@@ -877,6 +972,15 @@ cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileD
             if (e != cudaSuccess) return e;
         }
         return cudaLaunchKernelEx(&lc, k, *one.d, one.n, off);
+    }
+    if (one.multi) {
+        auto k = k_stream_collide_multi<S, SCHEME, SPT, PAR, V>;
+        if (smem > 48 * 1024) {
+            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
+        lc.gridDim = dim3((unsigned)one.multi->first_tile[one.multi->n]);
+        return cudaLaunchKernelEx(&lc, k, *one.multi, off);
     }
     auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
     if (smem > 48 * 1024) {
@@ -913,6 +1017,12 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
         if constexpr (SCHEME != kAB || S == kF32) return cudaErrorInvalidValue;
         else if (cfg.spt != 2) return cudaErrorInvalidValue;
         else return launch_sc_one<S, SCHEME, PAR, 5, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+    }
+    if (cfg.variant == 6 || cfg.variant == 7) {
+        if constexpr (SCHEME != kAA) return cudaErrorInvalidValue;
+        else if (cfg.spt != 2) return cudaErrorInvalidValue;
+        else if (cfg.variant == 6) return launch_sc_one<S, SCHEME, PAR, 6, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+        else return launch_sc_one<S, SCHEME, PAR, 7, 2>(cfg, doms, tiles, n_tiles, off, one, st);
     }
     if (cfg.variant == 2) {
         if (SCHEME == kAB) return cudaErrorInvalidValue;

@@ -355,6 +355,7 @@ struct Plan {
     std::vector<std::pair<size_t, size_t>> halo_blocks;  // (byte offset, bytes) per partition pair
     DomDev one{};       // single-domain plans: the descriptor passed by value to stream-collide
     bool single = false;
+    std::unique_ptr<MultiDom> multi;  // several domains: every descriptor passed by value
     int64_t n_tiles = 0;
     int n_fslots = 0;  // (domain, slot) pairs the body-force pass visits
     int n_ios = 0;
@@ -576,6 +577,7 @@ bool variant_ok(int storage, int scheme, int spt, int variant) {
         case 2: return spt != 4 && scheme == HG_SCHEME_AA;
         case 4: return spt == 1 && scheme == HG_SCHEME_AA;
         case 5: return spt == 2 && scheme == HG_SCHEME_AB && storage != HG_STORE_F32;
+        case 6: case 7: return spt == 2 && scheme == HG_SCHEME_AA;
         default: return false;
     }
 }
@@ -1337,6 +1339,19 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     if (doms.size() == 1) {
         p->single = true;
         p->one = make_domdev(ctx, ctx->doms[doms[0]]);
+    } else if (doms.size() <= (size_t)kMaxParamDoms) {
+        p->multi.reset(new MultiDom());
+        MultiDom &M = *p->multi;
+        M.n = (int32_t)doms.size();
+        int32_t t = 0;
+        for (size_t j = 0; j < doms.size(); ++j) {
+            hg_domain *d = ctx->doms[doms[j]];
+            M.first_tile[j] = t;
+            M.n_step[j] = d->n;
+            M.d[j] = make_domdev(ctx, d);
+            t += (int32_t)((d->n + ts - 1) / ts);
+        }
+        M.first_tile[doms.size()] = t;
     }
     p->n_chunks = (int)chunks.size();
     int rc = dev_alloc(ctx, p->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TileDev));
@@ -1427,7 +1442,7 @@ cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
         // after the first step of a group the previous kernel is this group's iolet update
         // (the first follows the step-counter advance, which the parity read needs)
         const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
-                            (const int64_t *)ctx->steps.p, off > 0 && p->n_ios > 0};
+                            (const int64_t *)ctx->steps.p, off > 0 && p->n_ios > 0, p->multi.get()};
         cudaError_t e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p,
                                               (const TileDev *)p->tiles.p, p->n_tiles, (int)off,
                                               step_parity(ctx, mode, off), one, ctx->stream);
@@ -1548,7 +1563,7 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float
     for (int64_t j = 0; j < n && e == cudaSuccess; ++j) {
         cudaEventRecord(ev[3 * j], ctx->stream);
         const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
-                            (const int64_t *)ctx->steps.p, false};  // timed launches stay serial
+                            (const int64_t *)ctx->steps.p, false, p->multi.get()};  // timed launches stay serial
         e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
                                   p->n_tiles, (int)j, step_parity(ctx, mode, j), one, ctx->stream);
         cudaEventRecord(ev[3 * j + 1], ctx->stream);
@@ -1591,8 +1606,9 @@ int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) 
     if (spt != 1 && spt != 2 && spt != 4) return fail(ctx, HG_ERR_ARG, "sites per thread must be 1, 2 or 4");
     if (!variant_ok(ctx->storage, ctx->scheme, spt, variant))
         return fail(ctx, HG_ERR_ARG, "kernel variant must be 0 or 3, 1 or 2 with 1 or 2 sites per thread "
-                                     "(2: AA only), 4 with 1 site per thread (AA only), or 5 with 2 sites "
-                                     "per thread (A/B, 16-bit storage only)");
+                                     "(2: AA only), 4 with 1 site per thread (AA only), 5 with 2 sites "
+                                     "per thread (A/B, 16-bit storage only), or 6 or 7 with 2 sites per "
+                                     "thread (AA only)");
     if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1947,6 +1963,19 @@ int split_plan(hg_split *sp, Plan *&out) {
     p->n_tiles = (int64_t)tiles.size();
     p->n_ios = (int)ios.size();
     p->n_chunks = (int)chunks.size();
+    if (sp->parts.size() <= (size_t)kMaxParamDoms) {
+        p->multi.reset(new MultiDom());
+        MultiDom &M = *p->multi;
+        M.n = (int32_t)sp->parts.size();
+        int32_t t = 0;
+        for (size_t j = 0; j < sp->parts.size(); ++j) {
+            M.first_tile[j] = t;
+            M.n_step[j] = sp->parts[j].n_own;
+            M.d[j] = sp->parts[j].dev;
+            t += (int32_t)((sp->parts[j].n_own + ts - 1) / ts);
+        }
+        M.first_tile[sp->parts.size()] = t;
+    }
     p->n_halo = (int64_t)sp->pack.size();
     p->halo_elem = (int)elem_bytes(ctx->storage);
     for (const auto &b : sp->blocks)

@@ -102,7 +102,7 @@ class Server:
 
     def __init__(self, device=0, storage="f16", scheme="aa", budget_bytes=180e9, chunk_steps=100,
                  block_size=0, sites_per_thread=0, kernel_variant=None, graph_steps=0,
-                 build_workers=1, policy="fifo"):
+                 build_workers=1, policy="fifo", ordering="morton"):
         st = H.STORAGE[storage] if isinstance(storage, str) else storage
         sc = H.SCHEME[scheme] if isinstance(scheme, str) else scheme
         if kernel_variant is None:
@@ -113,6 +113,7 @@ class Server:
                              sites_per_thread=sites_per_thread, kernel_variant=kernel_variant,
                              graph_steps=graph_steps)
         self.storage, self.scheme = st, sc
+        self.ordering = ordering          # device site layout of every request's domains
         self.budget = float(budget_bytes)
         self.chunk = int(chunk_steps)
         self.queue: list[Job] = []
@@ -166,7 +167,8 @@ class Server:
         return False
 
     def _estimate(self, job):
-        return sum(geometry_footprint(g, self.storage, self.scheme) for g in job.geoms)
+        return sum(geometry_footprint(g, self.storage, self.scheme, reordered=self.ordering != "morton")
+                   for g in job.geoms)
 
     def _build(self, job):
         """Host build and upload of a job's domains (worker thread; touches no server state)."""
@@ -174,7 +176,7 @@ class Server:
         doms = []
         try:
             for g in job.geoms:
-                doms.append(self.ctx.domain(g.xyz, g.iolets, tau=job.tau))
+                doms.append(self.ctx.domain(g.xyz, g.iolets, tau=job.tau, ordering=self.ordering))
         except Exception as e:  # noqa: BLE001 -- handed to the main thread
             return doms, e, time.perf_counter() - t
         return doms, None, time.perf_counter() - t

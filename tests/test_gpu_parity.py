@@ -258,7 +258,8 @@ LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128,
             ("aa", 64, 2, 1), ("aa", 128, 2, 2), ("aa", 256, 1, 2), ("aa", 64, 2, 2),
             ("ab", 256, 1, 3), ("ab", 128, 4, 3), ("aa", 256, 1, 3), ("aa", 128, 2, 3),
             ("aa", 256, 1, 4), ("aa", 64, 1, 4), ("aa", 512, 1, 4),
-            ("ab", 256, 2, 5), ("ab", 64, 2, 5)]   # variant 5: A/B, 16-bit storage only
+            ("ab", 256, 2, 5), ("ab", 64, 2, 5),   # variant 5: A/B, 16-bit storage only
+            ("aa", 256, 2, 6), ("aa", 64, 2, 6), ("aa", 128, 2, 7), ("aa", 512, 2, 7)]  # AA pairs
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])

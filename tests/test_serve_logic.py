@@ -39,7 +39,7 @@ class _Ctx:
         self.calls = []
         self.live = []
 
-    def domain(self, xyz, iolets, tau=0.8):
+    def domain(self, xyz, iolets, tau=0.8, ordering="morton"):
         d = _Dom(self, len(xyz), iolets)
         self.live.append(d)
         return d
@@ -159,14 +159,14 @@ class _SlowCtx(_Ctx):
 
     delay = 0.3
 
-    def domain(self, xyz, iolets, tau=0.8):
+    def domain(self, xyz, iolets, tau=0.8, ordering="morton"):
         if len(xyz) >= 2000:
             import time
 
             time.sleep(self.delay)
         if len(xyz) == 1234:
             raise SV.H.HgError(-1, "build failed")
-        return super().domain(xyz, iolets, tau)
+        return super().domain(xyz, iolets, tau, ordering)
 
     def sync(self):
         import time
