@@ -574,7 +574,7 @@ def run_split(args, H, device):
     the same domain unsplit; results are bit-identical, so only the time differs."""
     import torch
 
-    from paper_2010_04144_gb300.autotune import autotune
+    from paper_2010_04144_gb300.autotune import autotune, autotune_split
 
     geo, cfg = workload(scale=args.scale)
     rows = []
@@ -592,7 +592,11 @@ def run_split(args, H, device):
                     launch, _ = autotune(ctx)
             else:
                 obj = ctx.split(geo.xyz, geo.iolets, k, boundary_weight=args.boundary_weight)
-                ctx.set_launch(*launch)
+                if args.split_launch:
+                    ctx.set_launch(*launch)
+                    split_shape = launch
+                else:
+                    split_shape, _ = autotune_split(ctx, obj)
             obj.step(args.warmup) if k else ctx.step(args.warmup)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -604,7 +608,8 @@ def run_split(args, H, device):
             halo = sum(obj.info(p)["halo_in"] for p in range(k)) if k else 0
             ghosts = sum(obj.info(p)["ghosts"] for p in range(k)) if k else 0
             rows.append({"parts": k, "ms_per_step": ms, "mflups": geo.n / (ms / 1e3) / 1e6,
-                         "halo_values_per_step": halo, "ghost_sites": ghosts})
+                         "halo_values_per_step": halo, "ghost_sites": ghosts,
+                         "launch": list(launch if k == 0 else split_shape)})
         finally:
             ctx.close()
     base = rows[0]["ms_per_step"]
@@ -777,14 +782,19 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     if args.config != "tree":
+        # single-device workloads: under a multi-rank launch rank 0 runs them on its own
+        # device and the other ranks exit without work
+        if int(os.environ.get("RANK", "0")) != 0:
+            return
         import torch
 
         from paper_2010_04144_gb300 import hemegb as H
 
         H.lib()
-        torch.cuda.set_device(0)
+        device = int(os.environ.get("LOCAL_RANK", "0"))
+        torch.cuda.set_device(device)
         return {"coupled": run_coupled, "precision": run_precision, "serve": run_serve,
-                "split": run_split}[args.config](args, H, 0)
+                "split": run_split}[args.config](args, H, device)
 
     import torch
 

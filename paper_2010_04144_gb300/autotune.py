@@ -123,3 +123,29 @@ def tune_ordering(make_ctx, orderings=("morton", "rows", "bricks"), candidates=D
             ctx.close()
     o = min(table, key=lambda k: table[k][1])
     return o, table[o][0], table
+
+
+def autotune_split(ctx, split, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2):
+    """Launch shape of a split domain's stream-collide (the multi-domain entry kernel
+    its partitions run in): every candidate timed with CUDA events around `steps`
+    whole steps.  A split keeps no checkpoint, so tuning advances it; every shape
+    computes the same bits.  Returns (best, {candidate: ms per step})."""
+    import torch
+
+    if ctx.scheme != 1:
+        candidates = [c for c in candidates if c[2] not in AA_ONLY]
+    if ctx.scheme != 0 or ctx.storage == 0:
+        candidates = [c for c in candidates if c[2] not in AB_16BIT_ONLY]
+    timing = {}
+    for cand in candidates:
+        ctx.set_launch(*cand)
+        split.step(warmup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(ctx.stream)
+        split.step(steps)
+        e1.record(ctx.stream)
+        e1.synchronize()
+        timing[tuple(cand)] = e0.elapsed_time(e1) / steps
+    best = min(timing, key=timing.get)
+    ctx.set_launch(*best)
+    return best, timing
