@@ -768,8 +768,8 @@ def main():
     ap.add_argument("--serve-scheme", default="aa")
     ap.add_argument("--serve-ordering", default="auto", help="auto (tuned) or morton / rows / bricks")
     ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "backfill"])
-    ap.add_argument("--serve-build-workers", type=int, default=1,
-                    help="0: build admitted requests inline between ticks; 1: on a worker thread")
+    ap.add_argument("--serve-build-workers", type=int, default=4,
+                    help="0: build admitted requests inline between ticks; k: on k worker threads")
     ap.add_argument("--budget-gb", type=float, default=180.0)
     ap.add_argument("--large-scale", type=float, default=1.84,
                     help="tree config: scale of the ~77M-site precision tree timed beside the headline "

@@ -38,6 +38,18 @@ __host__ __device__ constexpr double WD(int i) {
     return i == 0 ? (1.0 / 3.0) : (i <= 6 ? (1.0 / 18.0) : (1.0 / 36.0));
 }
 
+// Lattice weights in FP32 as an unevaluated sum hi + lo (hi = w rounded to FP32,
+// lo = the remainder rounded to FP32): a product w x is formed as fma(hi, x, lo x),
+// good to about one rounding of the product.  With w rounded once to FP32 every
+// product would carry the weight's own relative error (up to 3e-8, the same sign at
+// every site and step), so the FP32 equilibrium would gain or lose mass and momentum
+// by that fraction in every collision -- a bias that accumulates over thousands of
+// steps, where the rounding of the products themselves varies and averages out.
+__host__ __device__ constexpr float WLO(int i) { return (float)(WD(i) - (double)W(i)); }
+template <int I> __device__ __forceinline__ float mulw(float x) {
+    return __fmaf_rn(W(I), x, __fmul_rn(WLO(I), x));
+}
+
 // ---- storage traits ----
 // ld/st convert between storage and the collision variable: FP32 stores f~ and
 // collides on f~; FP16/BF16 store h = f~/w (avoids subnormals) and collide on h
@@ -57,7 +69,7 @@ template <> struct St<kF16> {
     static constexpr bool kScaled = true;
     template <int I> static __device__ __forceinline__ float ld(T v) { return __half2float(v); }
     template <int I> static __device__ __forceinline__ T st(float v) { return __float2half_rn(v); }
-    template <int I> static __device__ __forceinline__ float phys(T v) { return __half2float(v) * W(I); }
+    template <int I> static __device__ __forceinline__ float phys(T v) { return mulw<I>(__half2float(v)); }
     static __device__ __forceinline__ double ldd(T v, int i) { return __dmul_rn((double)__half2float(v), WD(i)); }
 };
 template <> struct St<kBF16> {
@@ -65,7 +77,7 @@ template <> struct St<kBF16> {
     static constexpr bool kScaled = true;
     template <int I> static __device__ __forceinline__ float ld(T v) { return __bfloat162float(v); }
     template <int I> static __device__ __forceinline__ T st(float v) { return __float2bfloat16_rn(v); }
-    template <int I> static __device__ __forceinline__ float phys(T v) { return __bfloat162float(v) * W(I); }
+    template <int I> static __device__ __forceinline__ float phys(T v) { return mulw<I>(__bfloat162float(v)); }
     static __device__ __forceinline__ double ldd(T v, int i) { return __dmul_rn((double)__bfloat162float(v), WD(i)); }
 };
 
@@ -84,7 +96,7 @@ template <int B, int E, typename F> __device__ __forceinline__ void unroll(F &&f
 template <int I, bool SC>
 __device__ __forceinline__ float iolet_rule(const DomDev &D, int k, int slot, float raw) {
     const float val = D.bcv[k];
-    if (D.io_kind[k] == 0) return -raw + (SC ? 2.0f : 2.0f * W(I)) * val;  // anti-bounce-back
+    if (D.io_kind[k] == 0) return -raw + (SC ? 2.0f * val : mulw<I>(2.0f * val));  // anti-bounce-back
     return raw + val * D.coef[(int64_t)slot * 18 + (I - 1)];              // moving wall
 }
 
@@ -97,25 +109,30 @@ __device__ __forceinline__ float iolet_rule(const DomDev &D, int k, int slot, fl
 #define HG_SUB __fsub_rn
 #define HG_FMA __fmaf_rn
 
+// SC: the scaled variable h = f~/w (16-bit storage), whose equilibrium carries no
+// weight; otherwise f~, whose equilibrium is w times that (split-weight products).
+template <bool SC>
 __device__ __forceinline__ void relax_pairs(float g[19], float omega, float base, float rho,
-                                            float ux, float uy, float uz, float w1, float w2) {
+                                            float ux, float uy, float uz) {
     const float r45 = HG_MUL(4.5f, rho), r3 = HG_MUL(3.0f, rho);
-    auto pair = [&](int a, int b, float w, float cu) {
+    auto pair = [&](auto ia, int b, float cu) {
+        constexpr int a = decltype(ia)::v;
         const float q = HG_FMA(HG_MUL(r45, cu), cu, base);    // base + 4.5 rho cu^2
-        const float sym = HG_MUL(w, q);
-        const float asym = HG_MUL(w, HG_MUL(r3, cu));
+        const float c3 = HG_MUL(r3, cu);
+        const float sym = SC ? q : mulw<a>(q);
+        const float asym = SC ? c3 : mulw<a>(c3);
         g[a] = HG_FMA(omega, HG_SUB(HG_ADD(sym, asym), g[a]), g[a]);
         g[b] = HG_FMA(omega, HG_SUB(HG_SUB(sym, asym), g[b]), g[b]);
     };
-    pair(1, 2, w1, ux);
-    pair(3, 4, w1, uy);
-    pair(5, 6, w1, uz);
-    pair(7, 8, w2, HG_ADD(ux, uy));
-    pair(9, 10, w2, HG_SUB(ux, uy));
-    pair(11, 12, w2, HG_ADD(ux, uz));
-    pair(13, 14, w2, HG_SUB(ux, uz));
-    pair(15, 16, w2, HG_ADD(uy, uz));
-    pair(17, 18, w2, HG_SUB(uy, uz));
+    pair(IC<1>{}, 2, ux);
+    pair(IC<3>{}, 4, uy);
+    pair(IC<5>{}, 6, uz);
+    pair(IC<7>{}, 8, HG_ADD(ux, uy));
+    pair(IC<9>{}, 10, HG_SUB(ux, uy));
+    pair(IC<11>{}, 12, HG_ADD(ux, uz));
+    pair(IC<13>{}, 14, HG_SUB(ux, uz));
+    pair(IC<15>{}, 16, HG_ADD(uy, uz));
+    pair(IC<17>{}, 18, HG_SUB(uy, uz));
 }
 
 struct Moments {
@@ -147,8 +164,8 @@ __device__ __forceinline__ float4 collide(float g[19], float omega) {
     const float jy = HG_ADD(HG_ADD(HG_SUB(HG_ADD(d34, d78), d910), d1516), d1718);
     const float jz = HG_SUB(HG_ADD(HG_SUB(HG_ADD(d56, d1112), d1314), d1516), d1718);
     const Moments m = finish_moments(drho, jx, jy, jz);
-    g[0] = HG_FMA(omega, HG_SUB(HG_MUL(W(0), m.base), g[0]), g[0]);
-    relax_pairs(g, omega, m.base, m.rho, m.ux, m.uy, m.uz, W(1), W(7));
+    g[0] = HG_FMA(omega, HG_SUB(mulw<0>(m.base), g[0]), g[0]);
+    relax_pairs<false>(g, omega, m.base, m.rho, m.ux, m.uy, m.uz);
     return make_float4(m.drho, m.ux, m.uy, m.uz);
 }
 
@@ -160,19 +177,19 @@ __device__ __forceinline__ float4 collide_scaled(float g[19], float omega) {
     const float sd = HG_ADD(HG_ADD(HG_ADD(HG_ADD(g[7], g[8]), HG_ADD(g[9], g[10])),
                                    HG_ADD(HG_ADD(g[11], g[12]), HG_ADD(g[13], g[14]))),
                             HG_ADD(HG_ADD(g[15], g[16]), HG_ADD(g[17], g[18])));
-    const float drho = HG_FMA(W(0), g[0], HG_FMA(W(1), sa, HG_MUL(W(7), sd)));
+    const float drho = HG_ADD(mulw<0>(g[0]), HG_ADD(mulw<1>(sa), mulw<7>(sd)));
     const float d12 = HG_SUB(g[1], g[2]), d34 = HG_SUB(g[3], g[4]), d56 = HG_SUB(g[5], g[6]);
     const float d78 = HG_SUB(g[7], g[8]), d910 = HG_SUB(g[9], g[10]), d1112 = HG_SUB(g[11], g[12]);
     const float d1314 = HG_SUB(g[13], g[14]), d1516 = HG_SUB(g[15], g[16]), d1718 = HG_SUB(g[17], g[18]);
     const float ex = HG_ADD(HG_ADD(d78, d910), HG_ADD(d1112, d1314));
     const float ey = HG_ADD(HG_SUB(d78, d910), HG_ADD(d1516, d1718));
     const float ez = HG_ADD(HG_SUB(d1112, d1314), HG_SUB(d1516, d1718));
-    const float jx = HG_FMA(W(1), d12, HG_MUL(W(7), ex));
-    const float jy = HG_FMA(W(1), d34, HG_MUL(W(7), ey));
-    const float jz = HG_FMA(W(1), d56, HG_MUL(W(7), ez));
+    const float jx = HG_ADD(mulw<1>(d12), mulw<7>(ex));
+    const float jy = HG_ADD(mulw<1>(d34), mulw<7>(ey));
+    const float jz = HG_ADD(mulw<1>(d56), mulw<7>(ez));
     const Moments m = finish_moments(drho, jx, jy, jz);
     g[0] = HG_FMA(omega, HG_SUB(m.base, g[0]), g[0]);
-    relax_pairs(g, omega, m.base, m.rho, m.ux, m.uy, m.uz, 1.0f, 1.0f);
+    relax_pairs<true>(g, omega, m.base, m.rho, m.ux, m.uy, m.uz);
     return make_float4(m.drho, m.ux, m.uy, m.uz);
 }
 
@@ -910,6 +927,10 @@ __global__ void __launch_bounds__(512) k_stream_collide(const DomDev *__restrict
 template <int S, int SCHEME, int SPT, int PAR, int V>
 __global__ void __launch_bounds__(512) k_stream_collide_one(const __grid_constant__ DomDev D, int64_t n,
                                                             int off) {
+    // a launch chained after this one (the next domain of a per-domain launch
+    // sequence) may be scheduled once every block here has started; kernels launched
+    // without programmatic serialisation ignore the trigger
+    asm volatile("griddepcontrol.launch_dependents;");
     extern __shared__ __align__(128) uint32_t stage[];
     const int64_t ts = (int64_t)SPT * blockDim.x;
     TileDev tl;
@@ -922,31 +943,6 @@ __global__ void __launch_bounds__(512) k_stream_collide_one(const __grid_constan
     stream_collide_tile<S, SCHEME, SPT, PAR, V>(D, tl, odd, stage);
 }
 
-
-// Several domains per launch, every descriptor in the kernel parameter: each block
-// finds its domain by a uniform binary search over the tile prefix (constant-bank
-// reads), then runs exactly as the one-domain kernel.
-template <int S, int SCHEME, int SPT, int PAR, int V>
-__global__ void __launch_bounds__(512) k_stream_collide_multi(const __grid_constant__ MultiDom M, int off) {
-    extern __shared__ __align__(128) uint32_t stage[];
-    const int b = (int)blockIdx.x;
-    int lo = 0, hi = M.n - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (M.first_tile[mid] <= b) lo = mid;
-        else hi = mid - 1;
-    }
-    const DomDev &D = M.d[lo];
-    const int64_t ts = (int64_t)SPT * blockDim.x;
-    TileDev tl;
-    tl.dom = lo;
-    tl.start = (int64_t)(b - M.first_tile[lo]) * ts;
-    tl.count = (int32_t)(M.n_step[lo] - tl.start < ts ? M.n_step[lo] - tl.start : ts);
-    bool odd;
-    if constexpr (PAR == 2) odd = ((__ldg(D.step) + off + 1) & 1) != 0;
-    else odd = PAR == 1;
-    stream_collide_tile<S, SCHEME, SPT, PAR, V>(D, tl, odd, stage);
-}
 
 template <int S, int SCHEME, int PAR, int V, int SPT>
 cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
@@ -972,15 +968,6 @@ cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileD
             if (e != cudaSuccess) return e;
         }
         return cudaLaunchKernelEx(&lc, k, *one.d, one.n, off);
-    }
-    if (one.multi) {
-        auto k = k_stream_collide_multi<S, SCHEME, SPT, PAR, V>;
-        if (smem > 48 * 1024) {
-            cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
-        }
-        lc.gridDim = dim3((unsigned)one.multi->first_tile[one.multi->n]);
-        return cudaLaunchKernelEx(&lc, k, *one.multi, off);
     }
     auto k = k_stream_collide<S, SCHEME, SPT, PAR, V>;
     if (smem > 48 * 1024) {

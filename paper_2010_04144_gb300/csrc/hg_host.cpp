@@ -339,6 +339,13 @@ struct DevBuf {
 }  // namespace
 
 // ================================================================ objects
+// Plans over at most this many domains, each at least this large, launch
+// stream-collide once per domain (the single-domain kernel reads its descriptor
+// from the parameter bank at fixed offsets; the tile-table kernel copies it into
+// shared memory behind a barrier, measured 15-20 % slower per launch).
+constexpr int kSeparateMaxDoms = 8;
+constexpr int64_t kSeparateMinSites = (int64_t)1 << 20;
+
 struct PlanKey {
     std::vector<int32_t> doms;
     bool operator<(const PlanKey &o) const { return doms < o.doms; }
@@ -355,7 +362,11 @@ struct Plan {
     std::vector<std::pair<size_t, size_t>> halo_blocks;  // (byte offset, bytes) per partition pair
     DomDev one{};       // single-domain plans: the descriptor passed by value to stream-collide
     bool single = false;
-    std::unique_ptr<MultiDom> multi;  // several domains: every descriptor passed by value
+    // a few large domains (a coupled pair, a split's partitions): one single-domain
+    // launch each instead of one tile-table launch, chained by programmatic dependent
+    // launch; descriptor and sites stepped per launch
+    std::vector<DomDev> sep;
+    std::vector<int64_t> sep_n;
     int64_t n_tiles = 0;
     int n_fslots = 0;  // (domain, slot) pairs the body-force pass visits
     int n_ios = 0;
@@ -1339,19 +1350,14 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     if (doms.size() == 1) {
         p->single = true;
         p->one = make_domdev(ctx, ctx->doms[doms[0]]);
-    } else if (doms.size() <= (size_t)kMaxParamDoms) {
-        p->multi.reset(new MultiDom());
-        MultiDom &M = *p->multi;
-        M.n = (int32_t)doms.size();
-        int32_t t = 0;
-        for (size_t j = 0; j < doms.size(); ++j) {
-            hg_domain *d = ctx->doms[doms[j]];
-            M.first_tile[j] = t;
-            M.n_step[j] = d->n;
-            M.d[j] = make_domdev(ctx, d);
-            t += (int32_t)((d->n + ts - 1) / ts);
-        }
-        M.first_tile[doms.size()] = t;
+    } else if (doms.size() <= (size_t)kSeparateMaxDoms) {
+        bool large = true;
+        for (int32_t di : doms) large = large && ctx->doms[di]->n >= kSeparateMinSites;
+        if (large)
+            for (int32_t di : doms) {
+                p->sep.push_back(make_domdev(ctx, ctx->doms[di]));
+                p->sep_n.push_back(ctx->doms[di]->n);
+            }
     }
     p->n_chunks = (int)chunks.size();
     int rc = dev_alloc(ctx, p->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TileDev));
@@ -1436,16 +1442,34 @@ cudaError_t enqueue_halo(hg_ctx *ctx, Plan *p, int off) {
                               p->recv.p, off, ctx->stream);
 }
 
-cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
+// The stream-collide launch(es) of step offset `off`.  overlap: the first launch may
+// start while the previous step's iolet update runs; separate per-domain launches
+// after the first may start while the previous one runs (they share no data within
+// a step; sites with iolet links still wait, through the chain, for that update).
+cudaError_t launch_sc(hg_ctx *ctx, Plan *p, int off, int parity, bool overlap) {
     CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
+    const int64_t *steps = (const int64_t *)ctx->steps.p;
+    const DomDev *table = (const DomDev *)ctx->dom_table.p;
+    if (!p->sep.empty()) {
+        const int64_t ts = (int64_t)ctx->block * ctx->spt;
+        for (size_t j = 0; j < p->sep.size(); ++j) {
+            if (p->sep_n[j] == 0) continue;
+            const OneDomain one{&p->sep[j], p->sep_n[j], steps, j > 0 || overlap};
+            const cudaError_t e = launch_stream_collide(cfg, table, nullptr, (p->sep_n[j] + ts - 1) / ts, off,
+                                                        parity, one, ctx->stream);
+            if (e != cudaSuccess) return e;
+        }
+        return cudaSuccess;
+    }
+    const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0, steps, overlap};
+    return launch_stream_collide(cfg, table, (const TileDev *)p->tiles.p, p->n_tiles, off, parity, one, ctx->stream);
+}
+
+cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
     for (int64_t off = 0; off < k; ++off) {
         // after the first step of a group the previous kernel is this group's iolet update
         // (the first follows the step-counter advance, which the parity read needs)
-        const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
-                            (const int64_t *)ctx->steps.p, off > 0 && p->n_ios > 0, p->multi.get()};
-        cudaError_t e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p,
-                                              (const TileDev *)p->tiles.p, p->n_tiles, (int)off,
-                                              step_parity(ctx, mode, off), one, ctx->stream);
+        cudaError_t e = launch_sc(ctx, p, (int)off, step_parity(ctx, mode, off), off > 0 && p->n_ios > 0);
         if (e != cudaSuccess) return e;
         e = launch_guo_force(ctx->storage, ctx->scheme, (const DomDev *)ctx->dom_table.p,
                              (const int2 *)p->fslots.p, p->n_fslots, (int)off, ctx->stream);
@@ -1557,15 +1581,11 @@ int hg_step_profiled(hg_ctx *ctx, int64_t n, double *ms_sc, double *ms_io, float
     if (rc != HG_OK) return rc;
     std::vector<cudaEvent_t> ev((size_t)3 * n);
     for (auto &x : ev) CU(ctx, cudaEventCreate(&x));
-    CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
     const int mode = parity_mode(ctx, doms);
     cudaError_t e = cudaSuccess;
     for (int64_t j = 0; j < n && e == cudaSuccess; ++j) {
         cudaEventRecord(ev[3 * j], ctx->stream);
-        const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0,
-                            (const int64_t *)ctx->steps.p, false, p->multi.get()};  // timed launches stay serial
-        e = launch_stream_collide(cfg, (const DomDev *)ctx->dom_table.p, (const TileDev *)p->tiles.p,
-                                  p->n_tiles, (int)j, step_parity(ctx, mode, j), one, ctx->stream);
+        e = launch_sc(ctx, p, (int)j, step_parity(ctx, mode, j), false);  // timed launches stay serial
         cudaEventRecord(ev[3 * j + 1], ctx->stream);
         if (e == cudaSuccess)  // the body-force pass (if any) is timed with the iolet update
             e = launch_guo_force(ctx->storage, ctx->scheme, (const DomDev *)ctx->dom_table.p,
@@ -1963,19 +1983,11 @@ int split_plan(hg_split *sp, Plan *&out) {
     p->n_tiles = (int64_t)tiles.size();
     p->n_ios = (int)ios.size();
     p->n_chunks = (int)chunks.size();
-    if (sp->parts.size() <= (size_t)kMaxParamDoms) {
-        p->multi.reset(new MultiDom());
-        MultiDom &M = *p->multi;
-        M.n = (int32_t)sp->parts.size();
-        int32_t t = 0;
-        for (size_t j = 0; j < sp->parts.size(); ++j) {
-            M.first_tile[j] = t;
-            M.n_step[j] = sp->parts[j].n_own;
-            M.d[j] = sp->parts[j].dev;
-            t += (int32_t)((sp->parts[j].n_own + ts - 1) / ts);
+    if (sp->parts.size() <= 64)
+        for (const SplitPart &P : sp->parts) {
+            p->sep.push_back(P.dev);
+            p->sep_n.push_back(P.n_own);
         }
-        M.first_tile[sp->parts.size()] = t;
-    }
     p->n_halo = (int64_t)sp->pack.size();
     p->halo_elem = (int)elem_bytes(ctx->storage);
     for (const auto &b : sp->blocks)

@@ -41,22 +41,8 @@ struct DomDev {
     const float4 *io_force;   // per iolet: body-force density on its adjacent sites (null = none)
 };
 
-// A launch over up to kMaxParamDoms domains with every descriptor in the kernel
-// parameter (constant bank): block b belongs to the domain whose tile range
-// [first_tile[d], first_tile[d + 1]) holds b and steps sites [tile * T, tile * T + T)
-// of it, T = threads x sites per thread; no tile table, no descriptor copy, no
-// barrier before the first load.
-constexpr int kMaxParamDoms = 96;
-struct MultiDom {
-    int32_t n;                              // domains
-    int32_t first_tile[kMaxParamDoms + 1];  // tiles before domain d (prefix)
-    int32_t pad;
-    int64_t n_step[kMaxParamDoms];          // sites stepped: device positions [0, n_step)
-    DomDev d[kMaxParamDoms];
-};
-
 // A launch over one domain only: its descriptor (host copy, passed by value as a
-// kernel parameter) and site count; d == nullptr means "use multi, else the tile table".
+// kernel parameter) and site count; d == nullptr means "use the tile table".
 // steps: the context's per-domain step counters (indexed by TileDev::dom).
 // overlap_previous: the launch directly follows the previous step's iolet update
 // on the stream and may start before it ends (programmatic dependent launch);
@@ -66,7 +52,6 @@ struct OneDomain {
     int64_t n;
     const int64_t *steps;
     bool overlap_previous;
-    const MultiDom *multi;  // host copy passed by value (null: the tile table)
 };
 
 // One block of the stream-collide grid: `count` sites of domain `dom` from `start`.

@@ -183,24 +183,25 @@ __device__ __forceinline__ void guo_delta(float4 m, float fx, float fy, float fz
     const float b = HG_FMA(-0.5f, omega, 1.0f);
     // isotropic part shared by every direction: a (-1.5 (u_F^2 - u^2)) + b (-3 u_F.F)
     const float iso = HG_FMA(a, HG_MUL(-1.5f, HG_SUB(vsq, usq)), HG_MUL(b, HG_MUL(-3.0f, vf)));
-    d[0] = HG_MUL(SC ? 1.0f : W(0), iso);
-    auto pair = [&](int A, int B, float w, float cu, float cv, float cf) {
+    d[0] = SC ? iso : mulw<0>(iso);
+    auto pair = [&](auto iA, int B, float cu, float cv, float cf) {
+        constexpr int A = decltype(iA)::v;
         const float sym = HG_FMA(a, HG_MUL(4.5f, HG_SUB(HG_MUL(cv, cv), HG_MUL(cu, cu))),
                                  HG_FMA(b, HG_MUL(9.0f, HG_MUL(cv, cf)), iso));
         const float asym = HG_MUL(3.0f, HG_FMA(a, HG_SUB(cv, cu), HG_MUL(b, cf)));
-        d[A] = HG_MUL(w, HG_ADD(sym, asym));
-        d[B] = HG_MUL(w, HG_SUB(sym, asym));
+        const float p = HG_ADD(sym, asym), q = HG_SUB(sym, asym);
+        d[A] = SC ? p : mulw<A>(p);
+        d[B] = SC ? q : mulw<A>(q);
     };
-    const float w1 = SC ? 1.0f : W(1), w2 = SC ? 1.0f : W(7);
-    pair(1, 2, w1, m.y, vx, fx);
-    pair(3, 4, w1, m.z, vy, fy);
-    pair(5, 6, w1, m.w, vz, fz);
-    pair(7, 8, w2, HG_ADD(m.y, m.z), HG_ADD(vx, vy), HG_ADD(fx, fy));
-    pair(9, 10, w2, HG_SUB(m.y, m.z), HG_SUB(vx, vy), HG_SUB(fx, fy));
-    pair(11, 12, w2, HG_ADD(m.y, m.w), HG_ADD(vx, vz), HG_ADD(fx, fz));
-    pair(13, 14, w2, HG_SUB(m.y, m.w), HG_SUB(vx, vz), HG_SUB(fx, fz));
-    pair(15, 16, w2, HG_ADD(m.z, m.w), HG_ADD(vy, vz), HG_ADD(fy, fz));
-    pair(17, 18, w2, HG_SUB(m.z, m.w), HG_SUB(vy, vz), HG_SUB(fy, fz));
+    pair(IC<1>{}, 2, m.y, vx, fx);
+    pair(IC<3>{}, 4, m.z, vy, fy);
+    pair(IC<5>{}, 6, m.w, vz, fz);
+    pair(IC<7>{}, 8, HG_ADD(m.y, m.z), HG_ADD(vx, vy), HG_ADD(fx, fy));
+    pair(IC<9>{}, 10, HG_SUB(m.y, m.z), HG_SUB(vx, vy), HG_SUB(fx, fy));
+    pair(IC<11>{}, 12, HG_ADD(m.y, m.w), HG_ADD(vx, vz), HG_ADD(fx, fz));
+    pair(IC<13>{}, 14, HG_SUB(m.y, m.w), HG_SUB(vx, vz), HG_SUB(fx, fz));
+    pair(IC<15>{}, 16, HG_ADD(m.z, m.w), HG_ADD(vy, vz), HG_ADD(fy, fz));
+    pair(IC<17>{}, 18, HG_SUB(m.z, m.w), HG_SUB(vy, vz), HG_SUB(fy, fz));
     mf = make_float4(m.x, vx, vy, vz);
 }
 

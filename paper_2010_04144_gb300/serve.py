@@ -10,7 +10,7 @@ run are admitted, first come first served, as soon as their estimated HBM
 footprint fits the budget (policy "fifo"); policy "backfill" also lets a
 later request start early when it cannot delay the blocked head (EASY
 backfilling on memory, counted in ticks).  Their host-side build (site order, neighbour
-table, upload) runs on a worker thread while the GPU keeps executing ticks;
+table, upload) runs on worker threads while the GPU keeps executing ticks;
 a built request joins the active set at the next tick boundary, so builds
 never stall the GPU.  Finished requests are read back and retired, freeing
 their memory for the queue.
@@ -136,9 +136,9 @@ class Server:
         self.build_s = 0.0        # host time spent building domains (worker or inline)
         self.wait_s = 0.0         # main-thread time blocked on the GPU
         self.idle_s = 0.0         # main-thread time with nothing to step
-        # one worker: builds complete in admission order, and the hg_domain_create
-        # calls never overlap one another (each already uses every host core)
-        self._pool = ThreadPoolExecutor(max_workers=1) if build_workers else None
+        # build_workers threads: hg_domain_create calls may overlap one another (their
+        # serial phases then share the host cores); activation stays in admission order
+        self._pool = ThreadPoolExecutor(max_workers=int(build_workers)) if build_workers else None
 
     # ---- admission -------------------------------------------------------------
     def submit(self, job: Job):
@@ -243,14 +243,16 @@ class Server:
             self.building.append((job, _Done(self._build(job))))
 
     def _activate(self, block=False, timeout=None):
-        """Move completed builds (in admission order) into the active set; the GPU is idle."""
-        if block and self.building and not self.building[0][1].done():
+        """Move completed builds into the active set (with several build workers a later
+        admission may be ready first and joins at once); with block, wait for one first."""
+        if block and self.building and not any(f.done() for _, f in self.building):
             t = time.perf_counter()
-            wait([self.building[0][1]], timeout=timeout, return_when=FIRST_COMPLETED)
+            wait([f for _, f in self.building], timeout=timeout, return_when=FIRST_COMPLETED)
             self.idle_s += time.perf_counter() - t
         joined = []
-        while self.building and self.building[0][1].done():
-            job, fut = self.building.pop(0)
+        while any(f.done() for _, f in self.building):
+            i = next(k for k, (_, f) in enumerate(self.building) if f.done())
+            job, fut = self.building.pop(i)
             doms, err, secs = fut.result()
             self.build_s += secs
             if err is None and job.pairs and not job.cancelled:
