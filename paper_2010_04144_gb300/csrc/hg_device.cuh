@@ -596,24 +596,29 @@ template <> struct Pair<kF32> {
         *(float2 *)p = make_float2(a, b);
     }
 };
-template <int S16> struct Pair16 {
-    using T = typename St<S16>::T;
-    template <int I> static __device__ __forceinline__ void ld(const T *p, float &a, float &b) {
-        const uint32_t w = *(const uint32_t *)p;
-        if constexpr (S16 == kF16) {
-            a = St<kF16>::template ld<I>(__ushort_as_half((unsigned short)(w & 0xffffu)));
-            b = St<kF16>::template ld<I>(__ushort_as_half((unsigned short)(w >> 16)));
-        } else {
-            a = St<kBF16>::template ld<I>(__ushort_as_bfloat16((unsigned short)(w & 0xffffu)));
-            b = St<kBF16>::template ld<I>(__ushort_as_bfloat16((unsigned short)(w >> 16)));
-        }
+// Two adjacent 16-bit values move as one 4-byte word and convert with the paired
+// intrinsics (same round-to-nearest-even as the scalar conversions, so the bits
+// are those of every other variant; fewer instructions for kernels near their
+// issue limit).
+template <int S16> struct Pair16;
+template <> struct Pair16<kF16> {
+    template <int I> static __device__ __forceinline__ void ld(const __half *p, float &a, float &b) {
+        const float2 f = __half22float2(*reinterpret_cast<const __half2 *>(p));
+        a = f.x;
+        b = f.y;
     }
-    template <int I> static __device__ __forceinline__ void st(T *p, float a, float b) {
-        const T ha = St<S16>::template st<I>(a), hb = St<S16>::template st<I>(b);
-        uint32_t w;
-        if constexpr (S16 == kF16) w = (uint32_t)__half_as_ushort(ha) | ((uint32_t)__half_as_ushort(hb) << 16);
-        else w = (uint32_t)__bfloat16_as_ushort(ha) | ((uint32_t)__bfloat16_as_ushort(hb) << 16);
-        *(uint32_t *)p = w;
+    template <int I> static __device__ __forceinline__ void st(__half *p, float a, float b) {
+        *reinterpret_cast<__half2 *>(p) = __floats2half2_rn(a, b);
+    }
+};
+template <> struct Pair16<kBF16> {
+    template <int I> static __device__ __forceinline__ void ld(const __nv_bfloat16 *p, float &a, float &b) {
+        const float2 f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(p));
+        a = f.x;
+        b = f.y;
+    }
+    template <int I> static __device__ __forceinline__ void st(__nv_bfloat16 *p, float a, float b) {
+        *reinterpret_cast<__nv_bfloat162 *>(p) = __floats2bfloat162_rn(a, b);
     }
 };
 template <> struct Pair<kF16> : Pair16<kF16> {};

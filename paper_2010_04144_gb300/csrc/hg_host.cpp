@@ -339,11 +339,12 @@ struct DevBuf {
 }  // namespace
 
 // ================================================================ objects
-// Plans over at most this many domains, each at least this large, launch
-// stream-collide once per domain (the single-domain kernel reads its descriptor
-// from the parameter bank at fixed offsets; the tile-table kernel copies it into
-// shared memory behind a barrier, measured 15-20 % slower per launch).
-constexpr int kSeparateMaxDoms = 8;
+// In a plan over several domains, up to this many domains of at least this many
+// sites get a stream-collide launch of their own (the single-domain kernel reads its
+// descriptor from the parameter bank at fixed offsets; the tile-table kernel copies
+// it into shared memory behind a barrier, measured 15-20 % slower per launch); the
+// smaller domains share one tile-table launch.
+constexpr int kSeparateMaxDoms = 16;
 constexpr int64_t kSeparateMinSites = (int64_t)1 << 20;
 
 struct PlanKey {
@@ -1269,14 +1270,31 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
         for (const auto &kv : ctx->coupled)
             fed[{kv.second.src_dom, kv.second.src_k}].push_back(kv.first);
     }
-    for (int32_t di : doms) {
+    // large domains get a single-domain launch each (chained); the rest share one
+    // tile-table launch
+    std::vector<char> separate(doms.size(), 0);
+    if (doms.size() > 1) {
+        int n_sep = 0;
+        for (size_t j = 0; j < doms.size() && n_sep < kSeparateMaxDoms; ++j)
+            if (ctx->doms[doms[j]]->n >= kSeparateMinSites) {
+                separate[j] = 1;
+                ++n_sep;
+            }
+    }
+    for (size_t j = 0; j < doms.size(); ++j) {
+        const int32_t di = doms[j];
         hg_domain *d = ctx->doms[di];
-        for (int64_t s = 0; s < d->n; s += ts) {
-            TileDev t;
-            t.dom = di;
-            t.count = (int32_t)std::min(ts, d->n - s);
-            t.start = s;
-            tiles.push_back(t);
+        if (separate[j]) {
+            p->sep.push_back(make_domdev(ctx, d));
+            p->sep_n.push_back(d->n);
+        } else if (doms.size() > 1) {
+            for (int64_t s = 0; s < d->n; s += ts) {
+                TileDev t;
+                t.dom = di;
+                t.count = (int32_t)std::min(ts, d->n - s);
+                t.start = s;
+                tiles.push_back(t);
+            }
         }
         for (int k = 0; k < d->nio; ++k) {
             IoDev I;
@@ -1350,14 +1368,8 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     if (doms.size() == 1) {
         p->single = true;
         p->one = make_domdev(ctx, ctx->doms[doms[0]]);
-    } else if (doms.size() <= (size_t)kSeparateMaxDoms) {
-        bool large = true;
-        for (int32_t di : doms) large = large && ctx->doms[di]->n >= kSeparateMinSites;
-        if (large)
-            for (int32_t di : doms) {
-                p->sep.push_back(make_domdev(ctx, ctx->doms[di]));
-                p->sep_n.push_back(ctx->doms[di]->n);
-            }
+        const int64_t n1 = ctx->doms[doms[0]]->n;
+        p->n_tiles = (n1 + ts - 1) / ts;
     }
     p->n_chunks = (int)chunks.size();
     int rc = dev_alloc(ctx, p->tiles, std::max<size_t>(1, tiles.size()) * sizeof(TileDev));
@@ -1450,18 +1462,18 @@ cudaError_t launch_sc(hg_ctx *ctx, Plan *p, int off, int parity, bool overlap) {
     CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
     const int64_t *steps = (const int64_t *)ctx->steps.p;
     const DomDev *table = (const DomDev *)ctx->dom_table.p;
-    if (!p->sep.empty()) {
-        const int64_t ts = (int64_t)ctx->block * ctx->spt;
-        for (size_t j = 0; j < p->sep.size(); ++j) {
-            if (p->sep_n[j] == 0) continue;
-            const OneDomain one{&p->sep[j], p->sep_n[j], steps, j > 0 || overlap};
-            const cudaError_t e = launch_stream_collide(cfg, table, nullptr, (p->sep_n[j] + ts - 1) / ts, off,
-                                                        parity, one, ctx->stream);
-            if (e != cudaSuccess) return e;
-        }
-        return cudaSuccess;
+    const int64_t ts = (int64_t)ctx->block * ctx->spt;
+    bool chained = overlap;
+    for (size_t j = 0; j < p->sep.size(); ++j) {
+        if (p->sep_n[j] == 0) continue;
+        const OneDomain one{&p->sep[j], p->sep_n[j], steps, chained};
+        const cudaError_t e = launch_stream_collide(cfg, table, nullptr, (p->sep_n[j] + ts - 1) / ts, off,
+                                                    parity, one, ctx->stream);
+        if (e != cudaSuccess) return e;
+        chained = true;
     }
-    const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0, steps, overlap};
+    if (p->n_tiles == 0) return cudaSuccess;
+    const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0, steps, chained};
     return launch_stream_collide(cfg, table, (const TileDev *)p->tiles.p, p->n_tiles, off, parity, one, ctx->stream);
 }
 
@@ -1983,11 +1995,13 @@ int split_plan(hg_split *sp, Plan *&out) {
     p->n_tiles = (int64_t)tiles.size();
     p->n_ios = (int)ios.size();
     p->n_chunks = (int)chunks.size();
-    if (sp->parts.size() <= 64)
+    if (sp->parts.size() <= 64) {  // one single-domain launch per partition, no tile table
         for (const SplitPart &P : sp->parts) {
             p->sep.push_back(P.dev);
             p->sep_n.push_back(P.n_own);
         }
+        p->n_tiles = 0;
+    }
     p->n_halo = (int64_t)sp->pack.size();
     p->halo_elem = (int)elem_bytes(ctx->storage);
     for (const auto &b : sp->blocks)
