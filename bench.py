@@ -39,15 +39,24 @@ FALLBACK_HBM_GBS = 6800.0
 # device site orderings the autotuner tries (every one gives bit-identical results)
 ORDERINGS = ("morton", "rows", "bricks")
 
-# algorithmic bytes per site update of the stream-collide kernel
-BYTES_PER_UPDATE = {
-    ("f32", "ab"): 19 * 4 * 2 + 18 * 4,        # 224
-    ("f32", "aa"): 19 * 4 * 2 + 18 * 4 // 2,   # 188 (neighbour table on odd steps only)
-    ("f16", "aa"): 19 * 2 * 2 + 18 * 4 // 2,   # 112
-    ("bf16", "aa"): 19 * 2 * 2 + 18 * 4 // 2,  # 112
-    ("f16", "ab"): 19 * 2 * 2 + 18 * 4,        # 148
-    ("bf16", "ab"): 19 * 2 * 2 + 18 * 4,       # 148
-}
+def bytes_per_update(storage, scheme, variant=0, n=1, n_runs=0):
+    """Algorithmic bytes per site update of the stream-collide kernel: the 19 populations
+    read and written once each, plus the neighbour table on pull steps (every A/B step, the
+    odd AA steps): its 18 rows (72 bytes), or for the run-encoded variants (8..11, on a
+    domain that has runs) the per-site word (4 bytes), the 80-byte offset rows of the runs
+    shared by their sites and the per-1024-site chunk word.  With the table: 224 / 188 bytes
+    (FP32 A/B / AA), 148 / 112 (16-bit)."""
+    eb = 4 if storage == "f32" else 2
+    data = 19 * eb * 2
+    table = 4 + 80 * n_runs / n + 4 / 1024 if (variant >= 8 and n_runs > 0) else 72
+    return data + (table if scheme == "ab" else table / 2)
+
+
+def domain_bytes(ctx, storage, scheme, doms):
+    """Bytes per update averaged over the domains one launch sequence steps."""
+    v = ctx.launch[2]
+    tot = sum(d.n for d in doms)
+    return sum(bytes_per_update(storage, scheme, v, d.n, d.info()["n_runs"]) * d.n for d in doms) / tot
 DTYPE_NAME = {"f32": "f32", "f16": "f16-stored/f32-compute", "bf16": "bf16-stored/f32-compute"}
 
 
@@ -284,7 +293,9 @@ def time_variant(H, geo, storage, scheme, steps, warmup, dist, device, sampler, 
         e2e_s = max_over_ranks(time.perf_counter() - t0, dist, device)
         gs = 16
         launches = steps * (1 + (1 if geo.iolets else 0)) + (steps + gs - 1) // gs
+        n_runs = d.info()["n_runs"]
         return dict(n=n, ms=ms, reps=len(reps), timed_s=total / 1e3, ms_sc=ms_sc, ms_io=ms_io,
+                    n_runs=n_runs, bytes_per_update=bytes_per_update(storage, scheme, best[2], n, n_runs),
                     ordering=ordering, ordering_ms=order_ms, e2e_s=e2e_s, h2d=int(state.size),
                     d2h=int(n * 16), launches=launches, device_bytes=d.info()["device_bytes"],
                     launch={"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]},
@@ -512,7 +523,7 @@ def run_coupled(args, H, device):
         ms = e0.elapsed_time(e1)
         ms_sc, ms_io = ctx.step_profiled(min(args.steps, 200))
         n = da.n + dv.n
-        B = BYTES_PER_UPDATE[("f32", args.coupled_scheme)]
+        B = domain_bytes(ctx, "f32", args.coupled_scheme, [da, dv])
         per = ms_sc / min(args.steps, 200)
         peak, kind = hbm_peak()
         Mv = dv.iolet_stats()
@@ -570,20 +581,30 @@ def run_coupled(args, H, device):
 
 def run_split(args, H, device):
     """Split domain (Section 2.2 decomposition, halo exchange every step) on one device:
-    the whole hot path plus the pack / copy / unpack of the crossing populations, against
-    the same domain unsplit; results are bit-identical, so only the time differs."""
+    the whole hot path plus the exchange of the crossing populations (direct, or staged as
+    pack / copy / unpack), against the same domain unsplit, every partition's sites in the
+    unsplit domain's tuned ordering; results are bit-identical, so only the time differs."""
     import torch
 
-    from paper_2010_04144_gb300.autotune import autotune, autotune_split
+    from paper_2010_04144_gb300.autotune import autotune, autotune_split, tune_ordering
 
     geo, cfg = workload(scale=args.scale)
     rows = []
     launch = None
-    for k in [0] + [int(x) for x in args.parts.split(",")]:
+    tuned = {}
+    ordering = args.split_ordering
+    if ordering == "auto":  # the unsplit domain's best ordering, used by every partition too
+        def make(o):
+            c = H.Context(device=device, storage="f32", scheme="ab")
+            c.domain(geo.xyz, geo.iolets, ordering=o)
+            return c
+        ordering, _, _ = tune_ordering(make, ORDERINGS)
+    runs = [(0, None)] + [(int(x), ex) for x in args.parts.split(",") for ex in args.split_exchange.split(",")]
+    for k, ex in runs:
         ctx = H.Context(device=device, storage="f32", scheme="ab")
         try:
             if k == 0:
-                obj = ctx.domain(geo.xyz, geo.iolets)
+                obj = ctx.domain(geo.xyz, geo.iolets, ordering=ordering)
                 if args.split_launch:
                     b, rest = args.split_launch.split("x")
                     launch = (int(b), *[int(x) for x in rest.split("v")])
@@ -591,12 +612,17 @@ def run_split(args, H, device):
                 else:
                     launch, _ = autotune(ctx)
             else:
-                obj = ctx.split(geo.xyz, geo.iolets, k, boundary_weight=args.boundary_weight)
+                obj = ctx.split(geo.xyz, geo.iolets, k, boundary_weight=args.boundary_weight, ordering=ordering,
+                                exchange=ex)
                 if args.split_launch:
                     ctx.set_launch(*launch)
                     split_shape = launch
+                elif (k, "shape") in tuned:   # the other transport reuses the shape tuned for k
+                    split_shape = tuned[(k, "shape")]
+                    ctx.set_launch(*split_shape)
                 else:
                     split_shape, _ = autotune_split(ctx, obj)
+                    tuned[(k, "shape")] = split_shape
             obj.step(args.warmup) if k else ctx.step(args.warmup)
             torch.cuda.synchronize()
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -607,7 +633,7 @@ def run_split(args, H, device):
             ms = e0.elapsed_time(e1) / args.steps
             halo = sum(obj.info(p)["halo_in"] for p in range(k)) if k else 0
             ghosts = sum(obj.info(p)["ghosts"] for p in range(k)) if k else 0
-            rows.append({"parts": k, "ms_per_step": ms, "mflups": geo.n / (ms / 1e3) / 1e6,
+            rows.append({"parts": k, "exchange": ex, "ms_per_step": ms, "mflups": geo.n / (ms / 1e3) / 1e6,
                          "halo_values_per_step": halo, "ghost_sites": ghosts,
                          "launch": list(launch if k == 0 else split_shape)})
         finally:
@@ -615,12 +641,15 @@ def run_split(args, H, device):
     base = rows[0]["ms_per_step"]
     for r in rows:
         r["time_vs_unsplit"] = r["ms_per_step"] / base
-    line = {"metric": METRIC, "value": rows[-1]["mflups"], "unit": "MFLUPS", "n_gpus": 1,
+    last = [r for r in rows if r["parts"] == rows[-1]["parts"]]
+    line = {"metric": METRIC, "value": max(r["mflups"] for r in last), "unit": "MFLUPS", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "dtype": "f32",
             "data": "synthetic (seeded tree geometry, rest initial state)",
             "config": {**cfg, "steps_per_job": args.steps, "storage": "f32", "scheme": "ab",
-                       "launch": list(launch), "split": "contiguous Morton ranges, halo pack/copy/unpack "
-                                                        "per step on one device",
+                       "launch": list(launch), "ordering": ordering,
+                       "split": "contiguous Morton ranges, each partition's sites in the device ordering; "
+                                "halo exchange every step on one device (direct: one kernel; staged: "
+                                "pack, one copy per partition pair, unpack)",
                        "boundary_weight": args.boundary_weight},
             "split": rows}
     print(json.dumps(line))
@@ -654,8 +683,9 @@ def time_large(args, H, device, geo, results):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / k
             ms_sc, _ = ctx.step_profiled(16)
-            B = BYTES_PER_UPDATE[key]
+            B = domain_bytes(ctx, storage, scheme, [d])
             out[f"{storage}:{scheme}"] = {"mflups": d.n / (ms / 1e3) / 1e6, "ms_per_step": ms,
+                                          "bytes_per_update": B,
                                           "roofline_frac": B * d.n / (ms_sc / 16 / 1e3) / 1e9 / peak,
                                           "ordering": r["ordering"], "launch": L,
                                           "device_gb": d.info()["device_bytes"] / 1e9}
@@ -690,7 +720,7 @@ def run_precision(args, H, device):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1)
             ms_sc, _ = ctx.step_profiled(min(args.steps, 100))
-            B = BYTES_PER_UPDATE[(storage, scheme)]
+            B = domain_bytes(ctx, storage, scheme, [d])
             per = ms_sc / min(args.steps, 100)
             out[f"{storage}:{scheme}"] = {"mflups": d.n * args.steps / (ms / 1e3) / 1e6,
                                           "roofline_frac": B * d.n / (per / 1e3) / 1e9 / peak,
@@ -742,6 +772,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--config", default="tree", choices=["tree", "coupled", "precision", "serve", "split"])
     ap.add_argument("--parts", default="2,4,8", help="split config: partition counts to time")
+    ap.add_argument("--split-ordering", default="auto",
+                    help="split config: auto (the unsplit domain's tuned ordering) or morton / rows / bricks")
+    ap.add_argument("--split-exchange", default="direct,staged",
+                    help="split config: halo transports to time (direct, staged)")
     ap.add_argument("--split-launch", default="", help="split config: fixed launch BLOCKxSPTvVARIANT (no tuning)")
     ap.add_argument("--boundary-weight", type=float, default=1.0,
                     help="split config: load-balancing cost of a site next to an iolet")
@@ -836,10 +870,9 @@ def main():
             r = time_variant(H, geo, storage, scheme, args.steps, args.warmup, dist, device, sampler,
                              launch=launch, orderings=orders if launch is None else (orders[0],),
                              min_timed_s=args.min_timed_s)
-            B = BYTES_PER_UPDATE[(storage, scheme)]
+            B = r["bytes_per_update"]
             r["mflups"] = r["n"] * ws * args.steps / (r["ms"] / 1e3) / 1e6
             r["achieved_gbs"] = B * r["n"] / (r["ms_sc"] / args.steps / 1e3) / 1e9
-            r["bytes_per_update"] = B
             results[(storage, scheme)] = r
     finally:
         sampler.stop()
@@ -880,7 +913,7 @@ def main():
         "clocks": sampler.summary(),
         "variants": {f"{s}:{c}": {"mflups": r["mflups"], "achieved_gbs": r["achieved_gbs"],
                                    "roofline_frac": r["achieved_gbs"] / peak,
-                                   "bytes_per_update": r["bytes_per_update"],
+                                   "bytes_per_update": r["bytes_per_update"], "n_runs": r["n_runs"],
                                    "stream_collide_ms": r["ms_sc"] / args.steps,
                                    "iolet_update_ms": r["ms_io"] / args.steps,
                                    "launch": r["launch"], "ordering": r["ordering"],

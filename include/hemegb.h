@@ -120,7 +120,11 @@ typedef struct {
                                  6 = AA on pairs of adjacent sites: shared table loads for
                                      the gathers and the scatter, packed rest values, the
                                      even step on vector pairs (sites_per_thread 2);
-                                 7 = 6 with L2 256-byte prefetch hints on the loads */
+                                 7 = 6 with L2 256-byte prefetch hints on the loads;
+                                 8, 9, 10, 11 = 3, 5, 6, 7 reading the run-encoded
+                                     neighbour table (hg_domain_runs) instead of the
+                                     18 table rows; a launch over a domain without
+                                     one runs 3, 5, 6, 7; same shapes as 3, 5, 6, 7 */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */
@@ -180,7 +184,8 @@ const char *hg_last_error(hg_ctx *ctx);
 
 /* Wait for all work enqueued on the context's stream.  Returns HG_ERR_TIMEOUT
  * (and clears the flag) when a bounded device wait gave up since the last
- * call: the state is then not trusted.
+ * call, HG_ERR_STATE when a run-encoded kernel variant met a domain without a
+ * run encoding (the host never launches one so): the state is then not trusted.
  * Passage: infrastructure: no passage. */
 int hg_sync(hg_ctx *ctx);
 
@@ -208,6 +213,30 @@ int hg_domain_destroy(hg_domain *d);
  * Passage: infrastructure: no passage. */
 int hg_domain_info(hg_domain *d, int64_t *n_sites, int32_t *n_iolets, int64_t *n_adjacent,
                    int64_t *step, int64_t *device_bytes);
+
+/* Runs of the run-encoded neighbour table (0: none built).  Every domain keeps
+ * its 18-row table (72 bytes per site, what the gathers of a pull step read
+ * besides the populations); where it compresses (runs of at least 4.5 sites on
+ * average) the build also encodes it as runs: maximal ranges of consecutive
+ * device sites whose fluid links share one offset per direction, plus a 4-byte
+ * word per site flagging its non-fluid links.  In rows ordering a run covers
+ * most of an x-row of a vessel, so the encoding costs about 4 + 72 / run-length
+ * bytes per site.  Kernel variants 8..11 read it; the results are the same bits.
+ * Passage: Section 2.2 (indirect addressing of the sparse fluid-site list). */
+int hg_domain_runs(hg_domain *d, int64_t *n_runs);
+
+/* Host only: the run encoding hg_domain_create builds, for a device neighbour
+ * table nbr[18][row_stride] of sites [0, n) whose fluid entries lie in
+ * [0, n_ref) and whose other entries are the scheme's virtual indices
+ * (q + (opp(i) - i) row_stride for A/B, q + (i - opp(i)) row_stride for AA).
+ * Outputs: lword_out[row_stride] (bits 0..17: link i+1 non-fluid; bits 18..27:
+ * run minus run0_out[q >> 10]), run0_out[(row_stride + 1023) / 1024],
+ * rdelta_out[n_runs * 18] (at most n * 16 / 72 + 1 runs); any output may be
+ * NULL.  *n_runs_out = 0 when the table does not compress (average run below
+ * 4.5 sites) or an entry is not of that form.  Errors: HG_ERR_ARG.
+ * Passage: Section 2.2 (indirect addressing of the sparse fluid-site list). */
+int hg_encode_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t row_stride, int32_t scheme,
+                   uint32_t *lword_out, int32_t *run0_out, int32_t *rdelta_out, int64_t *n_runs_out);
 
 /* Canonical site coordinates, n_sites x 3 int32 (host), whatever the
  * device ordering.
@@ -403,15 +432,18 @@ int hg_ctx_inject_fault(hg_ctx *ctx, int32_t kind, int64_t arg);
  * contiguous ranges of equal cost (a site costs 1, a site with a link into an
  * iolet opening costs boundary_weight); each partition holds its own
  * distributions and neighbour table plus ghost copies of the sites it pulls
- * from, and after every stream-collide the crossing values are packed per
- * (sender, receiver) pair, copied into the receiver's buffer and unpacked into
- * its ghosts.  Iolet means are reduced over the whole domain in canonical
+ * from, and after every stream-collide the crossing values move into the
+ * receivers' ghosts: directly, by one kernel, or staged as messages (packed per
+ * (sender, receiver) pair, copied into the receiver's buffer, unpacked).  Iolet means are reduced over the whole domain in canonical
  * order, so a split run is bit-identical to the same domain unsplit.  All
  * partitions of a split live on the context's device; the A/B scheme only; a
  * split takes no part in coupling, and hg_step does not advance it. */
+#define HG_EXCHANGE_DIRECT 0 /* one kernel moves every halo value from sender to receiver */
+#define HG_EXCHANGE_STAGED 1 /* pack per (sender, receiver) block, one copy per block, unpack:
+                                the message form of a transport between devices */
 typedef struct {
     int32_t n_parts;        /* 1 <= n_parts <= min(n_fluid, 1024) */
-    int32_t reserved;
+    int32_t exchange;       /* HG_EXCHANGE_DIRECT or HG_EXCHANGE_STAGED (same bits either way) */
     double boundary_weight; /* cost of a site next to an iolet relative to a bulk site (<= 0: 1) */
 } hg_split_params;
 
@@ -426,7 +458,9 @@ int hg_split_layout(const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets,
                     const hg_split_params *sp, int64_t *first_out, int64_t *ghosts_out, int64_t *halo_out);
 
 /* Build a split domain (same inputs and checks as hg_domain_create; the context
- * must use the A/B scheme; lb->ordering must be HG_ORDER_MORTON).  Errors:
+ * must use the A/B scheme).  The cut is always taken on the canonical order;
+ * lb->ordering (as for hg_domain_create) sets the device order of each
+ * partition's owned sites, its ghosts following them.  Errors:
  * HG_ERR_ARG, HG_ERR_STATE (context full), HG_ERR_OOM, HG_ERR_CUDA.
  * Passage: Section 2.2 and Section 2.2.1. */
 int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n_fluid, const hg_iolet *iolets, int32_t n_iolets,

@@ -26,11 +26,13 @@ DEFAULT_CANDIDATES = (
     (256, 1, 3), (128, 1, 3), (256, 2, 3), (128, 2, 3), (512, 2, 3), (128, 4, 3), (256, 4, 3),
     (128, 2, 5), (256, 2, 5), (512, 2, 5),  # variant 5: A/B with 16-bit storage only
     (128, 2, 6), (256, 2, 6), (256, 2, 7), (512, 2, 7),  # variants 6, 7: AA on site pairs
+    # 8..11: 3, 5, 6, 7 reading the run-encoded neighbour table
+    (256, 1, 8), (128, 2, 8), (256, 2, 8), (128, 2, 9), (256, 2, 9), (128, 2, 10), (256, 2, 10), (256, 2, 11),
 )
 # Variant 4 (staged AA odd-step stores) is measured slower than variant 1 on
 # every workload tried; it stays available through Context.set_launch.
-AA_ONLY = (2, 4, 6, 7)
-AB_16BIT_ONLY = (5,)
+AA_ONLY = (2, 4, 6, 7, 10, 11)
+AB_16BIT_ONLY = (5, 9)
 
 
 def _cache_path():
@@ -126,9 +128,8 @@ def tune_ordering(make_ctx, orderings=("morton", "rows", "bricks"), candidates=D
 
 
 def autotune_split(ctx, split, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2):
-    """Launch shape of a split domain's stream-collide (the multi-domain entry kernel
-    its partitions run in): every candidate timed with CUDA events around `steps`
-    whole steps.  A split keeps no checkpoint, so tuning advances it; every shape
+    """Launch shape of a split domain's stream-collide (one single-domain launch per
+    partition): every candidate timed with CUDA events around `steps` whole steps.  A split keeps no checkpoint, so tuning advances it; every shape
     computes the same bits.  Returns (best, {candidate: ms per step})."""
     import torch
 

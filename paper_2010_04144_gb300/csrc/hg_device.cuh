@@ -11,6 +11,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "hg_internal.h"
 
 namespace hg {
@@ -199,6 +201,14 @@ template <int S> __device__ __forceinline__ float4 collide_s(float g[19], float 
 }
 
 
+// A pointer the compiler cannot see through: loads from it are not merged with
+// earlier loads from the same address.
+template <typename T> __device__ __forceinline__ const T *opaque_ptr(const T *p) {
+    const T *q;
+    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
+    return q;
+}
+
 template <typename T> __device__ __forceinline__ T ldg_nc(const T *p) { return __ldg(p); }
 template <> __device__ __forceinline__ __half ldg_nc(const __half *p) {
     return __ushort_as_half(__ldg(reinterpret_cast<const unsigned short *>(p)));
@@ -258,6 +268,106 @@ template <bool HINT, typename T> __device__ __forceinline__ T load_rw(const T *p
     else return *p;
 }
 
+// ---- neighbour entries of a site: the 18-row table or its run encoding ----
+// Both give the same int32 entry for link I (1..18): the fluid neighbour's device
+// index, or for a non-fluid link the virtual index s + dd np with dd = opp(I) - I
+// (A/B) or I - opp(I) (AA).  TabNb reads row I-1 of the table (72 bytes per site
+// in all); RunNb reads one word per site (non-fluid flags, run within the chunk),
+// the chunk's first run and the run's offsets, which the run's other sites also
+// read (L1 hits): about 4 + 72 / run-length bytes per site.  reload() gives an
+// accessor whose next reads are not merged with earlier ones, so a scatter after
+// the collision re-reads (cache hits) instead of keeping 18 entries in registers.
+template <bool HINT> struct TabNb {
+    const int32_t *p;
+    int64_t np;
+    __device__ __forceinline__ TabNb(const DomDev &D, int64_t s) : p(D.nbr + s), np(D.np) {}
+    __device__ __forceinline__ TabNb(const int32_t *p_, int64_t np_) : p(p_), np(np_) {}
+    template <int I> __device__ __forceinline__ int32_t at() const {
+        return load_nbr<HINT>(p + (int64_t)(I - 1) * np);
+    }
+    __device__ __forceinline__ void all(int32_t nb[18]) const {
+        unroll<1, 19>([&](auto ic) { nb[decltype(ic)::v - 1] = at<decltype(ic)::v>(); });
+    }
+    __device__ __forceinline__ TabNb reload() const { return TabNb(opaque_ptr(p), np); }
+};
+template <int SCHEME, bool HINT> struct RunNb {
+    uint32_t w;
+    const int32_t *rd;
+    int32_t s, np;
+    __device__ __forceinline__ RunNb(const DomDev &D, int64_t s_) : s((int32_t)s_), np((int32_t)D.np) {
+        w = (uint32_t)load_nbr<HINT>(reinterpret_cast<const int32_t *>(D.lword) + s_);
+        rd = D.rdelta + (int64_t)(__ldg(D.run0 + (s_ >> 10)) + (int32_t)(w >> 18)) * kRunStride;
+    }
+    __device__ __forceinline__ RunNb(uint32_t w_, const int32_t *rd_, int32_t s_, int32_t np_)
+        : w(w_), rd(rd_), s(s_), np(np_) {}
+    template <int I> __device__ __forceinline__ int32_t at() const {
+        constexpr int dd = SCHEME == kAA ? I - OPP(I) : OPP(I) - I;
+        return ((w >> (I - 1)) & 1u) ? s + dd * np : s + __ldg(rd + (I - 1));
+    }
+    // all 18 entries: the run's row as five 16-byte loads
+    __device__ __forceinline__ void all(int32_t nb[18]) const {
+        int32_t d[kRunStride];
+#pragma unroll
+        for (int k = 0; k < kRunStride / 4; ++k) {
+            const int4 v = __ldg(reinterpret_cast<const int4 *>(rd) + k);
+            d[4 * k] = v.x;
+            d[4 * k + 1] = v.y;
+            d[4 * k + 2] = v.z;
+            d[4 * k + 3] = v.w;
+        }
+        unroll<1, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            constexpr int dd = SCHEME == kAA ? I - OPP(I) : OPP(I) - I;
+            nb[I - 1] = ((w >> (I - 1)) & 1u) ? s + dd * np : s + d[I - 1];
+        });
+    }
+    __device__ __forceinline__ RunNb reload() const { return RunNb(w, opaque_ptr(rd), s, np); }
+};
+// The same for a pair of adjacent sites s, s+1 (s even: both in one 1024-site
+// chunk): one 8-byte load of both table entries, or of both words; a run shared
+// by the two (the usual case) is read once.
+template <bool HINT> struct TabNb2 {
+    const int32_t *p;
+    int64_t np;
+    __device__ __forceinline__ TabNb2(const DomDev &D, int64_t s) : p(D.nbr + s), np(D.np) {}
+    __device__ __forceinline__ TabNb2(const int32_t *p_, int64_t np_) : p(p_), np(np_) {}
+    template <int I> __device__ __forceinline__ int2 at() const {
+        return __ldg(reinterpret_cast<const int2 *>(p + (int64_t)(I - 1) * np));
+    }
+    __device__ __forceinline__ TabNb2 reload() const { return TabNb2(opaque_ptr(p), np); }
+};
+template <int SCHEME> struct RunNb2 {
+    uint32_t wa, wb;
+    const int32_t *ra, *rb;
+    int32_t s, np;
+    __device__ __forceinline__ RunNb2(const DomDev &D, int64_t s_) : s((int32_t)s_), np((int32_t)D.np) {
+        const uint2 w = __ldg(reinterpret_cast<const uint2 *>(D.lword + s_));
+        const int32_t r0 = __ldg(D.run0 + (s_ >> 10));
+        wa = w.x;
+        wb = w.y;
+        ra = D.rdelta + (int64_t)(r0 + (int32_t)(w.x >> 18)) * kRunStride;
+        rb = D.rdelta + (int64_t)(r0 + (int32_t)(w.y >> 18)) * kRunStride;
+    }
+    __device__ __forceinline__ RunNb2(uint32_t wa_, uint32_t wb_, const int32_t *ra_, const int32_t *rb_,
+                                      int32_t s_, int32_t np_)
+        : wa(wa_), wb(wb_), ra(ra_), rb(rb_), s(s_), np(np_) {}
+    template <int I> __device__ __forceinline__ int2 at() const {
+        constexpr int dd = SCHEME == kAA ? I - OPP(I) : OPP(I) - I;
+        const int32_t da = __ldg(ra + (I - 1));
+        const int32_t db = ra == rb ? da : __ldg(rb + (I - 1));
+        return make_int2(((wa >> (I - 1)) & 1u) ? s + dd * np : s + da,
+                         ((wb >> (I - 1)) & 1u) ? s + 1 + dd * np : s + 1 + db);
+    }
+    __device__ __forceinline__ RunNb2 reload() const {
+        const int32_t *q = opaque_ptr(ra);
+        return RunNb2(wa, wb, q, q + (rb - ra), s, np);
+    }
+};
+template <int SCHEME, bool HINT, bool RUNS>
+using NbOf = typename std::conditional<RUNS, RunNb<SCHEME, HINT>, TabNb<HINT>>::type;
+template <int SCHEME, bool RUNS>
+using Nb2Of = typename std::conditional<RUNS, RunNb2<SCHEME>, TabNb2<false>>::type;
+
 // ---- sites next to an iolet (rare path) ----
 // Neighbour table entries of non-fluid links hold a virtual index that makes
 // the ordinary address formula land on the site's own opposite slot, so a wall
@@ -307,14 +417,13 @@ template <typename T> __device__ __forceinline__ T *opaque(T *p) {
 }
 
 // ---- A/B pull: F_{t-1} in src, F_t to dst ----
-template <int S, bool HINT = false>
+template <int S, bool HINT = false, bool RUNS = false>
 __device__ __forceinline__ void site_ab(const DomDev &D, const typename St<S>::T *__restrict__ src,
                                         typename St<S>::T *__restrict__ dst, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
     int32_t nb[18];
-#pragma unroll
-    for (int i = 0; i < 18; ++i) nb[i] = load_nbr<HINT>(D.nbr + (int64_t)i * np + s);
+    NbOf<kAB, HINT, RUNS>(D, s).all(nb);
     float g[19];
     g[0] = Tr::template ld<0>(load_ro<HINT>(src + s));
     unroll<1, 19>([&](auto ic) {  // virtual indices: walls read their own opposite value
@@ -356,13 +465,13 @@ __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T 
 // ---- AA odd step: gather F_{t-1} (swapped) from x - c_i, scatter F_t to x + c_i ----
 // Entry OPP(I) of the site's row is the site at x + c_I; its virtual index for
 // a non-fluid link turns the scatter into the raw write to the own slot OPP(I).
-template <int S, bool HINT = false>
+template <int S, bool HINT = false, bool RUNS = false>
 __device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
+    const NbOf<kAA, HINT, RUNS> tab(D, s);
     int32_t nb[18];
-#pragma unroll
-    for (int i = 0; i < 18; ++i) nb[i] = load_nbr<HINT>(D.nbr + (int64_t)i * np + s);
+    tab.all(nb);
     float g[19];
     g[0] = Tr::template ld<0>(load_rw<HINT>(buf + s));
     unroll<1, 19>([&](auto ic) {
@@ -372,11 +481,11 @@ __device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *
     const int slot = iolet_fixup<S>(D, s, g);
     const float4 m = collide_s<S>(g, D.omega);
     typename St<S>::T *wb = opaque(buf);
-    const int32_t *nb2 = opaque(D.nbr);  // reread (L1 hits) instead of keeping 18 entries live
+    tab.reload().all(nb);  // reread (cache hits) instead of keeping 18 entries live
     wb[s] = Tr::template st<0>(g[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        wb[(int64_t)I * np + __ldg(nb2 + (int64_t)(OPP(I) - 1) * np + s)] = Tr::template st<I>(g[I]);
+        wb[(int64_t)I * np + nb[OPP(I) - 1]] = Tr::template st<I>(g[I]);
     });
     if (slot >= 0) D.bnd[slot] = m;
 }
@@ -628,16 +737,17 @@ template <> struct Pair<kBF16> : Pair16<kBF16> {};
 // Sites s and s+1 (s even) share one 8-byte load per neighbour-table row, one
 // 4-byte load of the rest values and one 4-byte store per direction: fewer
 // memory instructions per site for a kernel that runs near its issue limit.
-template <int S>
+template <int S, bool RUNS = false>
 __device__ __forceinline__ void site_ab_pair(const DomDev &D, const typename St<S>::T *__restrict__ src,
                                              typename St<S>::T *__restrict__ dst, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
+    const Nb2Of<kAB, RUNS> tab(D, s);
     float ga[19], gb[19];
     Pair<S>::template ld<0>(src + s, ga[0], gb[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int2 nb = __ldg(reinterpret_cast<const int2 *>(D.nbr + (int64_t)(I - 1) * np + s));
+        const int2 nb = tab.template at<I>();
         ga[I] = Tr::template ld<I>(ldg_nc(src + ((int64_t)I * np + nb.x)));
         gb[I] = Tr::template ld<I>(ldg_nc(src + ((int64_t)I * np + nb.y)));
     });
@@ -659,15 +769,16 @@ __device__ __forceinline__ void site_ab_pair(const DomDev &D, const typename St<
 // the gathers and for the re-read that addresses the scatter, and one load and one
 // store of their two rest values; the 18 gathers and 18 scattered stores stay per
 // site.  The odd step reads slot OPP(I) at x - c_I and writes slot I at x + c_I.
-template <int S, bool HINT>
+template <int S, bool HINT, bool RUNS = false>
 __device__ __forceinline__ void site_aa_odd_pair(const DomDev &D, typename St<S>::T *buf, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
+    const Nb2Of<kAA, RUNS> tab(D, s);
     float ga[19], gb[19];
     Pair<S>::template ld<0>(buf + s, ga[0], gb[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int2 nb = __ldg(reinterpret_cast<const int2 *>(D.nbr + (int64_t)(I - 1) * np + s));
+        const int2 nb = tab.template at<I>();
         ga[I] = Tr::template ld<I>(load_rw<HINT>(buf + ((int64_t)OPP(I) * np + nb.x)));
         gb[I] = Tr::template ld<I>(load_rw<HINT>(buf + ((int64_t)OPP(I) * np + nb.y)));
     });
@@ -676,11 +787,11 @@ __device__ __forceinline__ void site_aa_odd_pair(const DomDev &D, typename St<S>
     const float4 ma = collide_s<S>(ga, D.omega);
     const float4 mb = collide_s<S>(gb, D.omega);
     typename St<S>::T *wb = opaque(buf);
-    const int32_t *nb2 = opaque(D.nbr);  // reread (L1 hits) instead of keeping 36 entries live
+    const auto tab2 = tab.reload();  // reread (L1 hits) instead of keeping 36 entries live
     Pair<S>::template st<0>(wb + s, ga[0], gb[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int2 tg = __ldg(reinterpret_cast<const int2 *>(nb2 + (int64_t)(OPP(I) - 1) * np + s));
+        const int2 tg = tab2.template at<OPP(I)>();
         wb[(int64_t)I * np + tg.x] = Tr::template st<I>(ga[I]);
         wb[(int64_t)I * np + tg.y] = Tr::template st<I>(gb[I]);
     });
@@ -837,9 +948,9 @@ __device__ __forceinline__ void tile_aa_even_tma(const DomDev &D, const TileDev 
 // AA step kind), 2 = read from the domain's step counter per block (A/B, and AA
 // batches whose domains are at different parities).
 // One tile of one domain, after the prologue has located it.
-template <int S, int SCHEME, int SPT, int PAR, int V>
-__device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileDev &tl, bool odd,
-                                                    uint32_t *stage) {
+template <int S, int SCHEME, int SPT, int PAR, int V, bool RUNS>
+__device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const TileDev &tl, bool odd,
+                                                         uint32_t *stage) {
     using T = typename St<S>::T;
     if constexpr (V == 1 || V == 2 || V == 4) {
         if constexpr (SCHEME == kAB) {
@@ -858,14 +969,25 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
         // AA on adjacent pairs: each thread takes sites 2t and 2t+1 of the tile (SPT = 2)
         static_assert(SCHEME == kAA && SPT == 2, "variants 6 and 7 are the AA pair forms");
         constexpr bool HINT = V == 7;
+        T *buf = (T *)D.f[0];
+        if (RUNS && odd) {
+            // the run-encoded odd step takes one site at a time (decoding two runs at
+            // once keeps too many values live), sites t and t + blockDim, so a warp's
+            // gathers and scatters cover consecutive sites
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const int r = j * blockDim.x + threadIdx.x;
+                if (r < tl.count) site_aa_odd<S, HINT, true>(D, buf, tl.start + r);
+            }
+            return;
+        }
         const int r = 2 * threadIdx.x;
         const int64_t s = tl.start + r;  // even: tiles start at multiples of 2 * blockDim
-        T *buf = (T *)D.f[0];
         if (r + 1 < tl.count) {
-            if (odd) site_aa_odd_pair<S, HINT>(D, buf, s);
+            if (odd) site_aa_odd_pair<S, HINT, false>(D, buf, s);
             else site_aa_even_pair<S, HINT>(D, buf, s);
         } else if (r < tl.count) {  // ragged tail: one site
-            if (odd) site_aa_odd<S, HINT>(D, buf, s);
+            if (odd) site_aa_odd<S, HINT, false>(D, buf, s);
             else site_aa_even<S, HINT>(D, buf, s);
         }
     } else if constexpr (V == 5) {
@@ -875,8 +997,8 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
         const int64_t s = tl.start + r;  // even: tiles start at multiples of 2 * blockDim
         const T *src = (const T *)D.f[odd ? 0 : 1];
         T *dst = (T *)D.f[odd ? 1 : 0];
-        if (r + 1 < tl.count) site_ab_pair<S>(D, src, dst, s);
-        else if (r < tl.count) site_ab<S, false>(D, src, dst, s);  // ragged tail: one site
+        if (r + 1 < tl.count) site_ab_pair<S, RUNS>(D, src, dst, s);
+        else if (r < tl.count) site_ab<S, false, RUNS>(D, src, dst, s);  // ragged tail: one site
     } else {
         constexpr bool HINT = V == 3;
 #pragma unroll
@@ -888,16 +1010,35 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
                 if (live) {
                     const T *src = (const T *)D.f[odd ? 0 : 1];
                     T *dst = (T *)D.f[odd ? 1 : 0];
-                    site_ab<S, HINT>(D, src, dst, s);
+                    site_ab<S, HINT, RUNS>(D, src, dst, s);
                 }
             } else {
                 T *buf = (T *)D.f[0];
                 if (live) {
-                    if (odd) site_aa_odd<S, HINT>(D, buf, s);
+                    if (odd) site_aa_odd<S, HINT, RUNS>(D, buf, s);
                     else site_aa_even<S, HINT>(D, buf, s);
                 }
             }
         }
+    }
+}
+
+// Variants 8..11 are 3, 5, 6, 7 reading the run-encoded neighbour table.  The host
+// launches them only on domains that have one (the others get 3, 5, 6, 7); a domain
+// without one here is reported through the error word (code 2) and left untouched.
+template <int V> constexpr int table_variant() { return V == 8 ? 3 : V == 9 ? 5 : V == 10 ? 6 : V == 11 ? 7 : V; }
+
+template <int S, int SCHEME, int SPT, int PAR, int V>
+__device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileDev &tl, bool odd,
+                                                    uint32_t *stage) {
+    if constexpr (V >= 8) {
+        if (D.lword == nullptr) {
+            if (threadIdx.x == 0) atomicExch(D.err, 2);
+            return;
+        }
+        stream_collide_tile_impl<S, SCHEME, SPT, PAR, table_variant<V>(), true>(D, tl, odd, stage);
+    } else {
+        stream_collide_tile_impl<S, SCHEME, SPT, PAR, V, false>(D, tl, odd, stage);
     }
 }
 
@@ -1015,6 +1156,25 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
         else if (cfg.spt != 2) return cudaErrorInvalidValue;
         else if (cfg.variant == 6) return launch_sc_one<S, SCHEME, PAR, 6, 2>(cfg, doms, tiles, n_tiles, off, one, st);
         else return launch_sc_one<S, SCHEME, PAR, 7, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+    }
+    if (cfg.variant == 8) {
+        switch (cfg.spt) {
+            case 1: return launch_sc_one<S, SCHEME, PAR, 8, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 8, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 4: return launch_sc_one<S, SCHEME, PAR, 8, 4>(cfg, doms, tiles, n_tiles, off, one, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (cfg.variant == 9) {
+        if constexpr (SCHEME != kAB || S == kF32) return cudaErrorInvalidValue;
+        else if (cfg.spt != 2) return cudaErrorInvalidValue;
+        else return launch_sc_one<S, SCHEME, PAR, 9, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+    }
+    if (cfg.variant == 10 || cfg.variant == 11) {
+        if constexpr (SCHEME != kAA) return cudaErrorInvalidValue;
+        else if (cfg.spt != 2) return cudaErrorInvalidValue;
+        else if (cfg.variant == 10) return launch_sc_one<S, SCHEME, PAR, 10, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+        else return launch_sc_one<S, SCHEME, PAR, 11, 2>(cfg, doms, tiles, n_tiles, off, one, st);
     }
     if (cfg.variant == 2) {
         if (SCHEME == kAB) return cudaErrorInvalidValue;

@@ -356,13 +356,16 @@ struct Plan {
     std::vector<int32_t> doms;
     DevBuf tiles, ios, adv, chunks, partials, counters, rev, fslots;
     // halo exchange of a split domain (after stream-collide, before the iolet update):
-    // pack into `send`, copy each (sender, receiver) block to `recv`, unpack
-    DevBuf halo_pack, halo_unpack, send, recv;
+    // direct (one kernel moves every value from sender to receiver) or staged (pack
+    // into `send`, copy each (sender, receiver) block to `recv`, unpack)
+    DevBuf halo_pack, halo_unpack, send, recv, halo_moves;
     int64_t n_halo = 0;
     int halo_elem = 4;
+    bool halo_staged = false;
     std::vector<std::pair<size_t, size_t>> halo_blocks;  // (byte offset, bytes) per partition pair
     DomDev one{};       // single-domain plans: the descriptor passed by value to stream-collide
     bool single = false;
+    bool tiles_runs = true;  // every domain of the tile-table (or single) launch has a run encoding
     // a few large domains (a coupled pair, a split's partitions): one single-domain
     // launch each instead of one tile-table launch, chained by programmatic dependent
     // launch; descriptor and sites stepped per launch
@@ -414,6 +417,8 @@ struct SplitPart {
     int64_t first = 0, n_own = 0, n_loc = 0, np = 0;
     std::vector<int64_t> ghosts;       // global canonical indices of the ghost sites
     DevBuf f[2], nbr, iomask, ioprefix, gidx;  // gidx: local -> global canonical index
+    DevBuf lword, run0, rdelta;                // run-length encoded table (empty: not built)
+    int64_t n_runs = 0;
     DomDev dev{};
 };
 
@@ -425,6 +430,7 @@ struct hg_split {
     std::vector<hg_iolet> io;
     std::vector<int32_t> io_ptr;
     std::vector<SplitPart> parts;
+    bool staged = false;                            // halo transport (hg_split_params.exchange)
     std::vector<HaloDev> pack, unpack;              // grouped by (sender, receiver) pair
     std::vector<std::pair<size_t, size_t>> blocks;  // element (offset, count) per pair
     DevBuf bnd, io_codes, coef, slot_site, bcv, io_kind, M, slots, force;  // shared by the parts
@@ -451,6 +457,8 @@ struct hg_domain {
     std::vector<int32_t> canon_of_host;  // device -> canonical index (empty: identity)
     std::vector<int32_t> dev_of_host;    // canonical -> device index (empty: identity)
     DevBuf canon_of, dev_of;             // device copies of the two permutations
+    DevBuf lword, run0, rdelta;          // run-length encoded neighbour table (empty: not built)
+    int64_t n_runs = 0;
     int64_t bytes = 0;
 };
 
@@ -458,7 +466,8 @@ namespace {
 
 std::vector<DevBuf *> domain_buffers(hg_domain *d) {
     return {&d->f[0], &d->f[1], &d->nbr, &d->iomask, &d->ioprefix, &d->io_codes, &d->bnd, &d->coef,
-            &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force, &d->slot_site, &d->canon_of, &d->dev_of};
+            &d->bcv, &d->io_kind, &d->M, &d->slots, &d->force, &d->slot_site, &d->canon_of, &d->dev_of,
+            &d->lword, &d->run0, &d->rdelta};
 }
 
 // last failure of the calling thread and the context it concerned
@@ -522,7 +531,7 @@ void drop_plans(hg_ctx *ctx) {
         for (auto &g : p.graph)
             if (g) cudaGraphExecDestroy(g);
         for (DevBuf *b : {&p.tiles, &p.ios, &p.adv, &p.chunks, &p.partials, &p.counters, &p.rev, &p.fslots,
-                          &p.halo_pack, &p.halo_unpack, &p.send, &p.recv})
+                          &p.halo_pack, &p.halo_unpack, &p.send, &p.recv, &p.halo_moves})
             dev_free(ctx, *b);
     }
     ctx->plans.clear();
@@ -534,6 +543,9 @@ DomDev make_domdev(hg_ctx *ctx, hg_domain *d) {
     D.f[0] = d->f[0].p;
     D.f[1] = d->f[1].p;
     D.nbr = (const int32_t *)d->nbr.p;
+    D.lword = (const uint32_t *)d->lword.p;
+    D.run0 = (const int32_t *)d->run0.p;
+    D.rdelta = (const int32_t *)d->rdelta.p;
     D.iomask = (const uint32_t *)d->iomask.p;
     D.ioprefix = (const int32_t *)d->ioprefix.p;
     D.io_codes = (const int32_t *)d->io_codes.p;
@@ -590,6 +602,9 @@ bool variant_ok(int storage, int scheme, int spt, int variant) {
         case 4: return spt == 1 && scheme == HG_SCHEME_AA;
         case 5: return spt == 2 && scheme == HG_SCHEME_AB && storage != HG_STORE_F32;
         case 6: case 7: return spt == 2 && scheme == HG_SCHEME_AA;
+        case 8: return true;  // 8..11: variants 3, 5, 6, 7 reading the run-encoded table
+        case 9: return spt == 2 && scheme == HG_SCHEME_AB && storage != HG_STORE_F32;
+        case 10: case 11: return spt == 2 && scheme == HG_SCHEME_AA;
         default: return false;
     }
 }
@@ -599,6 +614,55 @@ int ensure_scratch(hg_ctx *ctx, size_t bytes) {
     CU(ctx, cudaStreamSynchronize(ctx->stream));
     dev_free(ctx, ctx->scratch);
     return dev_alloc(ctx, ctx->scratch, bytes);
+}
+
+// Run-length encoding of a device neighbour table ([18][np], sites [0, n); fluid
+// entries in [0, n_ref), every other entry the virtual index q + dd_i np with
+// dd_i = vdir * (opp(i) - i)).  A run is a maximal range of consecutive sites in
+// which each direction's fluid links share one offset (entry - site); non-fluid
+// links do not break a run, a per-site bit marks them instead.  rdelta holds
+// kRunStride entries per run (the 18 offsets, then zeros), so a run's row is one
+// aligned 80-byte block the kernels read with 16-byte loads.  Rows ordering
+// makes a run cover most of an x-row of a vessel.  Returns false (nothing built)
+// when an entry does not fit that form or the encoding would not save enough
+// traffic (runs shorter than 4.5 sites on average: more than 16 bytes per site).
+bool build_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t np, int vdir, std::vector<uint32_t> &lword,
+                std::vector<int32_t> &run0, std::vector<int32_t> &rdelta) {
+    lword.assign((size_t)np, 0u);
+    run0.assign((size_t)((np + 1023) / 1024), 0);
+    rdelta.clear();
+    int32_t cur[18] = {0};
+    bool have[18] = {false};
+    int64_t run = -1;
+    for (int64_t q = 0; q < n; ++q) {
+        uint32_t miss = 0;
+        bool brk = run < 0;
+        for (int i = 0; i < 18; ++i) {
+            const int32_t v = nbr[(size_t)i * np + q];
+            if (v >= 0 && v < n_ref) {
+                if (have[i] && cur[i] != v - (int32_t)q) brk = true;
+            } else {
+                const int dir = i + 1, opp = (dir & 1) ? dir + 1 : dir - 1;
+                if ((int64_t)v != q + (int64_t)vdir * (opp - dir) * np) return false;
+                miss |= 1u << i;
+            }
+        }
+        if (brk) {
+            ++run;
+            if ((run + 1) * 72 > 16 * n) return false;
+            rdelta.resize((size_t)(run + 1) * kRunStride, 0);
+            for (int i = 0; i < 18; ++i) have[i] = false;
+        }
+        if ((q & 1023) == 0) run0[(size_t)(q >> 10)] = (int32_t)run;
+        for (int i = 0; i < 18; ++i)
+            if (!((miss >> i) & 1u) && !have[i]) {
+                have[i] = true;
+                cur[i] = nbr[(size_t)i * np + q] - (int32_t)q;
+                rdelta[(size_t)run * kRunStride + i] = cur[i];
+            }
+        lword[(size_t)q] = miss | ((uint32_t)(run - run0[(size_t)(q >> 10)]) << 18);
+    }
+    return n > 0;
 }
 
 // Canonical site order (ascending 3-D Morton key) and neighbour table in
@@ -762,6 +826,9 @@ int hg_sync(hg_ctx *ctx) {
     if (e) {
         CU(ctx, cudaMemsetAsync(ctx->errw.p, 0, sizeof e, ctx->stream));
         CU(ctx, cudaStreamSynchronize(ctx->stream));
+        if (e == 2)
+            return fail(ctx, HG_ERR_STATE, "a run-encoded kernel variant met a domain without a run encoding; "
+                                           "the state is not trusted");
         return fail(ctx, HG_ERR_TIMEOUT, "a bounded device wait gave up (code %d); the state is not trusted", e);
     }
     return HG_OK;
@@ -933,6 +1000,10 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     std::vector<int32_t> slot_site((size_t)std::max<int64_t>(1, n_adj), 0);
     for (int64_t q = 0; q < n; ++q)
         if (slot_of[q] >= 0) slot_site[slot_of[q]] = (int32_t)q;
+    std::vector<uint32_t> lword;
+    std::vector<int32_t> run0, rdelta;
+    if (build_runs(nbr.data(), n, n, np, aa ? -1 : 1, lword, run0, rdelta))
+        d->n_runs = (int64_t)rdelta.size() / kRunStride;
     d->io_codes_host = codes;
     d->slot_of_dev = slot_of;
     d->slots_host = slots;
@@ -964,6 +1035,11 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     if (!canon_of.empty()) {
         A(d->canon_of, (size_t)n * 4);
         A(d->dev_of, (size_t)n * 4);
+    }
+    if (d->n_runs) {
+        A(d->lword, lword.size() * 4);
+        A(d->run0, run0.size() * 4);
+        A(d->rdelta, rdelta.size() * 4);
     }
     auto cleanup = [&] {
         for (DevBuf *b : domain_buffers(d.get())) dev_free(c, *b);
@@ -998,6 +1074,11 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     if (!canon_of.empty()) {
         H2D(d->canon_of, canon_of.data(), (size_t)n * 4);
         H2D(d->dev_of, dev_of.data(), (size_t)n * 4);
+    }
+    if (d->n_runs) {
+        H2D(d->lword, lword.data(), lword.size() * 4);
+        H2D(d->run0, run0.data(), run0.size() * 4);
+        H2D(d->rdelta, rdelta.data(), rdelta.size() * 4);
     }
     if (e == cudaSuccess) e = cudaMemsetAsync(d->f[0].p, 0, d->f[0].bytes, up);
     if (e == cudaSuccess && d->f[1].p) e = cudaMemsetAsync(d->f[1].p, 0, d->f[1].bytes, up);
@@ -1053,6 +1134,30 @@ int hg_domain_info(hg_domain *d, int64_t *n_sites, int32_t *n_iolets, int64_t *n
     if (n_adjacent) *n_adjacent = d->n_adj;
     if (step) *step = d->step;
     if (device_bytes) *device_bytes = d->bytes;
+    return HG_OK;
+}
+
+int hg_encode_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t row_stride, int32_t scheme,
+                   uint32_t *lword_out, int32_t *run0_out, int32_t *rdelta_out, int64_t *n_runs_out) {
+    if (!nbr || !n_runs_out || n < 1 || n_ref < n || row_stride < n || row_stride > ((int64_t)1 << 30) ||
+        (scheme != HG_SCHEME_AB && scheme != HG_SCHEME_AA))
+        return HG_ERR_ARG;
+    std::vector<uint32_t> lw;
+    std::vector<int32_t> r0, rd;
+    *n_runs_out = 0;
+    if (!build_runs(nbr, n, n_ref, row_stride, scheme == HG_SCHEME_AA ? -1 : 1, lw, r0, rd)) return HG_OK;
+    *n_runs_out = (int64_t)rd.size() / kRunStride;
+    if (lword_out) std::copy(lw.begin(), lw.end(), lword_out);
+    if (run0_out) std::copy(r0.begin(), r0.end(), run0_out);
+    if (rdelta_out)
+        for (int64_t r = 0; r < *n_runs_out; ++r)
+            std::copy(rd.begin() + r * kRunStride, rd.begin() + r * kRunStride + 18, rdelta_out + r * 18);
+    return HG_OK;
+}
+
+int hg_domain_runs(hg_domain *d, int64_t *n_runs) {
+    if (!d || !n_runs) return HG_ERR_ARG;
+    *n_runs = d->n_runs;
     return HG_OK;
 }
 
@@ -1288,6 +1393,7 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
             p->sep.push_back(make_domdev(ctx, d));
             p->sep_n.push_back(d->n);
         } else if (doms.size() > 1) {
+            p->tiles_runs = p->tiles_runs && d->n_runs > 0;
             for (int64_t s = 0; s < d->n; s += ts) {
                 TileDev t;
                 t.dom = di;
@@ -1368,6 +1474,7 @@ int build_plan(hg_ctx *ctx, const std::vector<int32_t> &doms, Plan *&out) {
     if (doms.size() == 1) {
         p->single = true;
         p->one = make_domdev(ctx, ctx->doms[doms[0]]);
+        p->tiles_runs = ctx->doms[doms[0]]->n_runs > 0;
         const int64_t n1 = ctx->doms[doms[0]]->n;
         p->n_tiles = (n1 + ts - 1) / ts;
     }
@@ -1442,6 +1549,9 @@ cudaError_t enqueue_halo(hg_ctx *ctx, Plan *p, int off) {
     if (p->n_halo == 0) return cudaSuccess;
     const DomDev *doms = (const DomDev *)ctx->dom_table.p;
     const int64_t *steps = (const int64_t *)ctx->steps.p;
+    if (!p->halo_staged)
+        return launch_halo_direct(p->halo_elem, doms, steps, (const HaloMove *)p->halo_moves.p, p->n_halo, off,
+                                  ctx->stream);
     cudaError_t e = launch_halo_pack(p->halo_elem, doms, steps, (const HaloDev *)p->halo_pack.p, p->n_halo,
                                      p->send.p, off, ctx->stream);
     for (const auto &b : p->halo_blocks) {
@@ -1458,8 +1568,15 @@ cudaError_t enqueue_halo(hg_ctx *ctx, Plan *p, int off) {
 // start while the previous step's iolet update runs; separate per-domain launches
 // after the first may start while the previous one runs (they share no data within
 // a step; sites with iolet links still wait, through the chain, for that update).
-cudaError_t launch_sc(hg_ctx *ctx, Plan *p, int off, int parity, bool overlap) {
+// The run-encoded variants (8..11) step only domains that have a run encoding;
+// a launch over any other domain takes the table form of the same variant.
+CollideCfg collide_cfg(hg_ctx *ctx, bool runs) {
     CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
+    if (cfg.variant >= 8 && !runs) cfg.variant = cfg.variant == 8 ? 3 : cfg.variant == 9 ? 5 : cfg.variant - 4;
+    return cfg;
+}
+
+cudaError_t launch_sc(hg_ctx *ctx, Plan *p, int off, int parity, bool overlap) {
     const int64_t *steps = (const int64_t *)ctx->steps.p;
     const DomDev *table = (const DomDev *)ctx->dom_table.p;
     const int64_t ts = (int64_t)ctx->block * ctx->spt;
@@ -1467,14 +1584,15 @@ cudaError_t launch_sc(hg_ctx *ctx, Plan *p, int off, int parity, bool overlap) {
     for (size_t j = 0; j < p->sep.size(); ++j) {
         if (p->sep_n[j] == 0) continue;
         const OneDomain one{&p->sep[j], p->sep_n[j], steps, chained};
-        const cudaError_t e = launch_stream_collide(cfg, table, nullptr, (p->sep_n[j] + ts - 1) / ts, off,
-                                                    parity, one, ctx->stream);
+        const cudaError_t e = launch_stream_collide(collide_cfg(ctx, p->sep[j].lword != nullptr), table, nullptr,
+                                                    (p->sep_n[j] + ts - 1) / ts, off, parity, one, ctx->stream);
         if (e != cudaSuccess) return e;
         chained = true;
     }
     if (p->n_tiles == 0) return cudaSuccess;
     const OneDomain one{p->single ? &p->one : nullptr, p->single ? ctx->doms[p->doms[0]]->n : 0, steps, chained};
-    return launch_stream_collide(cfg, table, (const TileDev *)p->tiles.p, p->n_tiles, off, parity, one, ctx->stream);
+    return launch_stream_collide(collide_cfg(ctx, p->tiles_runs), table, (const TileDev *)p->tiles.p, p->n_tiles,
+                                 off, parity, one, ctx->stream);
 }
 
 cudaError_t enqueue_steps(hg_ctx *ctx, Plan *p, int64_t k, int mode) {
@@ -1639,8 +1757,8 @@ int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) 
     if (!variant_ok(ctx->storage, ctx->scheme, spt, variant))
         return fail(ctx, HG_ERR_ARG, "kernel variant must be 0 or 3, 1 or 2 with 1 or 2 sites per thread "
                                      "(2: AA only), 4 with 1 site per thread (AA only), 5 with 2 sites "
-                                     "per thread (A/B, 16-bit storage only), or 6 or 7 with 2 sites per "
-                                     "thread (AA only)");
+                                     "per thread (A/B, 16-bit storage only), 6 or 7 with 2 sites per "
+                                     "thread (AA only), or 8..11 with the shapes of 3, 5, 6, 7");
     if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));
@@ -1942,7 +2060,8 @@ void split_layout(const std::vector<int32_t> &nbr, int64_t stride, int64_t n, in
 
 void free_split(hg_ctx *ctx, hg_split *sp) {
     for (SplitPart &P : sp->parts)
-        for (DevBuf *b : {&P.f[0], &P.f[1], &P.nbr, &P.iomask, &P.ioprefix, &P.gidx}) dev_free(ctx, *b);
+        for (DevBuf *b : {&P.f[0], &P.f[1], &P.nbr, &P.iomask, &P.ioprefix, &P.gidx, &P.lword, &P.run0, &P.rdelta})
+            dev_free(ctx, *b);
     for (DevBuf *b : {&sp->bnd, &sp->io_codes, &sp->coef, &sp->slot_site, &sp->bcv, &sp->io_kind, &sp->M,
                       &sp->slots, &sp->force})
         dev_free(ctx, *b);
@@ -1964,8 +2083,10 @@ int split_plan(hg_split *sp, Plan *&out) {
     p->doms = key.doms;
     const int64_t ts = (int64_t)ctx->block * ctx->spt;
     std::vector<TileDev> tiles;
-    for (const SplitPart &P : sp->parts)
+    for (const SplitPart &P : sp->parts) {
+        p->tiles_runs = p->tiles_runs && P.n_runs > 0;
         for (int64_t s = 0; s < P.n_own; s += ts) tiles.push_back(TileDev{P.idx, (int32_t)std::min(ts, P.n_own - s), s});
+    }
     std::vector<IoDev> ios;
     std::vector<int2> chunks;
     for (int k = 0; k < sp->nio; ++k) {
@@ -2004,8 +2125,10 @@ int split_plan(hg_split *sp, Plan *&out) {
     }
     p->n_halo = (int64_t)sp->pack.size();
     p->halo_elem = (int)elem_bytes(ctx->storage);
-    for (const auto &b : sp->blocks)
-        p->halo_blocks.push_back({b.first * p->halo_elem, b.second * p->halo_elem});
+    p->halo_staged = sp->staged;
+    if (p->halo_staged)
+        for (const auto &b : sp->blocks)
+            p->halo_blocks.push_back({b.first * p->halo_elem, b.second * p->halo_elem});
     int rc = HG_OK;
     auto A = [&](DevBuf &b, size_t bytes) {
         if (rc == HG_OK) rc = dev_alloc(ctx, b, bytes);
@@ -2018,13 +2141,15 @@ int split_plan(hg_split *sp, Plan *&out) {
     A(p->counters, (ios.size() + 1) * sizeof(unsigned));
     A(p->rev, sizeof(RevSrc));
     A(p->fslots, sizeof(int2));
-    A(p->halo_pack, std::max<size_t>(1, sp->pack.size()) * sizeof(HaloDev));
-    A(p->halo_unpack, std::max<size_t>(1, sp->unpack.size()) * sizeof(HaloDev));
-    A(p->send, std::max<size_t>(1, sp->pack.size()) * p->halo_elem);
-    A(p->recv, std::max<size_t>(1, sp->pack.size()) * p->halo_elem);
+    const size_t n_staged = p->halo_staged ? sp->pack.size() : 0, n_moves = p->halo_staged ? 0 : sp->pack.size();
+    A(p->halo_pack, std::max<size_t>(1, n_staged) * sizeof(HaloDev));
+    A(p->halo_unpack, std::max<size_t>(1, n_staged) * sizeof(HaloDev));
+    A(p->send, std::max<size_t>(1, n_staged) * p->halo_elem);
+    A(p->recv, std::max<size_t>(1, n_staged) * p->halo_elem);
+    A(p->halo_moves, std::max<size_t>(1, n_moves) * sizeof(HaloMove));
     auto release = [&] {
         for (DevBuf *b : {&p->tiles, &p->ios, &p->adv, &p->chunks, &p->partials, &p->counters, &p->rev,
-                          &p->fslots, &p->halo_pack, &p->halo_unpack, &p->send, &p->recv})
+                          &p->fslots, &p->halo_pack, &p->halo_unpack, &p->send, &p->recv, &p->halo_moves})
             dev_free(ctx, *b);
     };
     if (rc != HG_OK) {
@@ -2040,8 +2165,12 @@ int split_plan(hg_split *sp, Plan *&out) {
     H2D(p->ios, ios.data(), ios.size() * sizeof(IoDev));
     H2D(p->adv, key.doms.data(), key.doms.size() * 4);
     H2D(p->chunks, chunks.data(), chunks.size() * sizeof(int2));
-    H2D(p->halo_pack, sp->pack.data(), sp->pack.size() * sizeof(HaloDev));
-    H2D(p->halo_unpack, sp->unpack.data(), sp->unpack.size() * sizeof(HaloDev));
+    std::vector<HaloMove> moves(n_moves);
+    for (size_t j = 0; j < n_moves; ++j)
+        moves[j] = HaloMove{sp->pack[j].dom, sp->unpack[j].dom, (uint32_t)sp->pack[j].off, (uint32_t)sp->unpack[j].off};
+    H2D(p->halo_pack, sp->pack.data(), n_staged * sizeof(HaloDev));
+    H2D(p->halo_unpack, sp->unpack.data(), n_staged * sizeof(HaloDev));
+    H2D(p->halo_moves, moves.data(), n_moves * sizeof(HaloMove));
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // the host tables above are temporaries
     if (e != cudaSuccess) {
         cudaStreamSynchronize(st);
@@ -2093,7 +2222,11 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
     if (nio < 0 || nio > kMaxIolets || (nio > 0 && !iolets)) return fail(ctx, HG_ERR_ARG, "bad iolet array");
     const double tau = lb ? lb->tau : 0.8;
     if (!(tau > 0.5)) return fail(ctx, HG_ERR_ARG, "tau must exceed 1/2");
-    if (lb && lb->ordering != HG_ORDER_MORTON) return fail(ctx, HG_ERR_ARG, "split domains keep the canonical order");
+    const int32_t ordering = lb ? lb->ordering : HG_ORDER_MORTON;
+    if (ordering < HG_ORDER_MORTON || ordering > HG_ORDER_BRICKS)
+        return fail(ctx, HG_ERR_ARG, "unknown ordering %d", ordering);
+    if (spar->exchange != HG_EXCHANGE_DIRECT && spar->exchange != HG_EXCHANGE_STAGED)
+        return fail(ctx, HG_ERR_ARG, "unknown halo exchange %d", spar->exchange);
     for (int q = 0; q < nio; ++q)
         if (!iolet_ok(iolets[q])) return fail(ctx, HG_ERR_ARG, "iolet %d out of range", q);
     CU(ctx, cudaSetDevice(ctx->device));
@@ -2102,6 +2235,7 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
     sp->n = n;
     sp->nio = nio;
     sp->tau = tau;
+    sp->staged = spar->exchange == HG_EXCHANGE_STAGED;
     sp->io.assign(iolets, iolets + nio);
     std::vector<int32_t> xs, nbr;
     {
@@ -2126,7 +2260,33 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
             return fail(ctx, HG_ERR_STATE, "context holds too many domains");
         }
     }
-    // global boundary slots in canonical order (as the whole domain numbers them)
+    // Device order of each partition's owned sites: canonical (Morton) or, like a
+    // whole domain, rows or bricks of the partition's own sites.  perm[p][q] = offset
+    // (from the partition's first canonical site) of the site at device position q;
+    // inv[p] is the inverse.  Empty: identity.
+    std::vector<std::vector<int32_t>> perm(k), inv(k);
+    if (ordering != HG_ORDER_MORTON)
+        for (int p = 0; p < k; ++p) {
+            const int64_t a = L.first[p], m = L.first[p + 1] - a;
+            std::vector<int32_t> sub(xs.begin() + 3 * a, xs.begin() + 3 * (a + m));
+            std::string why;
+            if (device_order(sub, m, ordering, perm[p], why) != HG_OK) {
+                free_split(ctx, sp.get());
+                return fail(ctx, HG_ERR_ARG, "%s", why.c_str());
+            }
+            inv[p].resize(m);
+            for (int64_t q = 0; q < m; ++q) inv[p][perm[p][q]] = (int32_t)q;
+        }
+    auto canon_at = [&](int p, int64_t q) -> int64_t { return L.first[p] + (perm[p].empty() ? q : perm[p][q]); };
+    auto dev_pos = [&](int p, int64_t c) -> int64_t {
+        const int64_t o = c - L.first[p];
+        return inv[p].empty() ? o : inv[p][o];
+    };
+    // Global boundary slots: partition by partition, in each partition's device order
+    // (so a partition's slots are one consecutive run its iomask/ioprefix address);
+    // the per-iolet slot lists below stay in canonical site order, which keeps the
+    // iolet reductions' summation order, and so their bits, independent of the
+    // partitioning and the ordering.
     std::vector<int32_t> slot_of(n, -1);
     std::vector<int64_t> per_io(nio + 1, 0);
     int64_t n_adj = 0;
@@ -2141,12 +2301,14 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
         }
         return ns;
     };
-    for (int64_t c = 0; c < n; ++c) {
-        int seen[18];
-        const int ns = distinct(c, seen);
-        for (int t = 0; t < ns; ++t) per_io[seen[t] + 1]++;
-        if (ns) slot_of[c] = (int32_t)n_adj++;
-    }
+    for (int p = 0; p < k; ++p)
+        for (int64_t q = 0; q < L.first[p + 1] - L.first[p]; ++q) {
+            const int64_t c = canon_at(p, q);
+            int seen[18];
+            const int ns = distinct(c, seen);
+            for (int t = 0; t < ns; ++t) per_io[seen[t] + 1]++;
+            if (ns) slot_of[c] = (int32_t)n_adj++;
+        }
     sp->n_adj = n_adj;
     for (int q = 0; q < nio; ++q) per_io[q + 1] += per_io[q];
     sp->io_ptr.assign(per_io.begin(), per_io.end());
@@ -2163,7 +2325,7 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
                 int seen[18];
                 const int ns = distinct(c, seen);
                 for (int t = 0; t < ns; ++t) slots[fill[seen[t]]++] = sl;
-                slot_site[sl] = (int32_t)(c - L.first[p]);
+                slot_site[sl] = (int32_t)dev_pos(p, c);
                 for (int i = 1; i < 19; ++i) {
                     const int32_t v = nbr[(size_t)(i - 1) * n + c];
                     codes[(size_t)sl * 18 + (i - 1)] = v;
@@ -2186,7 +2348,8 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
     A(sp->slots, slots.size() * 4);
     A(sp->force, (size_t)std::max(1, nio) * 16);
     // per partition: local tables (owned sites first, then ghosts)
-    std::vector<std::vector<int32_t>> tab(k), mask(k), pref(k), gidx(k);
+    std::vector<std::vector<int32_t>> tab(k), mask(k), pref(k), gidx(k), r0(k), rd(k);
+    std::vector<std::vector<uint32_t>> lw(k);
     for (int p = 0; p < k && rc == HG_OK; ++p) {
         SplitPart &P = sp->parts[p];
         P.first = L.first[p];
@@ -2196,7 +2359,7 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
         P.np = std::max<int64_t>(128, (P.n_loc + 127) / 128 * 128);
         const int64_t a = P.first, b = L.first[p + 1], np = P.np;
         auto local = [&](int64_t v) -> int64_t {
-            if (v >= a && v < b) return v - a;
+            if (v >= a && v < b) return dev_pos(p, v);
             return P.n_own + (std::lower_bound(P.ghosts.begin(), P.ghosts.end(), v) - P.ghosts.begin());
         };
         std::vector<int32_t> &T = tab[p];
@@ -2204,26 +2367,26 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
         for (int i = 1; i < 19; ++i) {
             const int opp = (i & 1) ? i + 1 : i - 1;
             for (int64_t q = 0; q < np; ++q) {
-                const int32_t v = q < P.n_own ? nbr[(size_t)(i - 1) * n + a + q] : -1;
+                const int32_t v = q < P.n_own ? nbr[(size_t)(i - 1) * n + canon_at(p, q)] : -1;
                 T[(size_t)(i - 1) * np + q] = v >= 0 ? (int32_t)local(v) : (int32_t)(q + (int64_t)(opp - i) * np);
             }
         }
         mask[p].assign((size_t)np / 32, 0u);
         pref[p].assign((size_t)np / 32, 0);
-        int32_t acc = 0;
-        for (int64_t q = 0; q < P.n_own; ++q)
-            if (slot_of[a + q] >= 0) mask[p][q >> 5] |= 1u << (q & 31);
-        const int32_t base = [&] {
-            for (int64_t c = a; c < b; ++c)
-                if (slot_of[c] >= 0) return slot_of[c];
-            return (int32_t)0;
-        }();
+        int32_t acc = 0, base = -1;
+        for (int64_t q = 0; q < P.n_own; ++q) {
+            const int32_t sl = slot_of[canon_at(p, q)];
+            if (sl < 0) continue;
+            mask[p][q >> 5] |= 1u << (q & 31);
+            if (base < 0) base = sl;
+        }
+        base = std::max(base, 0);
         for (size_t w = 0; w < mask[p].size(); ++w) {
             pref[p][w] = base + acc;
             acc += __builtin_popcount(mask[p][w]);
         }
         gidx[p].resize(P.n_loc);
-        for (int64_t q = 0; q < P.n_own; ++q) gidx[p][q] = (int32_t)(a + q);
+        for (int64_t q = 0; q < P.n_own; ++q) gidx[p][q] = (int32_t)canon_at(p, q);
         for (size_t g = 0; g < P.ghosts.size(); ++g) gidx[p][P.n_own + g] = (int32_t)P.ghosts[g];
         A(P.f[0], 19 * (size_t)np * eb);
         A(P.f[1], 19 * (size_t)np * eb);
@@ -2231,6 +2394,13 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
         A(P.iomask, mask[p].size() * 4);
         A(P.ioprefix, pref[p].size() * 4);
         A(P.gidx, gidx[p].size() * 4);
+        // owned sites only (ghost rows are never read); entries may point at ghosts
+        if (build_runs(T.data(), P.n_own, P.n_loc, np, 1, lw[p], r0[p], rd[p])) {
+            P.n_runs = (int64_t)rd[p].size() / kRunStride;
+            A(P.lword, lw[p].size() * 4);
+            A(P.run0, r0[p].size() * 4);
+            A(P.rdelta, rd[p].size() * 4);
+        }
     }
     if (rc != HG_OK) {
         free_split(ctx, sp.get());
@@ -2246,7 +2416,7 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
             for (const auto &e : need) {
                 const int64_t g = P.n_own + (std::lower_bound(P.ghosts.begin(), P.ghosts.end(), e.second) -
                                              P.ghosts.begin());
-                sp->pack.push_back(HaloDev{Q.idx, 0, (int64_t)(e.first + 1) * Q.np + (e.second - Q.first)});
+                sp->pack.push_back(HaloDev{Q.idx, 0, (int64_t)(e.first + 1) * Q.np + dev_pos(q, e.second)});
                 sp->unpack.push_back(HaloDev{P.idx, 0, (int64_t)(e.first + 1) * P.np + g});
             }
             sp->blocks.push_back({off, need.size()});
@@ -2276,6 +2446,11 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
         H2D(P.iomask, mask[p].data(), mask[p].size() * 4);
         H2D(P.ioprefix, pref[p].data(), pref[p].size() * 4);
         H2D(P.gidx, gidx[p].data(), gidx[p].size() * 4);
+        if (P.n_runs) {
+            H2D(P.lword, lw[p].data(), lw[p].size() * 4);
+            H2D(P.run0, r0[p].data(), r0[p].size() * 4);
+            H2D(P.rdelta, rd[p].data(), rd[p].size() * 4);
+        }
         for (DevBuf *b : {&P.f[0], &P.f[1]})
             if (e == cudaSuccess) e = cudaMemsetAsync(b->p, 0, b->bytes, st);
         if (e == cudaSuccess) e = cudaMemsetAsync((int64_t *)ctx->steps.p + P.idx, 0, sizeof(int64_t), st);
@@ -2284,6 +2459,9 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
         D.f[0] = P.f[0].p;
         D.f[1] = P.f[1].p;
         D.nbr = (const int32_t *)P.nbr.p;
+        D.lword = (const uint32_t *)P.lword.p;
+        D.run0 = (const int32_t *)P.run0.p;
+        D.rdelta = (const int32_t *)P.rdelta.p;
         D.iomask = (const uint32_t *)P.iomask.p;
         D.ioprefix = (const int32_t *)P.ioprefix.p;
         D.io_codes = (const int32_t *)sp->io_codes.p;

@@ -20,9 +20,19 @@ enum Storage : int { kF32 = 0, kF16 = 1, kBF16 = 2 };
 enum Scheme : int { kAB = 0, kAA = 1 };
 
 // Per-domain descriptor read by the stream-collide and read-back kernels.
+constexpr int kRunStride = 20;  // int32 entries per run of a run-encoded neighbour table
+
 struct DomDev {
     void *f[2];               // distributions, SoA [19][np]; AA uses f[0] only
     const int32_t *nbr;       // [18][np] device codes
+    // The same table run-length encoded (null when it does not compress): per site
+    // a word whose bits 0..17 flag the non-fluid links (their entry is the virtual
+    // index) and whose bits 18..27 give the site's run relative to the run of its
+    // 1024-site chunk (run0); per run the 18 offsets (entry minus site index) its
+    // fluid links share.
+    const uint32_t *lword;
+    const int32_t *run0;
+    const int32_t *rdelta;    // kRunStride entries per run: 18 offsets, 2 zeros (16-byte rows)
     const uint32_t *iomask;   // bit s: site s has an iolet link
     const int32_t *ioprefix;  // per 32-site word: flagged sites before it (slot = rank of the flag)
     const int32_t *io_codes;  // per slot x 18: canonical codes (-1 wall, -(2+k) iolet, >= 0 fluid)
@@ -147,6 +157,15 @@ cudaError_t launch_halo_pack(int elem, const DomDev *doms, const int64_t *steps,
                              int64_t n, void *send, int off, cudaStream_t st);
 cudaError_t launch_halo_unpack(int elem, const DomDev *doms, const int64_t *steps, const HaloDev *ent,
                                int64_t n, const void *recv, int off, cudaStream_t st);
+// One halo value moved straight from the sender's F_t to the receiver's ghost (both
+// partitions on one device): element offsets into the partitions' distribution
+// buffers, below 19 * np < 2^32 (a split holds at most 200 * 2^20 sites).
+struct HaloMove {
+    int32_t src_dom, dst_dom;
+    uint32_t src_off, dst_off;
+};
+cudaError_t launch_halo_direct(int elem, const DomDev *doms, const int64_t *steps, const HaloMove *mv,
+                               int64_t n, int off, cudaStream_t st);
 // Mass of a state held in canonical order ([19][stride], sites [0, n)): the same
 // chunks, order and rounding as launch_mass.
 cudaError_t launch_mass_flat(int storage, const void *f, int64_t n, int64_t stride, double2 *partials,

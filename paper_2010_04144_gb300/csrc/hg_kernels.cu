@@ -361,6 +361,17 @@ __global__ void k_halo_unpack(const DomDev *__restrict__ doms, const int64_t *__
     }
 }
 
+template <typename W>
+__global__ void k_halo_direct(const DomDev *__restrict__ doms, const int64_t *__restrict__ steps,
+                              const HaloMove *__restrict__ mv, int64_t n, int off) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const HaloMove m = mv[e];
+        const int64_t t = steps[m.src_dom] + off + 1;
+        ((W *)doms[m.dst_dom].f[t & 1])[m.dst_off] = ((const W *)doms[m.src_dom].f[t & 1])[m.src_off];
+    }
+}
+
 constexpr int kMassChunk = 8192;
 constexpr int kMassThreads = 256;
 
@@ -519,6 +530,14 @@ cudaError_t launch_halo_unpack(int elem, const DomDev *doms, const int64_t *step
         k_halo_unpack<uint32_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, ent, n, (const uint32_t *)recv, off);
     else
         k_halo_unpack<uint16_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, ent, n, (const uint16_t *)recv, off);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_halo_direct(int elem, const DomDev *doms, const int64_t *steps, const HaloMove *mv,
+                               int64_t n, int off, cudaStream_t st) {
+    if (n <= 0) return cudaSuccess;
+    if (elem == 4) k_halo_direct<uint32_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, mv, n, off);
+    else k_halo_direct<uint16_t><<<rb_grid(n), 256, 0, st>>>(doms, steps, mv, n, off);
     return cudaGetLastError();
 }
 

@@ -23,6 +23,7 @@ STORAGE = {"f32": 0, "f16": 1, "bf16": 2}
 SCHEME = {"ab": 0, "aa": 1}
 COUPLE = {"forward": 0, "alternate": 1}
 ORDER = {"morton": 0, "rows": 1, "bricks": 2}
+EXCHANGE = {"direct": 0, "staged": 1}
 FAULT_ALLOC, FAULT_DEVICE_WAIT = 1, 2
 STORE_DTYPE = {0: np.float32, 1: np.float16, 2: None}  # bf16 is returned as uint16 bits
 
@@ -56,7 +57,7 @@ class hg_lb_params(C.Structure):
 
 
 class hg_split_params(C.Structure):
-    _fields_ = [("n_parts", C.c_int32), ("reserved", C.c_int32), ("boundary_weight", C.c_double)]
+    _fields_ = [("n_parts", C.c_int32), ("exchange", C.c_int32), ("boundary_weight", C.c_double)]
 
 
 class hg_pair(C.Structure):
@@ -75,6 +76,9 @@ _SIGS = {
     "hg_domain_destroy": ([C.c_void_p], C.c_int),
     "hg_domain_info": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
                        C.c_int),
+    "hg_domain_runs": ([C.c_void_p, C.c_void_p], C.c_int),
+    "hg_encode_runs": ([C.c_void_p, C.c_int64, C.c_int64, C.c_int64, C.c_int32, C.c_void_p, C.c_void_p,
+                        C.c_void_p, C.c_void_p], C.c_int),
     "hg_domain_sites": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_domain_neighbours": ([C.c_void_p, C.c_void_p], C.c_int),
     "hg_couple": ([C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32], C.c_int),
@@ -196,6 +200,26 @@ def build_neighbours(xyz, iolets):
     return xs[:n], nbr[:, :n]
 
 
+def encode_runs(nbr, n=None, n_ref=None, scheme="ab"):
+    """Host-only run encoding (hg_encode_runs) of a device neighbour table nbr
+    (18, row_stride) int32 for sites [0, n) (default: every column), fluid entries in
+    [0, n_ref) (default n): returns (lword (row_stride,) uint32, run0 (chunks,) int32,
+    rdelta (n_runs, 18) int32), or None when the table does not compress."""
+    nbr = np.ascontiguousarray(nbr, dtype=np.int32)
+    stride = nbr.shape[1]
+    n = stride if n is None else int(n)
+    n_ref = n if n_ref is None else int(n_ref)
+    lword = np.zeros(stride, np.uint32)
+    run0 = np.zeros((stride + 1023) // 1024, np.int32)
+    rdelta = np.zeros((n * 16 // 72 + 1, 18), np.int32)
+    nr = C.c_int64()
+    sch = SCHEME[scheme] if isinstance(scheme, str) else int(scheme)
+    _check(lib().hg_encode_runs(_p(nbr), n, n_ref, stride, sch, _p(lword), _p(run0), _p(rdelta), C.byref(nr)))
+    if nr.value == 0:
+        return None
+    return lword, run0, rdelta[:nr.value]
+
+
 def split_layout(xyz, iolets, n_parts, boundary_weight=1.0):
     """Host-only partition of a domain (Section 2.2 / 2.2.1): (first (k+1,), ghosts (k,),
     halo (k, k) with halo[q, p] = values partition p pulls from partition q per step)."""
@@ -249,6 +273,7 @@ class Context:
         h = C.c_void_p()
         _check(lib().hg_ctx_create(C.byref(p), C.byref(h)))
         self.h = h
+        self.launch = (int(block_size), int(sites_per_thread), int(kernel_variant))
         self.domains = []
 
     def _ck(self, rc):
@@ -257,8 +282,8 @@ class Context:
     def domain(self, xyz, iolets, tau=0.8, ordering="morton"):
         return Domain(self, xyz, iolets, tau, ordering)
 
-    def split(self, xyz, iolets, n_parts, tau=0.8, boundary_weight=1.0):
-        return Split(self, xyz, iolets, n_parts, tau, boundary_weight)
+    def split(self, xyz, iolets, n_parts, tau=0.8, boundary_weight=1.0, ordering="morton", exchange="direct"):
+        return Split(self, xyz, iolets, n_parts, tau, boundary_weight, ordering, exchange)
 
     def inject_fault(self, kind, arg=0):
         """Host-side fault injection (FAULT_ALLOC: the arg-th next allocation fails;
@@ -340,8 +365,10 @@ class Domain:
         n, nio, nadj, step, nb = (C.c_int64(), C.c_int32(), C.c_int64(), C.c_int64(), C.c_int64())
         self.ctx._ck(lib().hg_domain_info(self.h, C.byref(n), C.byref(nio), C.byref(nadj),
                                           C.byref(step), C.byref(nb)))
+        runs = C.c_int64()
+        self.ctx._ck(lib().hg_domain_runs(self.h, C.byref(runs)))
         return dict(n_sites=n.value, n_iolets=nio.value, n_adjacent=nadj.value, step=step.value,
-                    device_bytes=nb.value)
+                    device_bytes=nb.value, n_runs=runs.value)
 
     @property
     def step(self):
@@ -439,12 +466,16 @@ class Domain:
 class Split:
     """A domain cut into partitions with a halo exchange every step (Section 2.2)."""
 
-    def __init__(self, ctx: Context, xyz, iolets, n_parts, tau=0.8, boundary_weight=1.0):
+    def __init__(self, ctx: Context, xyz, iolets, n_parts, tau=0.8, boundary_weight=1.0, ordering="morton",
+                 exchange="direct"):
         self.ctx = ctx
         xyz = np.ascontiguousarray(xyz, dtype=np.int32).reshape(-1, 3)
         lb = hg_lb_params()
-        lb.tau, lb.ordering = float(tau), 0
-        sp = hg_split_params(int(n_parts), 0, float(boundary_weight))
+        lb.tau = float(tau)
+        lb.ordering = ORDER[ordering] if isinstance(ordering, str) else int(ordering)
+        self.ordering = lb.ordering
+        sp = hg_split_params(int(n_parts), EXCHANGE[exchange] if isinstance(exchange, str) else int(exchange),
+                             float(boundary_weight))
         h = C.c_void_p()
         ctx._ck(lib().hg_split_create(ctx.h, _p(xyz), xyz.shape[0], iolet_struct_array(iolets), len(iolets),
                                       C.byref(lb), C.byref(sp), C.byref(h)))

@@ -45,21 +45,22 @@ def adjacent_bound(radius):
 
 def footprint_bytes(n_sites, storage, scheme, n_iolets=2, iolet_radii=None, reordered=False):
     """Upper bound on the HBM bytes of one domain before it is built: distributions,
-    neighbour table, iolet mask and prefix per site; moments, link codes, link coefficients
-    and site index per boundary slot (164 B) plus one list entry per (site, iolet) pair;
-    per-iolet values; the two site permutations of a reordered layout; and the 256-byte
-    rounding of each buffer.  With the iolet radii the boundary slots are bounded per iolet
+    neighbour table, iolet mask and prefix per site; the table's run encoding where it is
+    built (4 bytes per site plus at most 16 bytes per site of run offsets); moments, link
+    codes, link coefficients and site index per boundary slot (164 B) plus one list entry
+    per (site, iolet) pair; per-iolet values; the two site permutations of a reordered
+    layout; and the 256-byte rounding of each buffer.  With the iolet radii the boundary slots are bounded per iolet
     (adjacent_bound); without them 5% of the sites is assumed."""
     np_ = max(128, (n_sites + 127) // 128 * 128)
     copies = 2 if scheme == H.SCHEME["ab"] else 1
-    per_site = 19 * _STATE_BYTES[storage] * copies + 72 + 0.25 + (8 if reordered else 0)
+    per_site = 19 * _STATE_BYTES[storage] * copies + 72 + 0.25 + (8 if reordered else 0) + 20 + 4 / 1024
     if iolet_radii is not None:
         pairs = min(18 * n_sites, sum(adjacent_bound(r) for r in iolet_radii))
         adjacent = min(n_sites, pairs)
         n_iolets = len(iolet_radii)
     else:
         adjacent = pairs = 0.05 * n_sites
-    return int(per_site * np_ + 164 * adjacent + 4 * pairs + 64 * n_iolets + 16 * 256 + 4 * 4096)
+    return int(per_site * np_ + 164 * adjacent + 4 * pairs + 64 * n_iolets + 20 * 256 + 4 * 4096)
 
 
 def geometry_footprint(geo, storage, scheme, reordered=False):

@@ -40,6 +40,32 @@ def test_orderings_bit_identical(gpu, storage, scheme, launch):
                 assert np.array_equal(x, y), (o, steps, k)
 
 
+@pytest.mark.parametrize("storage,scheme,pairs", [
+    ("f32", "ab", [((256, 2, 3), (256, 2, 8)), ((128, 1, 3), (128, 1, 8))]),
+    ("f16", "ab", [((256, 2, 5), (256, 2, 9)), ((128, 2, 5), (128, 4, 8))]),
+    ("f32", "aa", [((128, 2, 6), (128, 2, 10)), ((256, 2, 7), (256, 2, 11)), ((256, 1, 3), (256, 1, 8))]),
+    ("f16", "aa", [((128, 2, 6), (128, 2, 10)), ((64, 2, 7), (64, 2, 11))]),
+    ("bf16", "aa", [((256, 2, 6), (256, 2, 10))])])
+def test_run_encoded_table_bit_identical(gpu, storage, scheme, pairs):
+    """Variants 8..11 read the run-encoded neighbour table, which a rows- or bricks-ordered
+    domain has: same bits as their table-reading counterparts (3, 5, 6, 7), odd and even
+    step counts, through graph replays and direct steps."""
+    for o in ("rows", "bricks"):
+        geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
+        ctx = gpu.Context(storage=storage, scheme=scheme)
+        try:
+            d = ctx.domain(geo.xyz, geo.iolets, tau=0.8, ordering=o)
+            assert d.info()["n_runs"] > 0 and d.n / d.info()["n_runs"] > 4.5, o
+        finally:
+            ctx.close()
+        for base, runs in pairs:
+            for steps in (37, 120):
+                ref = _run_tree(gpu, o, storage, scheme, steps, base)
+                got = _run_tree(gpu, o, storage, scheme, steps, runs)
+                for k, (x, y) in enumerate(zip(ref, got)):
+                    assert np.array_equal(x, y), (o, base, runs, steps, k)
+
+
 def test_orderings_neighbours_match_oracle(gpu, oracle_mod):
     geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7))
     od = oracle_mod.Domain(geo.xyz, geo.iolets, tau=0.8)

@@ -259,7 +259,10 @@ LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128,
             ("ab", 256, 1, 3), ("ab", 128, 4, 3), ("aa", 256, 1, 3), ("aa", 128, 2, 3),
             ("aa", 256, 1, 4), ("aa", 64, 1, 4), ("aa", 512, 1, 4),
             ("ab", 256, 2, 5), ("ab", 64, 2, 5),   # variant 5: A/B, 16-bit storage only
-            ("aa", 256, 2, 6), ("aa", 64, 2, 6), ("aa", 128, 2, 7), ("aa", 512, 2, 7)]  # AA pairs
+            ("aa", 256, 2, 6), ("aa", 64, 2, 6), ("aa", 128, 2, 7), ("aa", 512, 2, 7),  # AA pairs
+            # 8..11: 3, 5, 6, 7 on the run-encoded table (here Morton order: the table path;
+            # the run path on rows-ordered domains is checked in test_gpu_orderings.py)
+            ("ab", 256, 2, 8), ("aa", 128, 1, 8), ("ab", 128, 2, 9), ("aa", 256, 2, 10), ("aa", 128, 2, 11)]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
@@ -268,7 +271,7 @@ def test_kernel_variants_bit_identical(gpu, storage):
     geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)
     ref = {}
     for (scheme, block, spt, var) in LAUNCHES:
-        if var == 5 and storage == "f32":
+        if var in (5, 9) and storage == "f32":
             continue
         ctx = gpu.Context(storage=storage, scheme=scheme, block_size=block, sites_per_thread=spt,
                           kernel_variant=var)
