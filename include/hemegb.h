@@ -124,7 +124,10 @@ typedef struct {
                                  8, 9, 10, 11 = 3, 5, 6, 7 reading the run-encoded
                                      neighbour table (hg_domain_runs) instead of the
                                      18 table rows; a launch over a domain without
-                                     one runs 3, 5, 6, 7; same shapes as 3, 5, 6, 7 */
+                                     one runs 3, 5, 6, 7; same shapes as 3, 5, 6, 7;
+                                 12 = 8 for AA (1 or 2 sites per thread) with the odd
+                                     step's 18 entries held across the collision
+                                     instead of reread */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */

@@ -465,7 +465,7 @@ __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T 
 // ---- AA odd step: gather F_{t-1} (swapped) from x - c_i, scatter F_t to x + c_i ----
 // Entry OPP(I) of the site's row is the site at x + c_I; its virtual index for
 // a non-fluid link turns the scatter into the raw write to the own slot OPP(I).
-template <int S, bool HINT = false, bool RUNS = false>
+template <int S, bool HINT = false, bool RUNS = false, bool KEEP = false>
 __device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
@@ -481,7 +481,10 @@ __device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *
     const int slot = iolet_fixup<S>(D, s, g);
     const float4 m = collide_s<S>(g, D.omega);
     typename St<S>::T *wb = opaque(buf);
-    tab.reload().all(nb);  // reread (cache hits) instead of keeping 18 entries live
+    // the scatter addresses are the gather addresses (entry OPP(I) of the site at x +
+    // c_I): KEEP holds the 18 entries across the collision, otherwise they are reread
+    // (cache hits), which frees 18 registers
+    if constexpr (!KEEP) tab.reload().all(nb);
     wb[s] = Tr::template st<0>(g[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
@@ -948,7 +951,7 @@ __device__ __forceinline__ void tile_aa_even_tma(const DomDev &D, const TileDev 
 // AA step kind), 2 = read from the domain's step counter per block (A/B, and AA
 // batches whose domains are at different parities).
 // One tile of one domain, after the prologue has located it.
-template <int S, int SCHEME, int SPT, int PAR, int V, bool RUNS>
+template <int S, int SCHEME, int SPT, int PAR, int V, bool RUNS, bool KEEP = false>
 __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const TileDev &tl, bool odd,
                                                          uint32_t *stage) {
     using T = typename St<S>::T;
@@ -1015,7 +1018,7 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
             } else {
                 T *buf = (T *)D.f[0];
                 if (live) {
-                    if (odd) site_aa_odd<S, HINT, RUNS>(D, buf, s);
+                    if (odd) site_aa_odd<S, HINT, RUNS, KEEP>(D, buf, s);
                     else site_aa_even<S, HINT>(D, buf, s);
                 }
             }
@@ -1026,7 +1029,11 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
 // Variants 8..11 are 3, 5, 6, 7 reading the run-encoded neighbour table.  The host
 // launches them only on domains that have one (the others get 3, 5, 6, 7); a domain
 // without one here is reported through the error word (code 2) and left untouched.
-template <int V> constexpr int table_variant() { return V == 8 ? 3 : V == 9 ? 5 : V == 10 ? 6 : V == 11 ? 7 : V; }
+// Variant 12 is 8 for the AA scheme with the odd step's 18 entries held across the
+// collision instead of reread.
+template <int V> constexpr int table_variant() {
+    return V == 8 || V == 12 ? 3 : V == 9 ? 5 : V == 10 ? 6 : V == 11 ? 7 : V;
+}
 
 template <int S, int SCHEME, int SPT, int PAR, int V>
 __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileDev &tl, bool odd,
@@ -1036,7 +1043,7 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
             if (threadIdx.x == 0) atomicExch(D.err, 2);
             return;
         }
-        stream_collide_tile_impl<S, SCHEME, SPT, PAR, table_variant<V>(), true>(D, tl, odd, stage);
+        stream_collide_tile_impl<S, SCHEME, SPT, PAR, table_variant<V>(), true, V == 12>(D, tl, odd, stage);
     } else {
         stream_collide_tile_impl<S, SCHEME, SPT, PAR, V, false>(D, tl, odd, stage);
     }
@@ -1162,6 +1169,14 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
             case 1: return launch_sc_one<S, SCHEME, PAR, 8, 1>(cfg, doms, tiles, n_tiles, off, one, st);
             case 2: return launch_sc_one<S, SCHEME, PAR, 8, 2>(cfg, doms, tiles, n_tiles, off, one, st);
             case 4: return launch_sc_one<S, SCHEME, PAR, 8, 4>(cfg, doms, tiles, n_tiles, off, one, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (cfg.variant == 12) {
+        if constexpr (SCHEME != kAA) return cudaErrorInvalidValue;
+        else switch (cfg.spt) {
+            case 1: return launch_sc_one<S, SCHEME, PAR, 12, 1>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 2: return launch_sc_one<S, SCHEME, PAR, 12, 2>(cfg, doms, tiles, n_tiles, off, one, st);
             default: return cudaErrorInvalidValue;
         }
     }

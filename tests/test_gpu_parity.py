@@ -260,9 +260,10 @@ LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128,
             ("aa", 256, 1, 4), ("aa", 64, 1, 4), ("aa", 512, 1, 4),
             ("ab", 256, 2, 5), ("ab", 64, 2, 5),   # variant 5: A/B, 16-bit storage only
             ("aa", 256, 2, 6), ("aa", 64, 2, 6), ("aa", 128, 2, 7), ("aa", 512, 2, 7),  # AA pairs
-            # 8..11: 3, 5, 6, 7 on the run-encoded table (here Morton order: the table path;
+            # 8..12: 3, 5, 6, 7, 3 on the run-encoded table (here Morton order: the table path;
             # the run path on rows-ordered domains is checked in test_gpu_orderings.py)
-            ("ab", 256, 2, 8), ("aa", 128, 1, 8), ("ab", 128, 2, 9), ("aa", 256, 2, 10), ("aa", 128, 2, 11)]
+            ("ab", 256, 2, 8), ("aa", 128, 1, 8), ("ab", 128, 2, 9), ("aa", 256, 2, 10), ("aa", 128, 2, 11),
+            ("aa", 256, 1, 12)]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
