@@ -497,8 +497,8 @@ def run_coupled(args, H, device):
         ven = S.tree(spec, venous=True)
     ctx = H.Context(device=device, storage="f32", scheme=args.coupled_scheme)
     try:
-        da = ctx.domain(art.xyz, art.iolets)
-        dv = ctx.domain(ven.xyz, ven.iolets)
+        da = ctx.domain(art.xyz, art.iolets, ordering=args.coupled_ordering)
+        dv = ctx.domain(ven.xyz, ven.iolets, ordering=args.coupled_ordering)
         if one_to_n:
             u = S.uniform_draws(2010041444, len(ven.iolets))
             pairs = SV.coupled_job_from_trees(0, 0.0, 0, art, ven, u).pairs
@@ -562,6 +562,7 @@ def run_coupled(args, H, device):
                            "fan_out_max": int(fan.max()), "fan_out_min": int(fan[1:].min()),
                            "factor_range": [min(p[2] for p in pairs), max(p[2] for p in pairs)],
                            "scheme": args.coupled_scheme, "exchange": args.coupled_mode,
+                           "ordering": args.coupled_ordering, "n_runs": [da.info()["n_runs"], dv.info()["n_runs"]],
                            "settle_steps": args.coupled_settle,
                            "launch": {"block": best[0], "sites_per_thread": best[1], "kernel_variant": best[2]}},
                 "roofline": {"bound": "hbm", "achieved": B * n / (per / 1e3) / 1e9, "peak": peak,
@@ -709,7 +710,7 @@ def run_precision(args, H, device):
     for storage, scheme in (("f32", "ab"), ("f32", "aa"), ("f16", "aa"), ("bf16", "aa")):
         ctx = H.Context(device=device, storage=storage, scheme=scheme)
         try:
-            d = ctx.domain(geo.xyz, geo.iolets)
+            d = ctx.domain(geo.xyz, geo.iolets, ordering="rows")
             best, _ = autotune(ctx)
             ctx.step(args.warmup)
             torch.cuda.synchronize()
@@ -781,6 +782,8 @@ def main():
                     help="split config: load-balancing cost of a site next to an iolet")
     ap.add_argument("--coupled-scale", type=float, default=2.12)
     ap.add_argument("--coupled-scheme", default="ab")
+    ap.add_argument("--coupled-ordering", default="rows",
+                    help="coupled config: device site ordering of both trees (the ~10M-site tree tunes to rows)")
     ap.add_argument("--coupled-settle", type=int, default=4000,
                     help="untimed steps before the coupled timing, so flow reaches the outlets")
     ap.add_argument("--velocity-area", action="store_true",
