@@ -127,7 +127,10 @@ typedef struct {
                                      one runs 3, 5, 6, 7; same shapes as 3, 5, 6, 7;
                                  12 = 8 for AA (1 or 2 sites per thread) with the odd
                                      step's 18 entries held across the collision
-                                     instead of reread */
+                                     instead of reread;
+                                 13 = 8 (2 or 4 sites per thread) with every site's
+                                     link word loaded, and its run row prefetched,
+                                     before the first site's gathers */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */

@@ -29,6 +29,7 @@ DEFAULT_CANDIDATES = (
     # 8..11: 3, 5, 6, 7 reading the run-encoded neighbour table
     (256, 1, 8), (128, 2, 8), (256, 2, 8), (128, 2, 9), (256, 2, 9), (128, 2, 10), (256, 2, 10), (256, 2, 11),
     (256, 1, 12), (128, 1, 12), (128, 2, 12),  # 12: AA, run-encoded, odd-step entries held
+    (128, 2, 13), (256, 2, 13), (128, 4, 13),  # 13: run-encoded, link words hoisted
 )
 # Variant 4 (staged AA odd-step stores) is measured slower than variant 1 on
 # every workload tried; it stays available through Context.set_launch.

@@ -286,9 +286,11 @@ template <bool HINT> struct TabNb {
         return load_nbr<HINT>(p + (int64_t)(I - 1) * np);
     }
     __device__ __forceinline__ void all(int32_t nb[18]) const {
-        unroll<1, 19>([&](auto ic) { nb[decltype(ic)::v - 1] = at<decltype(ic)::v>(); });
+#pragma unroll
+        for (int i = 0; i < 18; ++i) nb[i] = load_nbr<HINT>(p + (int64_t)i * np);
     }
     __device__ __forceinline__ TabNb reload() const { return TabNb(opaque_ptr(p), np); }
+    __device__ __forceinline__ void prefetch() const {}
 };
 template <int SCHEME, bool HINT> struct RunNb {
     uint32_t w;
@@ -322,6 +324,11 @@ template <int SCHEME, bool HINT> struct RunNb {
         });
     }
     __device__ __forceinline__ RunNb reload() const { return RunNb(w, opaque_ptr(rd), s, np); }
+    // bring the run's row into L1 ahead of all(): its 80 bytes span at most two lines
+    __device__ __forceinline__ void prefetch() const {
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(rd));
+        asm volatile("prefetch.global.L1 [%0];" ::"l"(rd + kRunStride - 1));
+    }
 };
 // The same for a pair of adjacent sites s, s+1 (s even: both in one 1024-site
 // chunk): one 8-byte load of both table entries, or of both words; a run shared
@@ -419,11 +426,16 @@ template <typename T> __device__ __forceinline__ T *opaque(T *p) {
 // ---- A/B pull: F_{t-1} in src, F_t to dst ----
 template <int S, bool HINT = false, bool RUNS = false>
 __device__ __forceinline__ void site_ab(const DomDev &D, const typename St<S>::T *__restrict__ src,
-                                        typename St<S>::T *__restrict__ dst, int64_t s) {
+                                        typename St<S>::T *__restrict__ dst, int64_t s);
+
+// The A/B site update with the site's neighbour accessor already made.
+template <int S, bool HINT, typename NB>
+__device__ __forceinline__ void site_ab_with(const DomDev &D, const typename St<S>::T *__restrict__ src,
+                                             typename St<S>::T *__restrict__ dst, int64_t s, const NB &tab) {
     using Tr = St<S>;
     const int64_t np = D.np;
     int32_t nb[18];
-    NbOf<kAB, HINT, RUNS>(D, s).all(nb);
+    tab.all(nb);
     float g[19];
     g[0] = Tr::template ld<0>(load_ro<HINT>(src + s));
     unroll<1, 19>([&](auto ic) {  // virtual indices: walls read their own opposite value
@@ -437,6 +449,12 @@ __device__ __forceinline__ void site_ab(const DomDev &D, const typename St<S>::T
         dst[(int64_t)I * np + s] = Tr::template st<I>(g[I]);
     });
     if (slot >= 0) D.bnd[slot] = m;
+}
+
+template <int S, bool HINT, bool RUNS>
+__device__ __forceinline__ void site_ab(const DomDev &D, const typename St<S>::T *__restrict__ src,
+                                        typename St<S>::T *__restrict__ dst, int64_t s) {
+    site_ab_with<S, HINT>(D, src, dst, s, NbOf<kAB, HINT, RUNS>(D, s));
 }
 
 // ---- AA even step: state G_t natural at the own site -> F_t swapped at the own site ----
@@ -465,11 +483,11 @@ __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T 
 // ---- AA odd step: gather F_{t-1} (swapped) from x - c_i, scatter F_t to x + c_i ----
 // Entry OPP(I) of the site's row is the site at x + c_I; its virtual index for
 // a non-fluid link turns the scatter into the raw write to the own slot OPP(I).
-template <int S, bool HINT = false, bool RUNS = false, bool KEEP = false>
-__device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s) {
+template <int S, bool HINT, bool RUNS, bool KEEP, typename NB>
+__device__ __forceinline__ void site_aa_odd_with(const DomDev &D, typename St<S>::T *buf, int64_t s,
+                                                 const NB &tab) {
     using Tr = St<S>;
     const int64_t np = D.np;
-    const NbOf<kAA, HINT, RUNS> tab(D, s);
     int32_t nb[18];
     tab.all(nb);
     float g[19];
@@ -484,13 +502,26 @@ __device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *
     // the scatter addresses are the gather addresses (entry OPP(I) of the site at x +
     // c_I): KEEP holds the 18 entries across the collision, otherwise they are reread
     // (cache hits), which frees 18 registers
-    if constexpr (!KEEP) tab.reload().all(nb);
     wb[s] = Tr::template st<0>(g[0]);
-    unroll<1, 19>([&](auto ic) {
-        constexpr int I = decltype(ic)::v;
-        wb[(int64_t)I * np + nb[OPP(I) - 1]] = Tr::template st<I>(g[I]);
-    });
+    if constexpr (RUNS || KEEP) {
+        if constexpr (!KEEP) tab.reload().all(nb);
+        unroll<1, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            wb[(int64_t)I * np + nb[OPP(I) - 1]] = Tr::template st<I>(g[I]);
+        });
+    } else {  // table: each store's entry reread right before it
+        const int32_t *nb2 = opaque(D.nbr);
+        unroll<1, 19>([&](auto ic) {
+            constexpr int I = decltype(ic)::v;
+            wb[(int64_t)I * np + __ldg(nb2 + (int64_t)(OPP(I) - 1) * np + s)] = Tr::template st<I>(g[I]);
+        });
+    }
     if (slot >= 0) D.bnd[slot] = m;
+}
+
+template <int S, bool HINT = false, bool RUNS = false, bool KEEP = false>
+__device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s) {
+    site_aa_odd_with<S, HINT, RUNS, KEEP>(D, buf, s, NbOf<kAA, HINT, RUNS>(D, s));
 }
 
 // ==== async-staged variant (V = 1) ==========================================
@@ -772,16 +803,15 @@ __device__ __forceinline__ void site_ab_pair(const DomDev &D, const typename St<
 // the gathers and for the re-read that addresses the scatter, and one load and one
 // store of their two rest values; the 18 gathers and 18 scattered stores stay per
 // site.  The odd step reads slot OPP(I) at x - c_I and writes slot I at x + c_I.
-template <int S, bool HINT, bool RUNS = false>
+template <int S, bool HINT>
 __device__ __forceinline__ void site_aa_odd_pair(const DomDev &D, typename St<S>::T *buf, int64_t s) {
     using Tr = St<S>;
     const int64_t np = D.np;
-    const Nb2Of<kAA, RUNS> tab(D, s);
     float ga[19], gb[19];
     Pair<S>::template ld<0>(buf + s, ga[0], gb[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int2 nb = tab.template at<I>();
+        const int2 nb = __ldg(reinterpret_cast<const int2 *>(D.nbr + (int64_t)(I - 1) * np + s));
         ga[I] = Tr::template ld<I>(load_rw<HINT>(buf + ((int64_t)OPP(I) * np + nb.x)));
         gb[I] = Tr::template ld<I>(load_rw<HINT>(buf + ((int64_t)OPP(I) * np + nb.y)));
     });
@@ -790,11 +820,11 @@ __device__ __forceinline__ void site_aa_odd_pair(const DomDev &D, typename St<S>
     const float4 ma = collide_s<S>(ga, D.omega);
     const float4 mb = collide_s<S>(gb, D.omega);
     typename St<S>::T *wb = opaque(buf);
-    const auto tab2 = tab.reload();  // reread (L1 hits) instead of keeping 36 entries live
+    const int32_t *nb2 = opaque(D.nbr);  // reread (L1 hits) instead of keeping 36 entries live
     Pair<S>::template st<0>(wb + s, ga[0], gb[0]);
     unroll<1, 19>([&](auto ic) {
         constexpr int I = decltype(ic)::v;
-        const int2 tg = tab2.template at<OPP(I)>();
+        const int2 tg = __ldg(reinterpret_cast<const int2 *>(nb2 + (int64_t)(OPP(I) - 1) * np + s));
         wb[(int64_t)I * np + tg.x] = Tr::template st<I>(ga[I]);
         wb[(int64_t)I * np + tg.y] = Tr::template st<I>(gb[I]);
     });
@@ -951,7 +981,7 @@ __device__ __forceinline__ void tile_aa_even_tma(const DomDev &D, const TileDev 
 // AA step kind), 2 = read from the domain's step counter per block (A/B, and AA
 // batches whose domains are at different parities).
 // One tile of one domain, after the prologue has located it.
-template <int S, int SCHEME, int SPT, int PAR, int V, bool RUNS, bool KEEP = false>
+template <int S, int SCHEME, int SPT, int PAR, int V, bool RUNS, bool KEEP = false, bool HOIST = false>
 __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const TileDev &tl, bool odd,
                                                          uint32_t *stage) {
     using T = typename St<S>::T;
@@ -987,7 +1017,7 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
         const int r = 2 * threadIdx.x;
         const int64_t s = tl.start + r;  // even: tiles start at multiples of 2 * blockDim
         if (r + 1 < tl.count) {
-            if (odd) site_aa_odd_pair<S, HINT, false>(D, buf, s);
+            if (odd) site_aa_odd_pair<S, HINT>(D, buf, s);
             else site_aa_even_pair<S, HINT>(D, buf, s);
         } else if (r < tl.count) {  // ragged tail: one site
             if (odd) site_aa_odd<S, HINT, false>(D, buf, s);
@@ -1002,6 +1032,36 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
         T *dst = (T *)D.f[odd ? 1 : 0];
         if (r + 1 < tl.count) site_ab_pair<S, RUNS>(D, src, dst, s);
         else if (r < tl.count) site_ab<S, false, RUNS>(D, src, dst, s);  // ragged tail: one site
+    } else if (HOIST && (SCHEME == kAB || odd)) {
+        // every site's link word first (and a prefetch of its run row into L1), then the
+        // sites one by one: a later site's decode no longer waits on its own word and row
+        constexpr bool HINT = V == 3;
+        uint32_t ws[SPT];
+        const int32_t *rds[SPT];
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) {
+            const int r = j * blockDim.x + threadIdx.x;
+            ws[j] = 0;
+            rds[j] = D.rdelta;
+            if (r < tl.count) {
+                const RunNb<SCHEME, HINT> t(D, tl.start + r);
+                t.prefetch();
+                ws[j] = t.w;
+                rds[j] = t.rd;
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < SPT; ++j) {
+            const int r = j * blockDim.x + threadIdx.x;
+            if (r >= tl.count) continue;
+            const int64_t s = tl.start + r;
+            const RunNb<SCHEME, HINT> t(ws[j], rds[j], (int32_t)s, (int32_t)D.np);
+            if constexpr (SCHEME == kAB) {
+                site_ab_with<S, HINT>(D, (const T *)D.f[odd ? 0 : 1], (T *)D.f[odd ? 1 : 0], s, t);
+            } else {
+                site_aa_odd_with<S, HINT, true, false>(D, (T *)D.f[0], s, t);
+            }
+        }
     } else {
         constexpr bool HINT = V == 3;
 #pragma unroll
@@ -1030,9 +1090,10 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
 // launches them only on domains that have one (the others get 3, 5, 6, 7); a domain
 // without one here is reported through the error word (code 2) and left untouched.
 // Variant 12 is 8 for the AA scheme with the odd step's 18 entries held across the
-// collision instead of reread.
+// collision instead of reread; 13 is 8 with every site's link word loaded (and its
+// run row prefetched) before the first site's gathers.
 template <int V> constexpr int table_variant() {
-    return V == 8 || V == 12 ? 3 : V == 9 ? 5 : V == 10 ? 6 : V == 11 ? 7 : V;
+    return V == 8 || V == 12 || V == 13 ? 3 : V == 9 ? 5 : V == 10 ? 6 : V == 11 ? 7 : V;
 }
 
 template <int S, int SCHEME, int SPT, int PAR, int V>
@@ -1043,7 +1104,8 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
             if (threadIdx.x == 0) atomicExch(D.err, 2);
             return;
         }
-        stream_collide_tile_impl<S, SCHEME, SPT, PAR, table_variant<V>(), true, V == 12>(D, tl, odd, stage);
+        stream_collide_tile_impl<S, SCHEME, SPT, PAR, table_variant<V>(), true, V == 12, V == 13>(D, tl, odd,
+                                                                                                 stage);
     } else {
         stream_collide_tile_impl<S, SCHEME, SPT, PAR, V, false>(D, tl, odd, stage);
     }
@@ -1169,6 +1231,13 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
             case 1: return launch_sc_one<S, SCHEME, PAR, 8, 1>(cfg, doms, tiles, n_tiles, off, one, st);
             case 2: return launch_sc_one<S, SCHEME, PAR, 8, 2>(cfg, doms, tiles, n_tiles, off, one, st);
             case 4: return launch_sc_one<S, SCHEME, PAR, 8, 4>(cfg, doms, tiles, n_tiles, off, one, st);
+            default: return cudaErrorInvalidValue;
+        }
+    }
+    if (cfg.variant == 13) {
+        switch (cfg.spt) {
+            case 2: return launch_sc_one<S, SCHEME, PAR, 13, 2>(cfg, doms, tiles, n_tiles, off, one, st);
+            case 4: return launch_sc_one<S, SCHEME, PAR, 13, 4>(cfg, doms, tiles, n_tiles, off, one, st);
             default: return cudaErrorInvalidValue;
         }
     }
