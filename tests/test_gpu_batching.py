@@ -1,8 +1,8 @@
 """Mixed plans: in a step over several domains, the large ones (≥ 2^20 sites) are launched
 one by one with the single-domain kernel, chained by programmatic dependent launch, and
 the small ones share one tile-table launch.  Each domain's result is bit-identical to the
-same domain stepped alone, for both schemes and 32/16-bit storage, with coupling between a
-large and a small domain."""
+same domain stepped alone, for both schemes and 32/16-bit storage, the table and the
+run-encoded kernel variants, with coupling between a large and a small domain."""
 import numpy as np
 import pytest
 
@@ -20,24 +20,34 @@ def _geoms():
     return [small[0], big, small[1]]
 
 
-def _alone(gpu, geo, storage, scheme, steps):
+def _alone(gpu, geo, storage, scheme, steps, launch=None):
     ctx = gpu.Context(storage=storage, scheme=scheme)
     try:
         d = ctx.domain(geo.xyz, geo.iolets, ordering="rows")
+        if launch:
+            ctx.set_launch(*launch)
         ctx.step(steps)
         return d.state(), d.iolet_stats(), d.boundary_values()
     finally:
         ctx.close()
 
 
-@pytest.mark.parametrize("storage,scheme", [("f32", "aa"), ("f16", "ab"), ("bf16", "aa")])
-def test_mixed_plan_bit_identical_to_alone(gpu, storage, scheme):
+@pytest.mark.parametrize("storage,scheme,launch", [
+    ("f32", "aa", None), ("f16", "ab", None), ("bf16", "aa", None),
+    # run-encoded variants: the large domain in its own launch, the small ones in the
+    # tile-table kernel; the reference is each domain alone with the table form
+    ("f32", "ab", (128, 2, 13)), ("f32", "aa", (256, 1, 8)), ("f16", "aa", (128, 2, 10)),
+    ("f16", "ab", (256, 2, 8))])
+def test_mixed_plan_bit_identical_to_alone(gpu, storage, scheme, launch):
     geos = _geoms()
     steps = 37
     ref = [_alone(gpu, g, storage, scheme, steps) for g in geos]
     ctx = gpu.Context(storage=storage, scheme=scheme)
     try:
         ds = [ctx.domain(g.xyz, g.iolets, ordering="rows") for g in geos]
+        assert all(d.info()["n_runs"] > 0 for d in ds)
+        if launch:
+            ctx.set_launch(*launch)
         ctx.step(steps)
         for d, r in zip(ds, ref):
             got = d.state(), d.iolet_stats(), d.boundary_values()
