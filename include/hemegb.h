@@ -126,11 +126,13 @@ typedef struct {
                                      18 table rows; a launch over a domain without
                                      one runs 3, 5, 6, 7; same shapes as 3, 5, 6, 7;
                                  12 = 8 for AA (1 or 2 sites per thread) with the odd
-                                     step's 18 entries held across the collision
-                                     instead of reread;
+                                     step's 18 entries stashed in shared memory
+                                     across the collision instead of decoded twice;
                                  13 = 8 (2 or 4 sites per thread) with every site's
                                      link word loaded, and its run row prefetched,
-                                     before the first site's gathers */
+                                     before the first site's gathers;
+                                 14 = 10 with the stash of 12 (AA, 2 sites per
+                                     thread) */
     void *stream;             /* cudaStream_t to order work on; NULL = a stream the context creates */
     hg_alloc_fn alloc;        /* NULL = cudaMalloc */
     hg_free_fn free;          /* NULL = cudaFree */

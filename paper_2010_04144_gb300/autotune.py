@@ -28,12 +28,13 @@ DEFAULT_CANDIDATES = (
     (128, 2, 6), (256, 2, 6), (256, 2, 7), (512, 2, 7),  # variants 6, 7: AA on site pairs
     # 8..11: 3, 5, 6, 7 reading the run-encoded neighbour table
     (256, 1, 8), (128, 2, 8), (256, 2, 8), (128, 2, 9), (256, 2, 9), (128, 2, 10), (256, 2, 10), (256, 2, 11),
-    (256, 1, 12), (128, 1, 12), (128, 2, 12),  # 12: AA, run-encoded, odd-step entries held
+    (256, 1, 12), (128, 1, 12), (128, 2, 12),  # 12: AA, run-encoded, odd-step entries stashed
     (128, 2, 13), (256, 2, 13), (128, 4, 13),  # 13: run-encoded, link words hoisted
+    (128, 2, 14), (256, 2, 14),  # 14: AA pairs even, run-encoded odd with the stash
 )
 # Variant 4 (staged AA odd-step stores) is measured slower than variant 1 on
 # every workload tried; it stays available through Context.set_launch.
-AA_ONLY = (2, 4, 6, 7, 10, 11, 12)
+AA_ONLY = (2, 4, 6, 7, 10, 11, 12, 14)
 AB_16BIT_ONLY = (5, 9)
 
 

@@ -483,13 +483,19 @@ __device__ __forceinline__ void site_aa_even(const DomDev &D, typename St<S>::T 
 // ---- AA odd step: gather F_{t-1} (swapped) from x - c_i, scatter F_t to x + c_i ----
 // Entry OPP(I) of the site's row is the site at x + c_I; its virtual index for
 // a non-fluid link turns the scatter into the raw write to the own slot OPP(I).
-template <int S, bool HINT, bool RUNS, bool KEEP, typename NB>
+template <int S, bool HINT, bool RUNS, bool STASH, typename NB>
 __device__ __forceinline__ void site_aa_odd_with(const DomDev &D, typename St<S>::T *buf, int64_t s,
-                                                 const NB &tab) {
+                                                 const NB &tab, int32_t *stash = nullptr) {
     using Tr = St<S>;
     const int64_t np = D.np;
     int32_t nb[18];
     tab.all(nb);
+    if constexpr (STASH) {  // 19 words per thread (odd stride: no bank conflicts), 18 used
+        stash += 19 * threadIdx.x;
+#pragma unroll
+        for (int i = 0; i < 18; ++i) stash[i] = nb[i];
+        asm volatile("" ::: "memory");  // the stash stores stay ahead of the gathers
+    }
     float g[19];
     g[0] = Tr::template ld<0>(load_rw<HINT>(buf + s));
     unroll<1, 19>([&](auto ic) {
@@ -500,11 +506,21 @@ __device__ __forceinline__ void site_aa_odd_with(const DomDev &D, typename St<S>
     const float4 m = collide_s<S>(g, D.omega);
     typename St<S>::T *wb = opaque(buf);
     // the scatter addresses are the gather addresses (entry OPP(I) of the site at x +
-    // c_I): KEEP holds the 18 entries across the collision, otherwise they are reread
-    // (cache hits), which frees 18 registers
+    // c_I): STASH takes the 18 entries back from shared memory, otherwise they are
+    // decoded again (cache hits); either frees 18 registers across the collision
     wb[s] = Tr::template st<0>(g[0]);
-    if constexpr (RUNS || KEEP) {
-        if constexpr (!KEEP) tab.reload().all(nb);
+    if constexpr (RUNS || STASH) {
+        if constexpr (STASH) {
+            // the stash address is known only once the collision has produced m: the
+            // reads cannot move above it, so the entries are not live across it
+            int32_t *st2;
+            asm volatile("{\n\t.reg .f32 t;\n\tmov.f32 t, %2;\n\tmov.b64 %0, %1;\n\t}"
+                         : "=l"(st2) : "l"(stash), "f"(m.x) : "memory");
+#pragma unroll
+            for (int i = 0; i < 18; ++i) nb[i] = st2[i];
+        } else {
+            tab.reload().all(nb);
+        }
         unroll<1, 19>([&](auto ic) {
             constexpr int I = decltype(ic)::v;
             wb[(int64_t)I * np + nb[OPP(I) - 1]] = Tr::template st<I>(g[I]);
@@ -519,9 +535,10 @@ __device__ __forceinline__ void site_aa_odd_with(const DomDev &D, typename St<S>
     if (slot >= 0) D.bnd[slot] = m;
 }
 
-template <int S, bool HINT = false, bool RUNS = false, bool KEEP = false>
-__device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s) {
-    site_aa_odd_with<S, HINT, RUNS, KEEP>(D, buf, s, NbOf<kAA, HINT, RUNS>(D, s));
+template <int S, bool HINT = false, bool RUNS = false, bool STASH = false>
+__device__ __forceinline__ void site_aa_odd(const DomDev &D, typename St<S>::T *buf, int64_t s,
+                                            int32_t *stash = nullptr) {
+    site_aa_odd_with<S, HINT, RUNS, STASH>(D, buf, s, NbOf<kAA, HINT, RUNS>(D, s), stash);
 }
 
 // ==== async-staged variant (V = 1) ==========================================
@@ -981,7 +998,7 @@ __device__ __forceinline__ void tile_aa_even_tma(const DomDev &D, const TileDev 
 // AA step kind), 2 = read from the domain's step counter per block (A/B, and AA
 // batches whose domains are at different parities).
 // One tile of one domain, after the prologue has located it.
-template <int S, int SCHEME, int SPT, int PAR, int V, bool RUNS, bool KEEP = false, bool HOIST = false>
+template <int S, int SCHEME, int SPT, int PAR, int V, bool RUNS, bool STASH = false, bool HOIST = false>
 __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const TileDev &tl, bool odd,
                                                          uint32_t *stage) {
     using T = typename St<S>::T;
@@ -1010,7 +1027,7 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
 #pragma unroll
             for (int j = 0; j < 2; ++j) {
                 const int r = j * blockDim.x + threadIdx.x;
-                if (r < tl.count) site_aa_odd<S, HINT, true>(D, buf, tl.start + r);
+                if (r < tl.count) site_aa_odd<S, HINT, true, STASH>(D, buf, tl.start + r, (int32_t *)stage);
             }
             return;
         }
@@ -1078,7 +1095,7 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
             } else {
                 T *buf = (T *)D.f[0];
                 if (live) {
-                    if (odd) site_aa_odd<S, HINT, RUNS, KEEP>(D, buf, s);
+                    if (odd) site_aa_odd<S, HINT, RUNS, STASH>(D, buf, s, (int32_t *)stage);
                     else site_aa_even<S, HINT>(D, buf, s);
                 }
             }
@@ -1089,11 +1106,12 @@ __device__ __forceinline__ void stream_collide_tile_impl(const DomDev &D, const 
 // Variants 8..11 are 3, 5, 6, 7 reading the run-encoded neighbour table.  The host
 // launches them only on domains that have one (the others get 3, 5, 6, 7); a domain
 // without one here is reported through the error word (code 2) and left untouched.
-// Variant 12 is 8 for the AA scheme with the odd step's 18 entries held across the
-// collision instead of reread; 13 is 8 with every site's link word loaded (and its
-// run row prefetched) before the first site's gathers.
+// Variant 12 is 8 for the AA scheme with the odd step's 18 entries stashed in shared
+// memory across the collision instead of decoded twice; 14 is 10 with the same stash;
+// 13 is 8 with every site's link word loaded (and its run row prefetched) before the
+// first site's gathers.
 template <int V> constexpr int table_variant() {
-    return V == 8 || V == 12 || V == 13 ? 3 : V == 9 ? 5 : V == 10 ? 6 : V == 11 ? 7 : V;
+    return V == 8 || V == 12 || V == 13 ? 3 : V == 9 ? 5 : V == 10 || V == 14 ? 6 : V == 11 ? 7 : V;
 }
 
 template <int S, int SCHEME, int SPT, int PAR, int V>
@@ -1104,7 +1122,7 @@ __device__ __forceinline__ void stream_collide_tile(const DomDev &D, const TileD
             if (threadIdx.x == 0) atomicExch(D.err, 2);
             return;
         }
-        stream_collide_tile_impl<S, SCHEME, SPT, PAR, table_variant<V>(), true, V == 12, V == 13>(D, tl, odd,
+        stream_collide_tile_impl<S, SCHEME, SPT, PAR, table_variant<V>(), true, V == 12 || V == 14, V == 13>(D, tl, odd,
                                                                                                  stage);
     } else {
         stream_collide_tile_impl<S, SCHEME, SPT, PAR, V, false>(D, tl, odd, stage);
@@ -1165,6 +1183,7 @@ cudaError_t launch_sc_one(const CollideCfg &cfg, const DomDev *doms, const TileD
     // V1/V4: cp.async stage of 4-byte words (V4 reuses it for the odd step's outputs);
     // V2 also holds the even step's 19 rows + mbarrier
     size_t smem = (V == 1 || V == 2 || V == 4) ? (size_t)SPT * 19 * cfg.block * 4 : 0;
+    if (V == 12 || V == 14) smem = (size_t)19 * cfg.block * 4;  // the AA odd step's entry stash
     if (V == 2) smem += 16;
     cudaLaunchConfig_t lc = {};
     lc.gridDim = dim3((unsigned)n_tiles);
@@ -1233,6 +1252,11 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
             case 4: return launch_sc_one<S, SCHEME, PAR, 8, 4>(cfg, doms, tiles, n_tiles, off, one, st);
             default: return cudaErrorInvalidValue;
         }
+    }
+    if (cfg.variant == 14) {
+        if constexpr (SCHEME != kAA) return cudaErrorInvalidValue;
+        else if (cfg.spt != 2) return cudaErrorInvalidValue;
+        else return launch_sc_one<S, SCHEME, PAR, 14, 2>(cfg, doms, tiles, n_tiles, off, one, st);
     }
     if (cfg.variant == 13) {
         switch (cfg.spt) {

@@ -607,6 +607,7 @@ bool variant_ok(int storage, int scheme, int spt, int variant) {
         case 10: case 11: return spt == 2 && scheme == HG_SCHEME_AA;
         case 12: return spt != 4 && scheme == HG_SCHEME_AA;
         case 13: return spt != 1;
+        case 14: return spt == 2 && scheme == HG_SCHEME_AA;
         default: return false;
     }
 }
@@ -1575,7 +1576,10 @@ cudaError_t enqueue_halo(hg_ctx *ctx, Plan *p, int off) {
 CollideCfg collide_cfg(hg_ctx *ctx, bool runs) {
     CollideCfg cfg{ctx->storage, ctx->scheme, ctx->block, ctx->spt, ctx->variant};
     if (cfg.variant >= 8 && !runs)
-        cfg.variant = cfg.variant == 8 || cfg.variant >= 12 ? 3 : cfg.variant == 9 ? 5 : cfg.variant - 4;
+        cfg.variant = cfg.variant == 8 || cfg.variant == 12 || cfg.variant == 13 ? 3
+                      : cfg.variant == 9                                      ? 5
+                      : cfg.variant == 10 || cfg.variant == 14                ? 6
+                                                                              : 7;
     return cfg;
 }
 
@@ -1762,7 +1766,8 @@ int hg_ctx_set_launch(hg_ctx *ctx, int32_t block, int32_t spt, int32_t variant) 
                                      "(2: AA only), 4 with 1 site per thread (AA only), 5 with 2 sites "
                                      "per thread (A/B, 16-bit storage only), 6 or 7 with 2 sites per "
                                      "thread (AA only), 8..11 with the shapes of 3, 5, 6, 7, 12 with 1 or "
-                                     "2 sites per thread (AA only), or 13 with 2 or 4 sites per thread");
+                                     "2 sites per thread (AA only), 13 with 2 or 4 sites per thread, or 14 "
+                                     "with 2 sites per thread (AA only)");
     if (block == ctx->block && spt == ctx->spt && variant == ctx->variant) return HG_OK;
     CU(ctx, cudaSetDevice(ctx->device));
     CU(ctx, cudaStreamSynchronize(ctx->stream));

@@ -44,7 +44,7 @@ class _Ctx:
 
 @pytest.mark.parametrize("storage,scheme,allowed", [
     (0, 0, {0, 1, 3, 8, 13}), (1, 0, {0, 1, 3, 5, 8, 9, 13}), (2, 0, {0, 1, 3, 5, 8, 9, 13}),
-    (0, 1, {0, 1, 2, 3, 6, 7, 8, 10, 11, 12, 13}), (1, 1, {0, 1, 2, 3, 6, 7, 8, 10, 11, 12, 13}),
+    (0, 1, {0, 1, 2, 3, 6, 7, 8, 10, 11, 12, 13, 14}), (1, 1, {0, 1, 2, 3, 6, 7, 8, 10, 11, 12, 13, 14}),
 ])
 def test_candidates_per_form(storage, scheme, allowed):
     ctx = _Ctx(storage, scheme, cost=lambda L: 1.0 + L[0] / 1e4 + L[1] / 1e3 + L[2] / 1e2)

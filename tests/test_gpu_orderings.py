@@ -44,12 +44,14 @@ def test_orderings_bit_identical(gpu, storage, scheme, launch):
     ("f32", "ab", [((256, 2, 3), (256, 2, 8)), ((128, 1, 3), (128, 1, 8)), ((128, 2, 3), (128, 2, 13))]),
     ("f16", "ab", [((256, 2, 5), (256, 2, 9)), ((128, 2, 5), (128, 4, 8)), ((64, 4, 3), (64, 4, 13))]),
     ("f32", "aa", [((128, 2, 6), (128, 2, 10)), ((256, 2, 7), (256, 2, 11)), ((256, 1, 3), (256, 1, 8)),
-                   ((256, 1, 3), (256, 1, 12)), ((128, 2, 3), (128, 2, 12)), ((128, 2, 3), (128, 2, 13))]),
-    ("f16", "aa", [((128, 2, 6), (128, 2, 10)), ((64, 2, 7), (64, 2, 11)), ((256, 1, 3), (256, 1, 12))]),
+                   ((256, 1, 3), (256, 1, 12)), ((128, 2, 3), (128, 2, 12)), ((128, 2, 3), (128, 2, 13)),
+                   ((256, 2, 6), (256, 2, 14))]),
+    ("f16", "aa", [((128, 2, 6), (128, 2, 10)), ((64, 2, 7), (64, 2, 11)), ((256, 1, 3), (256, 1, 12)),
+                   ((128, 2, 6), (128, 2, 14))]),
     ("bf16", "aa", [((256, 2, 6), (256, 2, 10))])])
 def test_run_encoded_table_bit_identical(gpu, storage, scheme, pairs):
-    """Variants 8..13 read the run-encoded neighbour table, which a rows- or bricks-ordered
-    domain has: same bits as their table-reading counterparts (3, 5, 6, 7, 3, 3), odd and even
+    """Variants 8..14 read the run-encoded neighbour table, which a rows- or bricks-ordered
+    domain has: same bits as their table-reading counterparts (3, 5, 6, 7, 3, 3, 6), odd and even
     step counts, through graph replays and direct steps."""
     for o in ("rows", "bricks"):
         geo = S.tree(S.TreeSpec(depth=4, root_radius=6, seed=7), inlet_speed=0.05, period=200.0)

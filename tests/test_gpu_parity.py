@@ -263,7 +263,7 @@ LAUNCHES = [("ab", 256, 1, 0), ("ab", 128, 2, 0), ("ab", 256, 1, 1), ("ab", 128,
             # 8..12: 3, 5, 6, 7, 3 on the run-encoded table (here Morton order: the table path;
             # the run path on rows-ordered domains is checked in test_gpu_orderings.py)
             ("ab", 256, 2, 8), ("aa", 128, 1, 8), ("ab", 128, 2, 9), ("aa", 256, 2, 10), ("aa", 128, 2, 11),
-            ("aa", 256, 1, 12), ("ab", 128, 2, 13), ("aa", 64, 4, 13)]
+            ("aa", 256, 1, 12), ("ab", 128, 2, 13), ("aa", 64, 4, 13), ("aa", 128, 2, 14)]
 
 
 @pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
