@@ -38,6 +38,15 @@ AA_ONLY = (2, 4, 6, 7, 10, 11, 12, 14)
 AB_16BIT_ONLY = (5, 9)
 
 
+def allowed(ctx, candidates):
+    """The candidates the context's storage and scheme support."""
+    if ctx.scheme != 1:
+        candidates = [c for c in candidates if c[2] not in AA_ONLY]
+    if ctx.scheme != 0 or ctx.storage == 0:
+        candidates = [c for c in candidates if c[2] not in AB_16BIT_ONLY]
+    return candidates
+
+
 def _cache_path():
     return os.environ.get("HEMEGB_TUNE_CACHE",
                           os.path.join(os.path.expanduser("~"), ".cache", "hemegb", "tune.json"))
@@ -81,10 +90,7 @@ def autotune(ctx, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2, use_cache=T
     """Pick the fastest launch shape for `ctx`; returns (best, {candidate: ms per launch})."""
     if not ctx.domains:
         raise ValueError("autotune needs at least one domain in the context")
-    if ctx.scheme != 1:
-        candidates = [c for c in candidates if c[2] not in AA_ONLY]
-    if ctx.scheme != 0 or ctx.storage == 0:
-        candidates = [c for c in candidates if c[2] not in AB_16BIT_ONLY]
+    candidates = allowed(ctx, candidates)
     key = _key(ctx, candidates)
     if use_cache:
         hit = _load().get(key)
@@ -136,10 +142,7 @@ def autotune_split(ctx, split, candidates=DEFAULT_CANDIDATES, steps=12, warmup=2
     computes the same bits.  Returns (best, {candidate: ms per step})."""
     import torch
 
-    if ctx.scheme != 1:
-        candidates = [c for c in candidates if c[2] not in AA_ONLY]
-    if ctx.scheme != 0 or ctx.storage == 0:
-        candidates = [c for c in candidates if c[2] not in AB_16BIT_ONLY]
+    candidates = allowed(ctx, candidates)
     timing = {}
     for cand in candidates:
         ctx.set_launch(*cand)

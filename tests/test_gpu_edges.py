@@ -21,7 +21,7 @@ from test_gpu_parity import TAU, TOL, field_errors
 pytestmark = pytest.mark.gpu
 
 STEPS = 40
-LAUNCHES = {"ab": [(64, 1, 0), (128, 2, 3), (64, 2, 1), (128, 2, 8), (128, 2, 13)],
+LAUNCHES = {"ab": [(64, 1, 0), (128, 2, 3), (64, 2, 1), (128, 2, 8), (128, 2, 13), (64, 4, 13)],
             "aa": [(64, 1, 0), (128, 2, 6), (64, 2, 2), (256, 1, 8), (128, 2, 10), (128, 2, 14)]}
 
 

@@ -245,6 +245,10 @@ def test_errors_are_reported(gpu):
             ctx.couple(a, b, [(0, 1, 1.0)])  # destination is a pressure iolet
         with pytest.raises(gpu.HgError):
             ctx.couple(a, a, [(0, 0, 1.0)])  # source and destination must differ
+        for bad in ((128, 1, 13), (128, 4, 5), (128, 2, 14), (128, 2, 15), (96, 3, 0), (48, 1, 0)):
+            with pytest.raises(gpu.HgError) as e:   # shape outside the variant's rules (A/B context)
+                ctx.set_launch(*bad)
+            assert e.value.code == gpu.HG_ERR_ARG, bad
         ctx.step(3)
         assert a.step == 3 and b.step == 3
         ctx.step_domains([a], 2)
