@@ -18,6 +18,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <chrono>
 #include <atomic>
 #include <cmath>
 #include <cstdarg>
@@ -45,6 +46,21 @@ const int kC[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},   {0, -1,
 inline double wgt(int i) { return i == 0 ? 1.0 / 3.0 : (i <= 6 ? 1.0 / 18.0 : 1.0 / 36.0); }
 
 // ---------------------------------------------------------------- threads
+// Phase timing of a build, printed to stderr when HEMEGB_TRACE_BUILD is set.
+struct PhaseTrace {
+    bool on;
+    std::chrono::steady_clock::time_point t;
+    int64_t n;
+    explicit PhaseTrace(int64_t n_) : on(getenv("HEMEGB_TRACE_BUILD") != nullptr), t(std::chrono::steady_clock::now()), n(n_) {}
+    void mark(const char *phase) {
+        if (!on) return;
+        const auto t2 = std::chrono::steady_clock::now();
+        fprintf(stderr, "hemegb build n=%lld %s %.3f s\n", (long long)n, phase,
+                std::chrono::duration<double>(t2 - t).count());
+        t = t2;
+    }
+};
+
 int n_threads() {
     unsigned h = std::thread::hardware_concurrency();
     if (h == 0) h = 4;
@@ -205,35 +221,56 @@ struct BlockIndex {
 void sort_keys(std::vector<uint64_t> &key, std::vector<int64_t> &idx) {
     const int64_t n = (int64_t)key.size();
     if (n <= 1) return;
+    // bucket by the top 12 bits of the key range (counting sort, in parallel over
+    // contiguous site chunks), then sort each bucket; keys are distinct, so the
+    // result does not depend on the thread count
+    const int T = (int)std::max<int64_t>(1, std::min<int64_t>(n_threads(), n / 65536 + 1));
+    const int64_t per = (n + T - 1) / T;
+    std::vector<uint64_t> mxs(T, 0);
+    parallel_for(T, [&](int64_t lo, int64_t hi) {
+        for (int64_t t = lo; t < hi; ++t)
+            for (int64_t s = t * per; s < std::min(n, (t + 1) * per); ++s) mxs[t] = std::max(mxs[t], key[s]);
+    }, 1);
     uint64_t mx = 0;
-    for (int64_t s = 0; s < n; ++s) mx = std::max(mx, key[s]);
+    for (uint64_t m : mxs) mx = std::max(mx, m);
     int bl = 64 - (mx ? __builtin_clzll(mx) : 63);
     const int nbits = 12;
     const int shift = std::max(0, bl - nbits);
     const int64_t nbk = (int64_t)1 << nbits;
+    std::vector<int64_t> hist((size_t)T * nbk, 0);  // [chunk][bucket]
+    parallel_for(T, [&](int64_t lo, int64_t hi) {
+        for (int64_t t = lo; t < hi; ++t)
+            for (int64_t s = t * per; s < std::min(n, (t + 1) * per); ++s) hist[(size_t)t * nbk + (key[s] >> shift)]++;
+    }, 1);
     std::vector<int64_t> cnt(nbk + 1, 0);
-    for (int64_t s = 0; s < n; ++s) cnt[(key[s] >> shift) + 1]++;
-    for (int64_t b = 0; b < nbk; ++b) cnt[b + 1] += cnt[b];
-    std::vector<std::pair<uint64_t, int64_t>> tmp(n);
     {
-        std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
-        for (int64_t s = 0; s < n; ++s) tmp[pos[key[s] >> shift]++] = {key[s], idx[s]};
-    }
-    std::atomic<int64_t> next{0};
-    std::vector<std::thread> th;
-    for (int t = 0; t < n_threads(); ++t)
-        th.emplace_back([&] {
-            for (;;) {
-                int64_t b = next.fetch_add(1);
-                if (b >= nbk) break;
-                std::sort(tmp.begin() + cnt[b], tmp.begin() + cnt[b + 1]);
+        int64_t acc = 0;
+        for (int64_t b = 0; b < nbk; ++b) {
+            cnt[b] = acc;
+            for (int t = 0; t < T; ++t) {
+                const int64_t h = hist[(size_t)t * nbk + b];
+                hist[(size_t)t * nbk + b] = acc;  // this chunk's first position in bucket b
+                acc += h;
             }
-        });
-    for (auto &x : th) x.join();
-    for (int64_t s = 0; s < n; ++s) {
-        key[s] = tmp[s].first;
-        idx[s] = tmp[s].second;
+        }
+        cnt[nbk] = acc;
     }
+    std::vector<std::pair<uint64_t, int64_t>> tmp(n);
+    parallel_for(T, [&](int64_t lo, int64_t hi) {
+        for (int64_t t = lo; t < hi; ++t) {
+            int64_t *pos = hist.data() + (size_t)t * nbk;
+            for (int64_t s = t * per; s < std::min(n, (t + 1) * per); ++s) tmp[pos[key[s] >> shift]++] = {key[s], idx[s]};
+        }
+    }, 1);
+    parallel_for(nbk, [&](int64_t lo, int64_t hi) {
+        for (int64_t b = lo; b < hi; ++b) std::sort(tmp.begin() + cnt[b], tmp.begin() + cnt[b + 1]);
+    }, 1);
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t s = lo; s < hi; ++s) {
+            key[s] = tmp[s].first;
+            idx[s] = tmp[s].second;
+        }
+    });
 }
 
 // Device layout of a domain's sites (the canonical order is always Morton):
@@ -623,7 +660,8 @@ int ensure_scratch(hg_ctx *ctx, size_t bytes) {
 // entries in [0, n_ref), every other entry the virtual index q + dd_i np with
 // dd_i = vdir * (opp(i) - i)).  A run is a maximal range of consecutive sites in
 // which each direction's fluid links share one offset (entry - site); non-fluid
-// links do not break a run, a per-site bit marks them instead.  rdelta holds
+// links do not break a run, a per-site bit marks them instead; every 2^20-site span
+// starts a run (the spans are encoded in parallel).  rdelta holds
 // kRunStride entries per run (the 18 offsets, then zeros), so a run's row is one
 // aligned 80-byte block the kernels read with 16-byte loads.  Rows ordering
 // makes a run cover most of an x-row of a vessel.  Returns false (nothing built)
@@ -631,41 +669,79 @@ int ensure_scratch(hg_ctx *ctx, size_t bytes) {
 // traffic (runs shorter than 4.5 sites on average: more than 16 bytes per site).
 bool build_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t np, int vdir, std::vector<uint32_t> &lword,
                 std::vector<int32_t> &run0, std::vector<int32_t> &rdelta) {
+    if (n <= 0) return false;
     lword.assign((size_t)np, 0u);
     run0.assign((size_t)((np + 1023) / 1024), 0);
     rdelta.clear();
-    int32_t cur[18] = {0};
-    bool have[18] = {false};
-    int64_t run = -1;
-    for (int64_t q = 0; q < n; ++q) {
-        uint32_t miss = 0;
-        bool brk = run < 0;
-        for (int i = 0; i < 18; ++i) {
-            const int32_t v = nbr[(size_t)i * np + q];
-            if (v >= 0 && v < n_ref) {
-                if (have[i] && cur[i] != v - (int32_t)q) brk = true;
-            } else {
-                const int dir = i + 1, opp = (dir & 1) ? dir + 1 : dir - 1;
-                if ((int64_t)v != q + (int64_t)vdir * (opp - dir) * np) return false;
-                miss |= 1u << i;
+    // Spans of 2^20 sites (whole 1024-site chunks) are encoded in parallel, each starting
+    // a run of its own; run0 and the rows then move by the runs of the spans before.
+    constexpr int64_t kSpan = (int64_t)1 << 20;
+    const int64_t n_span = (n + kSpan - 1) / kSpan;
+    std::vector<std::vector<int32_t>> rows(n_span);
+    std::vector<int64_t> runs(n_span, 0);
+    std::atomic<bool> bad{false};             // an entry of the wrong form, or too many runs
+    std::atomic<int64_t> counted{0};          // runs so far, all spans: stop once it cannot pay
+    parallel_for(n_span, [&](int64_t lo, int64_t hi) {
+        for (int64_t sp = lo; sp < hi && !bad; ++sp) {
+            const int64_t a = sp * kSpan, b = std::min(n, a + kSpan);
+            std::vector<int32_t> &rd = rows[sp];
+            int32_t cur[18] = {0};
+            bool have[18] = {false};
+            int64_t run = -1;  // local to the span
+            for (int64_t q = a; q < b && !bad; ++q) {
+                uint32_t miss = 0;
+                bool brk = run < 0;
+                for (int i = 0; i < 18; ++i) {
+                    const int32_t v = nbr[(size_t)i * np + q];
+                    if (v >= 0 && v < n_ref) {
+                        if (have[i] && cur[i] != v - (int32_t)q) brk = true;
+                    } else {
+                        const int dir = i + 1, opp = (dir & 1) ? dir + 1 : dir - 1;
+                        if ((int64_t)v != q + (int64_t)vdir * (opp - dir) * np) {
+                            bad = true;
+                            return;
+                        }
+                        miss |= 1u << i;
+                    }
+                }
+                if (brk) {
+                    ++run;
+                    if ((counted.fetch_add(1) + 1) * 72 > 16 * n) {
+                        bad = true;
+                        return;
+                    }
+                    rd.resize((size_t)(run + 1) * kRunStride, 0);
+                    for (int i = 0; i < 18; ++i) have[i] = false;
+                }
+                if ((q & 1023) == 0) run0[(size_t)(q >> 10)] = (int32_t)run;  // local until shifted
+                for (int i = 0; i < 18; ++i)
+                    if (!((miss >> i) & 1u) && !have[i]) {
+                        have[i] = true;
+                        cur[i] = nbr[(size_t)i * np + q] - (int32_t)q;
+                        rd[(size_t)run * kRunStride + i] = cur[i];
+                    }
+                lword[(size_t)q] = miss | ((uint32_t)(run - run0[(size_t)(q >> 10)]) << 18);
             }
+            runs[sp] = run + 1;
         }
-        if (brk) {
-            ++run;
-            if ((run + 1) * 72 > 16 * n) return false;
-            rdelta.resize((size_t)(run + 1) * kRunStride, 0);
-            for (int i = 0; i < 18; ++i) have[i] = false;
-        }
-        if ((q & 1023) == 0) run0[(size_t)(q >> 10)] = (int32_t)run;
-        for (int i = 0; i < 18; ++i)
-            if (!((miss >> i) & 1u) && !have[i]) {
-                have[i] = true;
-                cur[i] = nbr[(size_t)i * np + q] - (int32_t)q;
-                rdelta[(size_t)run * kRunStride + i] = cur[i];
-            }
-        lword[(size_t)q] = miss | ((uint32_t)(run - run0[(size_t)(q >> 10)]) << 18);
+    }, 1);
+    if (bad) return false;
+    int64_t total = 0;
+    std::vector<int64_t> first(n_span, 0);
+    for (int64_t sp = 0; sp < n_span; ++sp) {
+        first[sp] = total;
+        total += runs[sp];
     }
-    return n > 0;
+    if (total * 72 > 16 * n || total > INT32_MAX) return false;
+    rdelta.resize((size_t)total * kRunStride);
+    parallel_for(n_span, [&](int64_t lo, int64_t hi) {
+        for (int64_t sp = lo; sp < hi; ++sp) {
+            std::copy(rows[sp].begin(), rows[sp].end(), rdelta.begin() + first[sp] * kRunStride);
+            const int64_t c0 = sp * (kSpan >> 10), c1 = std::min<int64_t>((int64_t)run0.size(), c0 + (kSpan >> 10));
+            for (int64_t c = c0; c < c1 && c * 1024 < n; ++c) run0[(size_t)c] += (int32_t)first[sp];
+        }
+    }, 1);
+    return true;
 }
 
 // Canonical site order (ascending 3-D Morton key) and neighbour table in
@@ -885,6 +961,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     d->ordering = ordering;
     d->io.assign(iolets, iolets + nio);
 
+    PhaseTrace trace(n);
     // --- canonical order and neighbour table (canonical codes)
     const int64_t np = d->np;
     std::vector<int32_t> nbr;
@@ -894,6 +971,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         if (brc != HG_OK) return fail(ctx, brc, "%s", why.c_str());
     }
 
+    trace.mark("canonical order and table");
     // --- device ordering: a permutation of the canonical order (none for Morton).
     // The table's columns move to their device positions and fluid entries are
     // renumbered; every other table is built in device order below, except the
@@ -921,8 +999,8 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         }
     }
     auto canon = [&](int64_t q) -> int64_t { return canon_of.empty() ? q : canon_of[q]; };
-    auto devix = [&](int64_t c) -> int64_t { return dev_of.empty() ? c : dev_of[c]; };
 
+    trace.mark("device ordering");
     // --- iolet adjacency: slots numbered in device order (the kernels find a
     // site's slot as the rank of its flag), per-iolet CSR lists in canonical order
     std::vector<int32_t> slot_of(n, -1);
@@ -941,32 +1019,48 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         }
         return n_seen;
     };
-    for (int64_t q = 0; q < n; ++q) {
-        int seen[18];
-        const int ns = distinct_iolets(q, seen);
-        for (int t = 0; t < ns; ++t) per_io[seen[t] + 1]++;
-        if (ns) slot_of[q] = (int32_t)n_adj++;
-    }
+    // which sites have a link into an opening (parallel), then their slots in device order
+    std::vector<uint8_t> touches((size_t)n, 0);
+    if (nio > 0)
+        parallel_for(n, [&](int64_t lo, int64_t hi) {
+            for (int64_t q = lo; q < hi; ++q)
+                for (int i = 0; i < 18; ++i)
+                    if (nbr[(size_t)i * np + q] < -1) {
+                        touches[(size_t)q] = 1;
+                        break;
+                    }
+        });
+    std::vector<int64_t> flagged;  // device positions of those sites, ascending
+    for (int64_t q = 0; q < n; ++q)
+        if (touches[(size_t)q]) {
+            int seen[18];
+            const int ns = distinct_iolets(q, seen);
+            for (int t = 0; t < ns; ++t) per_io[seen[t] + 1]++;
+            slot_of[q] = (int32_t)n_adj++;
+            flagged.push_back(q);
+        }
+    std::vector<uint8_t>().swap(touches);
     d->n_adj = n_adj;
     for (int k = 0; k < nio; ++k) per_io[k + 1] += per_io[k];
     d->io_ptr.assign(per_io.begin(), per_io.end());
     std::vector<int32_t> slots(std::max<int64_t>(1, per_io[nio]));
     {
+        std::vector<std::pair<int64_t, int64_t>> by_canon;  // (canonical index, device position)
+        by_canon.reserve(flagged.size());
+        for (int64_t q : flagged) by_canon.push_back({canon(q), q});
+        std::sort(by_canon.begin(), by_canon.end());
         std::vector<int64_t> fill(per_io.begin(), per_io.end() - 1);
-        for (int64_t c = 0; c < n; ++c) {
-            const int64_t q = devix(c);
-            if (slot_of[q] < 0) continue;
+        for (const auto &cq : by_canon) {
             int seen[18];
-            const int ns = distinct_iolets(q, seen);
-            for (int t = 0; t < ns; ++t) slots[fill[seen[t]]++] = slot_of[q];
+            const int ns = distinct_iolets(cq.second, seen);
+            for (int t = 0; t < ns; ++t) slots[fill[seen[t]]++] = slot_of[cq.second];
         }
     }
     std::vector<float> coef((size_t)std::max<int64_t>(1, n_adj) * 18, 0.0f);
     std::vector<uint32_t> mask((size_t)(np / 32), 0u);
     std::vector<int32_t> codes((size_t)std::max<int64_t>(1, n_adj) * 18, -1);
-    for (int64_t q = 0; q < n; ++q) {
+    for (int64_t q : flagged) {
         const int32_t sl = slot_of[q];
-        if (sl < 0) continue;
         mask[q >> 5] |= 1u << (q & 31);
         const int64_t c = canon(q);
         for (int i = 1; i < 19; ++i) {  // canonical codes: fluid links hold the canonical source
@@ -988,6 +1082,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
             acc += __builtin_popcount(mask[w]);
         }
     }
+    trace.mark("iolet slots");
     // virtual indices for every non-fluid link (walls and iolet links alike)
     const bool aa = ctx->scheme == HG_SCHEME_AA;
     parallel_for(n, [&](int64_t lo, int64_t hi) {
@@ -1003,6 +1098,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     std::vector<int32_t> slot_site((size_t)std::max<int64_t>(1, n_adj), 0);
     for (int64_t q = 0; q < n; ++q)
         if (slot_of[q] >= 0) slot_site[slot_of[q]] = (int32_t)q;
+    trace.mark("virtual indices");
     std::vector<uint32_t> lword;
     std::vector<int32_t> run0, rdelta;
     if (build_runs(nbr.data(), n, n, np, aa ? -1 : 1, lword, run0, rdelta))
@@ -1013,6 +1109,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     d->canon_of_host = canon_of;
     d->dev_of_host = dev_of;
 
+    trace.mark("run encoding");
     // --- device buffers
     hg_ctx *c = ctx;
     const size_t eb = elem_bytes(ctx->storage);
@@ -1058,6 +1155,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         bcv[k] = (float)(iolets[k].value * pulse(iolets[k].pulse, 1.0, iolets[k].period));
         kinds[k] = (int8_t)iolets[k].kind;
     }
+    trace.mark("allocation");
     // uploads run on a stream of this build, so a build on another thread
     // neither waits for nor races with the context's stream
     cudaStream_t up = nullptr;
@@ -1101,6 +1199,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         cleanup();
         return fail(ctx, HG_ERR_CUDA, "upload failed: %s", cudaGetErrorString(e));
     }
+    trace.mark("upload");
     {
         std::lock_guard<std::mutex> lk(ctx->mu);
         ctx->doms[slot_idx] = d.get();

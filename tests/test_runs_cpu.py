@@ -11,7 +11,8 @@ flagging its non-fluid links and naming its run, per run 18 offsets).  Checked h
     larger than the site count, site counts below and across 1024-site chunks, and
     fluid entries beyond the encoded sites (the ghosts of a split partition);
   * a rows-ordered vessel tree compresses (runs of tens of sites); a random order does
-    not, and the encoder then reports no encoding;
+    not, and the encoder then reports no encoding; a table of more than 2^20 sites is
+    encoded in spans whose runs join up in order;
   * an entry that is neither a fluid index nor the scheme's virtual index, and bad
     arguments, are refused.
 
@@ -99,6 +100,23 @@ def test_rows_tree_compresses_and_small_tables(hemegb_lib):
         enc = hemegb_lib.encode_runs(T, n=n, n_ref=n_all, scheme="ab")  # entries beyond n: ghosts
         assert enc is not None, n
         assert np.array_equal(_decode(*enc, n, n_all, "ab"), T[:, :n].astype(np.int64)), n
+
+
+def test_spans_of_a_large_table(hemegb_lib):
+    """More than 2^20 sites: the encoder works on spans of 2^20 sites in parallel, each
+    starting a run; the decode is still every entry, and run0 follows the spans' offsets."""
+    geo = S.cylinder(radius=30, length=420)
+    xs, nbr_c = hemegb_lib.build_neighbours(geo.xyz, geo.iolets)
+    n = xs.shape[0]
+    assert n > (1 << 20)
+    stride = (n + 127) // 128 * 128
+    T = _device_table(xs, nbr_c, _rows_order(xs), "aa", stride)
+    lword, run0, rdelta = hemegb_lib.encode_runs(T, n=n, scheme="aa")
+    assert np.array_equal(_decode(lword, run0, rdelta, n, stride, "aa"), T[:, :n].astype(np.int64))
+    q = np.arange(n)
+    run = run0[q >> 10] + (lword[:n] >> 18).astype(np.int64)
+    assert run[0] == 0 and run[-1] == rdelta.shape[0] - 1 and np.all(np.diff(run) >= 0)
+    assert run[1 << 20] == run[(1 << 20) - 1] + 1                 # a span starts a run
 
 
 def test_random_order_does_not_compress(hemegb_lib):
