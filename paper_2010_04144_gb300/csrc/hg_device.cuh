@@ -273,24 +273,19 @@ template <bool HINT, typename T> __device__ __forceinline__ T load_rw(const T *p
 // index, or for a non-fluid link the virtual index s + dd np with dd = opp(I) - I
 // (A/B) or I - opp(I) (AA).  TabNb reads row I-1 of the table (72 bytes per site
 // in all); RunNb reads one word per site (non-fluid flags, run within the chunk),
-// the chunk's first run and the run's offsets, which the run's other sites also
-// read (L1 hits): about 4 + 72 / run-length bytes per site.  reload() gives an
-// accessor whose next reads are not merged with earlier ones, so a scatter after
-// the collision re-reads (cache hits) instead of keeping 18 entries in registers.
+// the chunk's first run and the run's 80-byte row of offsets, which the run's other
+// sites also read (L1 hits): about 4 + 80 / run-length bytes per site.
+// RunNb::reload() gives an accessor whose next reads are not merged with earlier
+// ones, so a scatter after the collision re-reads (cache hits) instead of keeping
+// 18 entries in registers.
 template <bool HINT> struct TabNb {
     const int32_t *p;
     int64_t np;
     __device__ __forceinline__ TabNb(const DomDev &D, int64_t s) : p(D.nbr + s), np(D.np) {}
-    __device__ __forceinline__ TabNb(const int32_t *p_, int64_t np_) : p(p_), np(np_) {}
-    template <int I> __device__ __forceinline__ int32_t at() const {
-        return load_nbr<HINT>(p + (int64_t)(I - 1) * np);
-    }
     __device__ __forceinline__ void all(int32_t nb[18]) const {
 #pragma unroll
         for (int i = 0; i < 18; ++i) nb[i] = load_nbr<HINT>(p + (int64_t)i * np);
     }
-    __device__ __forceinline__ TabNb reload() const { return TabNb(opaque_ptr(p), np); }
-    __device__ __forceinline__ void prefetch() const {}
 };
 template <int SCHEME, bool HINT> struct RunNb {
     uint32_t w;
@@ -302,10 +297,6 @@ template <int SCHEME, bool HINT> struct RunNb {
     }
     __device__ __forceinline__ RunNb(uint32_t w_, const int32_t *rd_, int32_t s_, int32_t np_)
         : w(w_), rd(rd_), s(s_), np(np_) {}
-    template <int I> __device__ __forceinline__ int32_t at() const {
-        constexpr int dd = SCHEME == kAA ? I - OPP(I) : OPP(I) - I;
-        return ((w >> (I - 1)) & 1u) ? s + dd * np : s + __ldg(rd + (I - 1));
-    }
     // all 18 entries: the run's row as five 16-byte loads
     __device__ __forceinline__ void all(int32_t nb[18]) const {
         int32_t d[kRunStride];
@@ -337,11 +328,9 @@ template <bool HINT> struct TabNb2 {
     const int32_t *p;
     int64_t np;
     __device__ __forceinline__ TabNb2(const DomDev &D, int64_t s) : p(D.nbr + s), np(D.np) {}
-    __device__ __forceinline__ TabNb2(const int32_t *p_, int64_t np_) : p(p_), np(np_) {}
     template <int I> __device__ __forceinline__ int2 at() const {
         return __ldg(reinterpret_cast<const int2 *>(p + (int64_t)(I - 1) * np));
     }
-    __device__ __forceinline__ TabNb2 reload() const { return TabNb2(opaque_ptr(p), np); }
 };
 template <int SCHEME> struct RunNb2 {
     uint32_t wa, wb;
@@ -355,19 +344,12 @@ template <int SCHEME> struct RunNb2 {
         ra = D.rdelta + (int64_t)(r0 + (int32_t)(w.x >> 18)) * kRunStride;
         rb = D.rdelta + (int64_t)(r0 + (int32_t)(w.y >> 18)) * kRunStride;
     }
-    __device__ __forceinline__ RunNb2(uint32_t wa_, uint32_t wb_, const int32_t *ra_, const int32_t *rb_,
-                                      int32_t s_, int32_t np_)
-        : wa(wa_), wb(wb_), ra(ra_), rb(rb_), s(s_), np(np_) {}
     template <int I> __device__ __forceinline__ int2 at() const {
         constexpr int dd = SCHEME == kAA ? I - OPP(I) : OPP(I) - I;
         const int32_t da = __ldg(ra + (I - 1));
         const int32_t db = ra == rb ? da : __ldg(rb + (I - 1));
         return make_int2(((wa >> (I - 1)) & 1u) ? s + dd * np : s + da,
                          ((wb >> (I - 1)) & 1u) ? s + 1 + dd * np : s + 1 + db);
-    }
-    __device__ __forceinline__ RunNb2 reload() const {
-        const int32_t *q = opaque_ptr(ra);
-        return RunNb2(wa, wb, q, q + (rb - ra), s, np);
     }
 };
 template <int SCHEME, bool HINT, bool RUNS>
