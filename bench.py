@@ -436,7 +436,8 @@ def serve_stats(args, H, device, prepared=None):
     srv = SV.Server(device=device, storage=args.serve_storage, scheme=args.serve_scheme,
                     budget_bytes=args.budget_gb * 1e9, chunk_steps=100, block_size=shape[0],
                     sites_per_thread=shape[1], kernel_variant=shape[2],
-                    build_workers=args.serve_build_workers, policy=args.serve_policy, ordering=ordering)
+                    build_workers=args.serve_build_workers, policy=args.serve_policy, ordering=ordering,
+                    tick_site_steps=args.serve_tick_sites or None)
     try:
         for r, g in zip(reqs, geos):
             if r.coupled:
@@ -459,7 +460,8 @@ def serve_stats(args, H, device, prepared=None):
     cfg = {"workload": f"first {len(reqs)} of the seeded 256-request stream (Poisson {args.rate}/s, "
                        f"sites log-uniform [{args.min_sites:.0e}, {args.max_sites:.0e}], half coupled "
                        f"pairs, {args.serve_steps} steps each)",
-           "budget_gb": args.budget_gb, "tick_steps": 100, "scheme": args.serve_scheme,
+           "budget_gb": args.budget_gb, "tick_steps": 100, "tick_site_steps": args.serve_tick_sites or None,
+           "scheme": args.serve_scheme,
            "storage": args.serve_storage, "ordering": ordering, "ordering_ms": order_ms,
            "launch": list(shape), "launch_tuned_on_sites": tuned_sites,
            "build_workers": args.serve_build_workers, "policy": args.serve_policy,
@@ -803,6 +805,9 @@ def main():
     ap.add_argument("--serve-steps", type=int, default=2000)
     ap.add_argument("--serve-storage", default="f16")
     ap.add_argument("--serve-scheme", default="aa")
+    ap.add_argument("--serve-tick-sites", type=float, default=3e8,
+                    help="serving: site updates each request advances per tick, in steps of 100 x a power "
+                         "of two (0: 100 steps for every request)")
     ap.add_argument("--serve-ordering", default="auto", help="auto (tuned) or morton / rows / bricks")
     ap.add_argument("--serve-policy", default="fifo", choices=["fifo", "backfill"])
     ap.add_argument("--serve-build-workers", type=int, default=4,

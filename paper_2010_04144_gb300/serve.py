@@ -5,7 +5,9 @@ to be advanced a given number of steps.  The server keeps every admitted
 request's distributions resident in HBM and advances all of them together:
 each tick is one hg_step_domains call, i.e. one stream-collide launch per step
 whose tile table spans every active domain (plus one iolet-update launch),
-captured as a CUDA graph per active set.  Requests that arrive while others
+captured as a CUDA graph per active set.  With tick_site_steps, a tick gives every
+request about the same number of site updates instead of the same step count (one
+hg_step_domains call per step count), so small requests are not paced by large ones.  Requests that arrive while others
 run are admitted, first come first served, as soon as their estimated HBM
 footprint fits the budget (policy "fifo"); policy "backfill" also lets a
 later request start early when it cannot delay the blocked head (EASY
@@ -103,7 +105,7 @@ class Server:
 
     def __init__(self, device=0, storage="f16", scheme="aa", budget_bytes=180e9, chunk_steps=100,
                  block_size=0, sites_per_thread=0, kernel_variant=None, graph_steps=0,
-                 build_workers=1, policy="fifo", ordering="morton"):
+                 build_workers=1, policy="fifo", ordering="morton", tick_site_steps=None):
         st = H.STORAGE[storage] if isinstance(storage, str) else storage
         sc = H.SCHEME[scheme] if isinstance(scheme, str) else scheme
         if kernel_variant is None:
@@ -117,6 +119,11 @@ class Server:
         self.ordering = ordering          # device site layout of every request's domains
         self.budget = float(budget_bytes)
         self.chunk = int(chunk_steps)
+        # None: every active request advances chunk_steps per tick (the same step count);
+        # a number: each request advances about tick_site_steps site updates per tick,
+        # chunk_steps x a power of two, at least chunk_steps, at most what it has left, so a
+        # small request finishes in few ticks instead of pacing at the big ones' rate
+        self.tick_site_steps = None if tick_site_steps is None else float(tick_site_steps)
         self.queue: list[Job] = []
         self.building: list[tuple[Job, object]] = []   # (job, future) in admission order
         self.active: list[Job] = []
@@ -196,7 +203,18 @@ class Server:
 
     def _ticks_left(self, job):
         left = job.steps - job.done_steps
-        return -(-left // self.chunk)
+        return -(-left // self._tick_steps(job)) if left > 0 else 0
+
+    def _tick_steps(self, job):
+        """Steps the request advances in its next tick."""
+        left = job.steps - job.done_steps
+        if self.tick_site_steps is None:
+            return min(self.chunk, left)
+        n = max(1, sum(g.n for g in job.geoms))
+        k = self.chunk
+        while k * 2 <= left and 2 * k * n <= self.tick_site_steps:
+            k *= 2
+        return min(k, left)
 
     def _backfill(self, now_s):
         """EASY backfilling on memory, counted in ticks: the blocked head's start (its shadow
@@ -311,21 +329,28 @@ class Server:
             self._activate()
             self._admit(clock() - t0)
             if self.active:
-                stepping = [d for j in self.active for d in j.domains]
                 ticking = list(self.active)
-                k = min(self.chunk, min(j.steps - j.done_steps for j in ticking))
-                self.ctx.step_domains(stepping, k)  # asynchronous: builds run meanwhile
+                if self.tick_site_steps is None:  # one step count for every request
+                    k = min(self.chunk, min(j.steps - j.done_steps for j in ticking))
+                    groups = {k: ticking}
+                else:
+                    groups = {}
+                    for j in ticking:
+                        groups.setdefault(self._tick_steps(j), []).append(j)
+                for k, jobs in sorted(groups.items()):  # asynchronous: builds run meanwhile
+                    self.ctx.step_domains([d for j in jobs for d in j.domains], k)
                 t = time.perf_counter()
                 self.ctx.sync()
                 self.wait_s += time.perf_counter() - t
                 self.ticks += 1
-                self.site_steps += sum(d.n for d in stepping) * k
-                for j in ticking:
-                    if j.cancelled:
-                        continue
-                    j.done_steps += k
-                    if j.done_steps >= j.steps:
-                        self._retire(j, read=True, now_s=clock() - t0)
+                for k, jobs in groups.items():
+                    self.site_steps += sum(d.n for j in jobs for d in j.domains) * k
+                    for j in jobs:
+                        if j.cancelled:
+                            continue
+                        j.done_steps += k
+                        if j.done_steps >= j.steps:
+                            self._retire(j, read=True, now_s=clock() - t0)
             elif self.building:
                 # nothing to step: wait for the oldest build, or for the next arrival if sooner
                 gap = self.queue[0].arrival_s - (clock() - t0) if self.queue else 0.0

@@ -3,8 +3,9 @@
 FIFO admission by HBM footprint, no starvation, budget never exceeded,
 cancellation, exact step counts per request, a failed build that fails its own
 request only, a built domain larger than its estimate holding admissions back,
-and the footprint estimate as an upper bound on the boundary slots of an
-iolet-heavy geometry.
+the footprint estimate as an upper bound on the boundary slots of an
+iolet-heavy geometry, and ticks that give every request an equal share of site
+updates instead of an equal step count.
 """
 import numpy as np
 import pytest
@@ -307,3 +308,32 @@ def test_unknown_policy_rejected(monkeypatch):
     monkeypatch.setattr(SV.H, "Context", lambda **kw: _Ctx(**kw))
     with pytest.raises(ValueError):
         SV.Server(policy="lifo")
+
+
+def test_equal_share_ticks(monkeypatch):
+    """With tick_site_steps every request advances about that many site updates per tick:
+    a small request takes a multiple of the tick's step count in one call, a large one
+    the plain tick; each request still ends at exactly its step count, and the small
+    one finishes in fewer ticks than under equal step counts."""
+    monkeypatch.setattr(SV.H, "Context", lambda **kw: _Ctx(**kw))
+    out = {}
+    for share in (None, 4e5):
+        srv = SV.Server(storage="f16", scheme="aa", budget_bytes=1e12, chunk_steps=50,
+                        build_workers=0, tick_site_steps=share)
+        small, large = _job(0, 0.0, n=1000, steps=1000), _job(1, 0.0, n=20000, steps=1000)
+        srv.submit(small)
+        srv.submit(large)
+        clk = _Clock()
+        srv.run(clock=clk, sleep=clk.sleep)
+        srv.close()
+        assert all(j.done_steps == j.steps for j in srv.finished) and len(srv.finished) == 2
+        assert all(d.step == 1000 for d in srv.ctx.live)
+        steps = [c for c in srv.ctx.calls if c[0] == "step"]
+        out[share] = (small.finished_s, large.finished_s, steps, srv.ticks)
+    plain, shared = out[None], out[4e5]
+    assert all(k == 50 for _, _, k in plain[2])                     # one step count per tick
+    assert {k for _, _, k in shared[2]} >= {50, 400}                # 4e5 / 1000 sites -> 400 steps
+    assert shared[0] < plain[0]                                     # the small request is done sooner
+    assert shared[3] == plain[3] == 20                              # the large one sets the tick count
+    with pytest.raises(ValueError):                                 # steps stay multiples of the tick
+        SV.Server(storage="f16", scheme="aa", tick_site_steps=4e5).submit(_job(2, 0.0, steps=130))
