@@ -164,7 +164,7 @@ def kernel_source_sha():
     import hashlib
 
     h = hashlib.sha256()
-    for f in ("hg_device.cuh", "hg_sc_f32.cu", "hg_sc_f16.cu", "hg_sc_bf16.cu", "hg_internal.h"):
+    for f in ("hg_device.cuh", "hg_sc_part.cu", "hg_internal.h"):
         with open(os.path.join(ROOT, "paper_2010_04144_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

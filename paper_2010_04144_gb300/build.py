@@ -17,7 +17,13 @@ LIB = os.path.join(PKG, "libhemegb.so")
 CUDA_HOME = os.environ.get("CUDA_HOME", "/usr/local/cuda")
 NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["hg_sc_f32.cu", "hg_sc_f16.cu", "hg_sc_bf16.cu", "hg_kernels.cu", "hg_host.cpp", "hg_noalloc.cu"]
+# (source, object name, extra flags): hg_sc_part.cu once per (storage, scheme, launch parity)
+# combination of the stream-collide kernels, so the heavy instantiations compile in parallel
+_PARTS = [(s, c, p) for s in (0, 1, 2) for c, p in ((0, 2), (1, 0), (1, 1), (1, 2))]
+UNITS = ([("hg_sc_part.cu", f"hg_sc_{s}{c}{p}", [f"-DHG_PART_S={s}", f"-DHG_PART_SCHEME={c}",
+                                                   f"-DHG_PART_PAR={p}"]) for s, c, p in _PARTS]
+         + [("hg_kernels.cu", "hg_kernels", []), ("hg_host.cpp", "hg_host", []), ("hg_noalloc.cu", "hg_noalloc", [])])
+SOURCES = sorted({u[0] for u in UNITS})
 HEADERS = ["hg_internal.h", "hg_device.cuh", os.path.join("..", "..", "include", "hemegb.h")]
 
 
@@ -29,10 +35,10 @@ def _stale() -> bool:
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def _compile_cmd(src: str, obj: str, verbose_ptxas: bool) -> list:
+def _compile_cmd(src: str, obj: str, verbose_ptxas: bool, extra=()) -> list:
     if src.endswith(".cu"):
         cmd = [NVCC, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
-               "--expt-relaxed-constexpr", "-c", src, "-o", obj]
+               "--expt-relaxed-constexpr", *extra, "-c", src, "-o", obj]
         if verbose_ptxas:
             cmd.insert(1, "-Xptxas=-v")
         return cmd
@@ -45,12 +51,12 @@ def build(force: bool = False, verbose_ptxas: bool = False) -> str:
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     objs, procs = [], []
-    for f in SOURCES:
-        obj = os.path.join(BUILD, f + ".o")
+    for f, name, extra in UNITS:
+        obj = os.path.join(BUILD, name + ".o")
         objs.append(obj)
-        procs.append((f, subprocess.Popen(_compile_cmd(os.path.join(CSRC, f), obj, verbose_ptxas),
-                                          stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
-                                          text=True)))
+        procs.append((name, subprocess.Popen(_compile_cmd(os.path.join(CSRC, f), obj, verbose_ptxas, extra),
+                                             stdout=subprocess.PIPE, stderr=subprocess.STDOUT,
+                                             text=True)))
     errs = []
     for f, p in procs:
         out, _ = p.communicate()

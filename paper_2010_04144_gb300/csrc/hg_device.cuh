@@ -1,6 +1,6 @@
 // hg_device.cuh -- device code of the stream-collide kernel, shared by the
-// translation units that instantiate it (one per storage type, compiled in
-// parallel: hg_sc_f32.cu, hg_sc_f16.cu, hg_sc_bf16.cu) and by hg_kernels.cu,
+// translation units that instantiate it (hg_sc_part.cu, compiled once per storage
+// type, scheme and launch parity, in parallel) and by hg_kernels.cu,
 // whose read-back and boundary kernels use the same lattice tables, storage
 // traits and collision.  Everything here has internal linkage, so each
 // translation unit owns the instantiations it makes.
@@ -1282,25 +1282,6 @@ cudaError_t launch_sc_spt(const CollideCfg &cfg, const DomDev *doms, const TileD
     }
 }
 
-template <int S>
-cudaError_t launch_sc_storage(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
-                              int64_t n_tiles, int off, int parity, const OneDomain &one, cudaStream_t st) {
-    // A/B reads its buffer parity per block: specialising it measured slower (the
-    // compile-time buffer choice raised the variant-3 kernel from 52 to 58 registers)
-    if (cfg.scheme == kAB) return launch_sc_spt<S, kAB, 2>(cfg, doms, tiles, n_tiles, off, one, st);
-    if (parity == 0) return launch_sc_spt<S, kAA, 0>(cfg, doms, tiles, n_tiles, off, one, st);
-    if (parity == 1) return launch_sc_spt<S, kAA, 1>(cfg, doms, tiles, n_tiles, off, one, st);
-    return launch_sc_spt<S, kAA, 2>(cfg, doms, tiles, n_tiles, off, one, st);
-}
-
 }  // namespace
-
-// One per storage type, each in its own translation unit.
-cudaError_t launch_sc_f32(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
-                          int off, int parity, const OneDomain &one, cudaStream_t st);
-cudaError_t launch_sc_f16(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
-                          int off, int parity, const OneDomain &one, cudaStream_t st);
-cudaError_t launch_sc_bf16(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
-                           int off, int parity, const OneDomain &one, cudaStream_t st);
 
 }  // namespace hg

@@ -120,6 +120,21 @@ struct CollideCfg {
 cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles,
                                   int64_t n_tiles, int off, int parity, const OneDomain &one,
                                   cudaStream_t st);
+// The stream-collide kernels of one storage type S (0 f32, 1 f16, 2 bf16), scheme
+// (0 A/B, 1 AA) and launch parity PAR (0 even, 1 odd, 2 read from the step counter;
+// A/B always 2): every variant and shape, instantiated in a translation unit of its
+// own (hg_sc_part.cu, compiled once per combination, so the twelve build in parallel).
+template <int S, int SCHEME, int PAR>
+cudaError_t launch_sc_part(const CollideCfg &cfg, const DomDev *doms, const TileDev *tiles, int64_t n_tiles,
+                           int off, const OneDomain &one, cudaStream_t st);
+#define HG_SC_PART_DECL(S_, C_, P_)                                                                  \
+    template <>                                                                                     \
+    cudaError_t launch_sc_part<S_, C_, P_>(const CollideCfg &, const DomDev *, const TileDev *, int64_t, int, \
+                                           const OneDomain &, cudaStream_t);
+HG_SC_PART_DECL(0, 0, 2) HG_SC_PART_DECL(0, 1, 0) HG_SC_PART_DECL(0, 1, 1) HG_SC_PART_DECL(0, 1, 2)
+HG_SC_PART_DECL(1, 0, 2) HG_SC_PART_DECL(1, 1, 0) HG_SC_PART_DECL(1, 1, 1) HG_SC_PART_DECL(1, 1, 2)
+HG_SC_PART_DECL(2, 0, 2) HG_SC_PART_DECL(2, 1, 0) HG_SC_PART_DECL(2, 1, 1) HG_SC_PART_DECL(2, 1, 2)
+#undef HG_SC_PART_DECL
 // One CTA per (iolet, chunk) in `chunks`; partials: 2 doubles per chunk;
 // counters: n_ios + 1 zeroed unsigned ints (left zeroed on return).
 cudaError_t launch_iolet_update(const IoDev *ios, int n_ios, const int2 *chunks, int n_chunks,

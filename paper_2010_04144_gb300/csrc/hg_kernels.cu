@@ -7,7 +7,7 @@
 //
 // Kernels
 //   k_stream_collide_one / k_stream_collide (hg_device.cuh, instantiated per
-//                      storage type in hg_sc_f32.cu / hg_sc_f16.cu / hg_sc_bf16.cu):
+//                      storage type, scheme and launch parity in hg_sc_part.cu):
 //                      fused streaming + boundary rules + LBGK collision for
 //                      every site of one domain, or of many through a tile
 //                      table; A/B pull or AA in place; FP32 / FP16 / BF16
@@ -446,9 +446,16 @@ cudaError_t launch_stream_collide(const CollideCfg &cfg, const DomDev *doms, con
                                   int64_t n_tiles, int off, int parity, const OneDomain &one,
                                   cudaStream_t st) {
     if (n_tiles <= 0) return cudaSuccess;
-    if (cfg.storage == kF32) return launch_sc_f32(cfg, doms, tiles, n_tiles, off, parity, one, st);
-    if (cfg.storage == kF16) return launch_sc_f16(cfg, doms, tiles, n_tiles, off, parity, one, st);
-    if (cfg.storage == kBF16) return launch_sc_bf16(cfg, doms, tiles, n_tiles, off, parity, one, st);
+    // A/B reads its buffer parity per block: specialising it measured slower (the
+    // compile-time buffer choice raised the variant-3 kernel from 52 to 58 registers)
+    const int par = cfg.scheme == kAB ? 2 : (parity == 0 || parity == 1 ? parity : 2);
+#define HG_PART(S_, C_, P_)                                                                    \
+    if (cfg.storage == S_ && cfg.scheme == C_ && par == P_)                                   \
+        return launch_sc_part<S_, C_, P_>(cfg, doms, tiles, n_tiles, off, one, st);
+    HG_PART(kF32, kAB, 2) HG_PART(kF32, kAA, 0) HG_PART(kF32, kAA, 1) HG_PART(kF32, kAA, 2)
+    HG_PART(kF16, kAB, 2) HG_PART(kF16, kAA, 0) HG_PART(kF16, kAA, 1) HG_PART(kF16, kAA, 2)
+    HG_PART(kBF16, kAB, 2) HG_PART(kBF16, kAA, 0) HG_PART(kBF16, kAA, 1) HG_PART(kBF16, kAA, 2)
+#undef HG_PART
     return cudaErrorInvalidValue;
 }
 
