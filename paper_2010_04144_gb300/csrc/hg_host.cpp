@@ -88,6 +88,21 @@ template <typename F> void parallel_for(int64_t n, F &&fn, int64_t grain = 1 << 
     for (auto &x : th) x.join();
 }
 
+// A table whose elements are left uninitialised on resize, so a large table is
+// first written (and its pages first touched) by the parallel loop that fills it.
+template <class T> struct NoInitAlloc : std::allocator<T> {
+    using std::allocator<T>::allocator;
+    template <class U> struct rebind { using other = NoInitAlloc<U>; };
+    template <class U, class... A> void construct(U *p, A &&...a) {
+        if constexpr (sizeof...(A) == 0) ::new ((void *)p) U;
+        else ::new ((void *)p) U(std::forward<A>(a)...);
+    }
+};
+using I32Table = std::vector<int32_t, NoInitAlloc<int32_t>>;
+using U32Table = std::vector<uint32_t, NoInitAlloc<uint32_t>>;
+using U64Table = std::vector<uint64_t, NoInitAlloc<uint64_t>>;
+using I64Table = std::vector<int64_t, NoInitAlloc<int64_t>>;
+
 // ---------------------------------------------------------------- Morton
 inline uint64_t spread21(uint64_t v) {
     v &= 0x1fffffULL;
@@ -162,7 +177,7 @@ struct BlockIndex {
 
     static inline uint64_t hash(uint64_t k) { return (k * 0x9E3779B97F4A7C15ULL) >> 17; }
 
-    void build(const std::vector<uint64_t> &keys) {
+    void build(const U64Table &keys) {
         const int64_t n = (int64_t)keys.size();
         for (int64_t s = 0; s < n; ++s) {
             const uint64_t b = keys[s] >> 9;
@@ -197,28 +212,60 @@ struct BlockIndex {
         }
     }
 
-    inline int64_t find(uint64_t key) const {
-        const uint64_t b = key >> 9;
+    // block id of block key b, or -1
+    inline int64_t block_id(uint64_t b) const {
         uint64_t h = hash(b) & mask;
         for (;;) {
             const int32_t id = table[h];
-            if (id < 0) return -1;
-            if (bkey[id] == b) {
-                const unsigned o = (unsigned)(key & 511);
-                const uint64_t w = bits[(int64_t)id * 8 + (o >> 6)];
-                const uint64_t bit = 1ULL << (o & 63);
-                if (!(w & bit)) return -1;
-                return first[id] + prefix[(int64_t)id * 8 + (o >> 6)] +
-                       __builtin_popcountll(w & (bit - 1));
-            }
+            if (id < 0 || bkey[id] == b) return id;
             h = (h + 1) & mask;
         }
     }
+    // canonical index of the site with Morton key `key` in block `id`, or -1
+    inline int64_t rank(int64_t id, uint64_t key) const {
+        const unsigned o = (unsigned)(key & 511);
+        const uint64_t w = bits[id * 8 + (o >> 6)];
+        const uint64_t bit = 1ULL << (o & 63);
+        if (!(w & bit)) return -1;
+        return first[id] + prefix[id * 8 + (o >> 6)] + __builtin_popcountll(w & (bit - 1));
+    }
 };
+
+// A thread's lookups with the last block seen in each of the eight slots that the
+// 2x2x2 neighbourhood of blocks maps to (the low bit of each block coordinate): the
+// 18 neighbours of consecutive canonical sites mostly fall in the same few blocks.
+struct BlockCache {
+    const BlockIndex &bi;
+    uint64_t tag[8];
+    int64_t id[8];
+    explicit BlockCache(const BlockIndex &b) : bi(b) {
+        for (int k = 0; k < 8; ++k) tag[k] = ~0ULL, id[k] = -1;
+    }
+    inline int64_t find(uint64_t key) {
+        const uint64_t b = key >> 9;
+        const int slot = (int)(b & 7);
+        if (tag[slot] != b) {
+            tag[slot] = b;
+            id[slot] = bi.block_id(b);
+        }
+        return id[slot] < 0 ? -1 : bi.rank(id[slot], key);
+    }
+};
+
+// Morton key of the lattice point one unit along +-axis from the point with key k
+// (dilated-integer increment: the other axes' bits are held at one / zero so the
+// carry or borrow runs through the axis' own bits only); the caller keeps the
+// coordinate inside [0, 2^21).
+inline uint64_t morton_step(uint64_t k, int axis, int d) {
+    const uint64_t M = 0x1249249249249249ULL << axis;
+    if (d > 0) return (((k | ~M) + 1) & M) | (k & ~M);
+    if (d < 0) return (((k & M) - 1) & M) | (k & ~M);
+    return k;
+}
 
 // Canonical order: sort (key, index) pairs by key -- bucket by the leading key
 // bits, then sort each bucket, buckets in parallel.
-void sort_keys(std::vector<uint64_t> &key, std::vector<int64_t> &idx) {
+void sort_keys(U64Table &key, I64Table &idx) {
     const int64_t n = (int64_t)key.size();
     if (n <= 1) return;
     // bucket by the top 12 bits of the key range (counting sort, in parallel over
@@ -255,7 +302,12 @@ void sort_keys(std::vector<uint64_t> &key, std::vector<int64_t> &idx) {
         }
         cnt[nbk] = acc;
     }
-    std::vector<std::pair<uint64_t, int64_t>> tmp(n);
+    struct KeyIdx {
+        uint64_t first;
+        int64_t second;
+        bool operator<(const KeyIdx &o) const { return first < o.first || (first == o.first && second < o.second); }
+    };
+    std::vector<KeyIdx, NoInitAlloc<KeyIdx>> tmp(n);  // every element written by the scatter
     parallel_for(T, [&](int64_t lo, int64_t hi) {
         for (int64_t t = lo; t < hi; ++t) {
             int64_t *pos = hist.data() + (size_t)t * nbk;
@@ -293,8 +345,8 @@ int device_order(const std::vector<int32_t> &xyz, int64_t n, int ordering, std::
             lo[e] = std::min(lo[e], xyz[3 * s + e]);
             hi[e] = std::max(hi[e], xyz[3 * s + e]);
         }
-    std::vector<uint64_t> key(n);
-    std::vector<int64_t> idx(n);
+    U64Table key(n);  // both written in full by the parallel loop below
+    I64Table idx(n);
     if (ordering == HG_ORDER_ROWS) {
         parallel_for(n, [&](int64_t a, int64_t b) {
             for (int64_t s = a; s < b; ++s) {
@@ -327,7 +379,9 @@ int device_order(const std::vector<int32_t> &xyz, int64_t n, int ordering, std::
     }
     sort_keys(key, idx);
     canon_of.resize(n);
-    for (int64_t q = 0; q < n; ++q) canon_of[q] = (int32_t)idx[q];
+    parallel_for(n, [&](int64_t lo, int64_t hi) {
+        for (int64_t q = lo; q < hi; ++q) canon_of[q] = (int32_t)idx[q];
+    });
     return HG_OK;
 }
 
@@ -667,10 +721,11 @@ int ensure_scratch(hg_ctx *ctx, size_t bytes) {
 // makes a run cover most of an x-row of a vessel.  Returns false (nothing built)
 // when an entry does not fit that form or the encoding would not save enough
 // traffic (runs shorter than 4.5 sites on average: more than 16 bytes per site).
-bool build_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t np, int vdir, std::vector<uint32_t> &lword,
+bool build_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t np, int vdir, U32Table &lword,
                 std::vector<int32_t> &run0, std::vector<int32_t> &rdelta) {
     if (n <= 0) return false;
-    lword.assign((size_t)np, 0u);
+    lword.resize((size_t)np);  // [0, n) is written by the spans below, in parallel
+    std::fill(lword.begin() + n, lword.end(), 0u);
     run0.assign((size_t)((np + 1023) / 1024), 0);
     rdelta.clear();
     // Spans of 2^20 sites (whole 1024-site chunks) are encoded in parallel, each starting
@@ -751,9 +806,9 @@ bool build_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t np, int vd
 // nbr has 18 rows of `stride` entries (>= n; the padding is -1).  Returns HG_OK
 // or HG_ERR_ARG with the reason in `why`.
 int build_canonical(const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32_t nio, int64_t stride,
-                    std::vector<int32_t> &xyz_sorted, std::vector<int32_t> &nbr, std::string &why) {
-    std::vector<uint64_t> key(n);
-    std::vector<int64_t> idx(n);
+                    std::vector<int32_t> &xyz_sorted, I32Table &nbr, std::string &why) {
+    U64Table key(n);  // both written in full by the parallel loop below
+    I64Table idx(n);
     std::atomic<int> bad{0};
     parallel_for(n, [&](int64_t lo, int64_t hi) {
         for (int64_t s = lo; s < hi; ++s) {
@@ -780,7 +835,7 @@ int build_canonical(const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32
         for (int64_t s = lo; s < hi; ++s)
             for (int c = 0; c < 3; ++c) xyz_sorted[3 * s + c] = xyz[3 * idx[s] + c];
     });
-    std::vector<int64_t>().swap(idx);
+    I64Table().swap(idx);
     BlockIndex bi;
     bi.build(key);
     std::vector<IoletGeom> geo(nio);
@@ -792,15 +847,20 @@ int build_canonical(const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32
         const double r = iolets[k].radius / 1024.0 + 3.0;
         geo[k].reach2 = r * r + 1.0;
     }
-    nbr.assign((size_t)18 * stride, -1);
+    nbr.resize((size_t)18 * stride);  // every entry is written below, in parallel
+    if (stride > n)
+        for (int i = 0; i < 18; ++i) std::fill(nbr.begin() + (size_t)i * stride + n, nbr.begin() + (size_t)(i + 1) * stride, -1);
     parallel_for(n, [&](int64_t lo, int64_t hi) {
+        BlockCache cache(bi);
         for (int64_t s = lo; s < hi; ++s) {
             const int64_t x = xyz_sorted[3 * s], y = xyz_sorted[3 * s + 1], z = xyz_sorted[3 * s + 2];
+            const uint64_t ks = key[s];  // the site's own Morton key (sorted order)
             for (int i = 1; i < 19; ++i) {
                 const int64_t qx = x - kC[i][0], qy = y - kC[i][1], qz = z - kC[i][2];
                 int64_t v = -1;
                 if (qx >= 0 && qy >= 0 && qz >= 0 && qx < (1 << 21) && qy < (1 << 21) && qz < (1 << 21))
-                    v = bi.find(morton3((uint32_t)qx, (uint32_t)qy, (uint32_t)qz));
+                    v = cache.find(morton_step(morton_step(morton_step(ks, 0, -kC[i][0]), 1, -kC[i][1]), 2,
+                                               -kC[i][2]));
                 nbr[(size_t)(i - 1) * stride + s] = v >= 0 ? (int32_t)v : classify(geo, qx, qy, qz);
             }
         }
@@ -964,7 +1024,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     PhaseTrace trace(n);
     // --- canonical order and neighbour table (canonical codes)
     const int64_t np = d->np;
-    std::vector<int32_t> nbr;
+    I32Table nbr;
     {
         std::string why;
         const int brc = build_canonical(xyz, n, iolets, nio, np, d->xyz, nbr, why);
@@ -986,7 +1046,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
         parallel_for(n, [&](int64_t lo, int64_t hi) {
             for (int64_t q = lo; q < hi; ++q) dev_of[canon_of[q]] = (int32_t)q;
         });
-        std::vector<int32_t> row(n);
+        I32Table row(n);
         for (int i = 0; i < 18; ++i) {
             int32_t *r = nbr.data() + (size_t)i * np;
             parallel_for(n, [&](int64_t lo, int64_t hi) {
@@ -995,7 +1055,7 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
                     row[q] = v >= 0 ? dev_of[v] : v;
                 }
             });
-            std::copy(row.begin(), row.end(), r);
+            parallel_for(n, [&](int64_t lo, int64_t hi) { std::copy(row.begin() + lo, row.begin() + hi, r + lo); });
         }
     }
     auto canon = [&](int64_t q) -> int64_t { return canon_of.empty() ? q : canon_of[q]; };
@@ -1003,7 +1063,8 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     trace.mark("device ordering");
     // --- iolet adjacency: slots numbered in device order (the kernels find a
     // site's slot as the rank of its flag), per-iolet CSR lists in canonical order
-    std::vector<int32_t> slot_of(n, -1);
+    I32Table slot_of(n);
+    parallel_for(n, [&](int64_t lo, int64_t hi) { std::fill(slot_of.begin() + lo, slot_of.begin() + hi, -1); });
     int64_t n_adj = 0;
     std::vector<int64_t> per_io(nio + 1, 0);
     auto distinct_iolets = [&](int64_t q, int seen[18]) {
@@ -1099,12 +1160,12 @@ int hg_domain_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet 
     for (int64_t q = 0; q < n; ++q)
         if (slot_of[q] >= 0) slot_site[slot_of[q]] = (int32_t)q;
     trace.mark("virtual indices");
-    std::vector<uint32_t> lword;
+    U32Table lword;
     std::vector<int32_t> run0, rdelta;
     if (build_runs(nbr.data(), n, n, np, aa ? -1 : 1, lword, run0, rdelta))
         d->n_runs = (int64_t)rdelta.size() / kRunStride;
     d->io_codes_host = codes;
-    d->slot_of_dev = slot_of;
+    d->slot_of_dev.assign(slot_of.begin(), slot_of.end());
     d->slots_host = slots;
     d->canon_of_host = canon_of;
     d->dev_of_host = dev_of;
@@ -1244,7 +1305,7 @@ int hg_encode_runs(const int32_t *nbr, int64_t n, int64_t n_ref, int64_t row_str
     if (!nbr || !n_runs_out || n < 1 || n_ref < n || row_stride < n || row_stride > ((int64_t)1 << 30) ||
         (scheme != HG_SCHEME_AB && scheme != HG_SCHEME_AA))
         return HG_ERR_ARG;
-    std::vector<uint32_t> lw;
+    U32Table lw;
     std::vector<int32_t> r0, rd;
     *n_runs_out = 0;
     if (!build_runs(nbr, n, n_ref, row_stride, scheme == HG_SCHEME_AA ? -1 : 1, lw, r0, rd)) return HG_OK;
@@ -1365,7 +1426,8 @@ int hg_build_neighbours(const int32_t *xyz, int64_t n, const hg_iolet *iolets, i
     if (nio < 0 || nio > kMaxIolets || (nio > 0 && !iolets)) return HG_ERR_ARG;
     for (int k = 0; k < nio; ++k)
         if (!iolet_ok(iolets[k])) return HG_ERR_ARG;
-    std::vector<int32_t> xs, nbr;
+    std::vector<int32_t> xs;
+    I32Table nbr;
     std::string why;
     const int rc = build_canonical(xyz, n, iolets, nio, n, xs, nbr, why);
     if (rc != HG_OK) return fail(nullptr, rc, "%s", why.c_str());
@@ -2126,7 +2188,7 @@ struct SplitLayout {
     std::vector<std::vector<std::pair<int32_t, int64_t>>> need;  // [q * k + p]: (direction i, site) p pulls from q
 };
 
-inline bool has_iolet_link(const std::vector<int32_t> &nbr, int64_t stride, int64_t s) {
+inline bool has_iolet_link(const I32Table &nbr, int64_t stride, int64_t s) {
     for (int i = 0; i < 18; ++i)
         if (nbr[(size_t)i * stride + s] < -1) return true;
     return false;
@@ -2134,7 +2196,7 @@ inline bool has_iolet_link(const std::vector<int32_t> &nbr, int64_t stride, int6
 
 // Cuts with equal cost per partition (a site costs 1, a site with an iolet link
 // `bw`), every partition non-empty; ghosts and the halo each partition needs.
-void split_layout(const std::vector<int32_t> &nbr, int64_t stride, int64_t n, int k, double bw, SplitLayout &L) {
+void split_layout(const I32Table &nbr, int64_t stride, int64_t n, int k, double bw, SplitLayout &L) {
     std::vector<double> pre(n + 1, 0.0);
     for (int64_t s = 0; s < n; ++s) pre[s + 1] = pre[s] + (has_iolet_link(nbr, stride, s) ? bw : 1.0);
     L.first.assign(k + 1, 0);
@@ -2303,7 +2365,8 @@ int hg_split_layout(const int32_t *xyz, int64_t n, const hg_iolet *iolets, int32
     if (k < 1 || k > 1024 || k > n) return HG_ERR_ARG;
     for (int q = 0; q < nio; ++q)
         if (!iolet_ok(iolets[q])) return HG_ERR_ARG;
-    std::vector<int32_t> xs, nbr;
+    std::vector<int32_t> xs;
+    I32Table nbr;
     std::string why;
     if (build_canonical(xyz, n, iolets, nio, n, xs, nbr, why) != HG_OK) return fail(nullptr, HG_ERR_ARG, "%s", why.c_str());
     SplitLayout L;
@@ -2345,7 +2408,8 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
     sp->tau = tau;
     sp->staged = spar->exchange == HG_EXCHANGE_STAGED;
     sp->io.assign(iolets, iolets + nio);
-    std::vector<int32_t> xs, nbr;
+    std::vector<int32_t> xs;
+    I32Table nbr;
     {
         std::string why;
         if (build_canonical(xyz, n, iolets, nio, n, xs, nbr, why) != HG_OK)
@@ -2457,7 +2521,7 @@ int hg_split_create(hg_ctx *ctx, const int32_t *xyz, int64_t n, const hg_iolet *
     A(sp->force, (size_t)std::max(1, nio) * 16);
     // per partition: local tables (owned sites first, then ghosts)
     std::vector<std::vector<int32_t>> tab(k), mask(k), pref(k), gidx(k), r0(k), rd(k);
-    std::vector<std::vector<uint32_t>> lw(k);
+    std::vector<U32Table> lw(k);
     for (int p = 0; p < k && rc == HG_OK; ++p) {
         SplitPart &P = sp->parts[p];
         P.first = L.first[p];
