@@ -226,10 +226,11 @@ int hg_domain_info(hg_domain *d, int64_t *n_sites, int32_t *n_iolets, int64_t *n
  * its 18-row table (72 bytes per site, what the gathers of a pull step read
  * besides the populations); where it compresses (runs of at least 4.5 sites on
  * average) the build also encodes it as runs: maximal ranges of consecutive
- * device sites whose fluid links share one offset per direction, plus a 4-byte
- * word per site flagging its non-fluid links.  In rows ordering a run covers
- * most of an x-row of a vessel, so the encoding costs about 4 + 72 / run-length
- * bytes per site.  Kernel variants 8..11 read it; the results are the same bits.
+ * device sites whose fluid links share one offset per direction (each 2^20-site
+ * span starting a new run), plus a 4-byte word per site flagging its non-fluid
+ * links.  In rows ordering a run covers most of an x-row of a vessel, so the
+ * encoding costs about 4 + 80 / run-length bytes per site (80-byte rows).
+ * Kernel variants 8..14 read it; the results are the same bits.
  * Passage: Section 2.2 (indirect addressing of the sparse fluid-site list). */
 int hg_domain_runs(hg_domain *d, int64_t *n_runs);
 
